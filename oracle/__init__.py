@@ -1,0 +1,486 @@
+"""Plain CPU oracle for the batched alignment DP of MuSAlS (arXiv 2601.15458).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library and imports nothing from it.
+Every function takes raw byte strings (ASCII residues, ``-`` for a gap) and
+computes the plain definition of what the GPU path computes:
+
+* :func:`lev` / :func:`lev_pairs` -- the Levenshtein distance ``f`` of
+  Alg. 1 (section "Clustering"), full-matrix Wagner-Fischer (``oracle.c``).
+* :func:`nw` / :func:`nw_pairs` -- Needleman-Wunsch (section "Merging",
+  step 2) as a minimum-cost DP with a flat cost model and the traceback
+  preference diagonal > up > left (``oracle.c``).
+* :func:`brute_alignments` -- every alignment of two short strings, used to
+  pin the two functions above.
+* :func:`kmer_counts`, :func:`pair_feature` -- 4-mer count profiles and the
+  pair feature of the learned band proposer (no counterpart in the paper; the
+  definition is this project's).
+* :func:`mlp_forward`, :func:`mlp_backward`, :func:`adam_step` -- the band
+  proposer network 256->128->64->1 in float64 on bf16-rounded operands.
+* :func:`partition` -- Alg. 1 ``Partition`` with the readings listed in the
+  design notes (medoid sample rule, tie-breaks).
+* :func:`merge_tree` -- the post-order merge of section "Merging".
+
+Functions that no independent fact pins say "parity unpinned" in their
+docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc into ``liboracle.so`` (host code only)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               src, "-o", tmp])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.oracle_lev.restype = ctypes.c_int32
+            L.oracle_lev.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64]
+            L.oracle_nw.restype = ctypes.c_int32
+            L.oracle_nw.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    i32p, u8p, i64p]
+            L.oracle_lev_pairs.restype = ctypes.c_int32
+            L.oracle_lev_pairs.argtypes = [u8p, i64p, i32p, ctypes.c_int64, i32p, ctypes.c_int32]
+            L.oracle_nw_pairs.restype = ctypes.c_int32
+            L.oracle_nw_pairs.argtypes = [u8p, i64p, i32p, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          i32p, u8p, i64p, i64p, ctypes.c_int32]
+            _lib = L
+    return _lib
+
+
+def _ptr(arr: np.ndarray, ctype):
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _as_u8(s) -> np.ndarray:
+    if isinstance(s, np.ndarray):
+        return np.ascontiguousarray(s, dtype=np.uint8)
+    return np.frombuffer(bytes(s), dtype=np.uint8).copy()
+
+
+def cpu_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------------------
+# Levenshtein and Needleman-Wunsch (C, full matrix)
+# ---------------------------------------------------------------------------
+
+def lev(a, b) -> int:
+    """Unit-cost edit distance f(a, b) of Alg. 1, full-matrix Wagner-Fischer."""
+    A, B = _as_u8(a), _as_u8(b)
+    d = _load().oracle_lev(_ptr(A, ctypes.c_uint8), len(A), _ptr(B, ctypes.c_uint8), len(B))
+    if d < 0:
+        raise MemoryError("oracle_lev: matrix allocation failed")
+    return int(d)
+
+
+def nw(a, b, match: int = 0, mismatch: int = 1, gap: int = 1):
+    """Minimum-cost global alignment (section "Merging", step 2).
+
+    Returns ``(score, ops)`` with ``ops`` a bytes string over ``M X D I``
+    in forward order; ``D`` consumes a residue of ``a`` against a gap, ``I``
+    consumes a residue of ``b`` against a gap.
+    """
+    A, B = _as_u8(a), _as_u8(b)
+    ops = np.zeros(len(A) + len(B) + 1, dtype=np.uint8)
+    score = ctypes.c_int32(0)
+    L = ctypes.c_int64(0)
+    rc = _load().oracle_nw(_ptr(A, ctypes.c_uint8), len(A), _ptr(B, ctypes.c_uint8), len(B),
+                           match, mismatch, gap, ctypes.byref(score),
+                           _ptr(ops, ctypes.c_uint8), ctypes.byref(L))
+    if rc != 0:
+        raise MemoryError("oracle_nw: matrix allocation failed")
+    return int(score.value), bytes(ops[: L.value])
+
+
+def lev_pairs(arena: np.ndarray, offs: np.ndarray, pairs: np.ndarray, nthreads: int | None = None) -> np.ndarray:
+    """``f`` over a pair list ``pairs[P, 2]`` of indices into the sequence arena."""
+    arena = np.ascontiguousarray(arena, dtype=np.uint8)
+    offs = np.ascontiguousarray(offs, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(pairs), dtype=np.int32)
+    if len(pairs) == 0:
+        return out
+    rc = _load().oracle_lev_pairs(_ptr(arena, ctypes.c_uint8), _ptr(offs, ctypes.c_int64),
+                                  _ptr(pairs, ctypes.c_int32), len(pairs),
+                                  _ptr(out, ctypes.c_int32), nthreads or cpu_threads())
+    if rc != 0:
+        raise MemoryError("oracle_lev_pairs: allocation failed")
+    return out
+
+
+def nw_pairs(arena, offs, pairs, match=0, mismatch=1, gap=1, nthreads=None):
+    """NW over a pair list. Returns ``(score[P], ops_bytes, ops_off[P+1], ops_len[P])``."""
+    arena = np.ascontiguousarray(arena, dtype=np.uint8)
+    offs = np.ascontiguousarray(offs, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    lens = np.diff(offs)
+    cap = lens[pairs[:, 0]] + lens[pairs[:, 1]] if len(pairs) else np.zeros(0, np.int64)
+    ops_off = np.zeros(len(pairs) + 1, dtype=np.int64)
+    np.cumsum(cap, out=ops_off[1:])
+    ops = np.zeros(max(int(ops_off[-1]), 1), dtype=np.uint8)
+    score = np.zeros(len(pairs), dtype=np.int32)
+    ops_len = np.zeros(len(pairs), dtype=np.int64)
+    if len(pairs):
+        rc = _load().oracle_nw_pairs(_ptr(arena, ctypes.c_uint8), _ptr(offs, ctypes.c_int64),
+                                     _ptr(pairs, ctypes.c_int32), len(pairs), match, mismatch, gap,
+                                     _ptr(score, ctypes.c_int32), _ptr(ops, ctypes.c_uint8),
+                                     _ptr(ops_off, ctypes.c_int64), _ptr(ops_len, ctypes.c_int64),
+                                     nthreads or cpu_threads())
+        if rc != 0:
+            raise MemoryError("oracle_nw_pairs: allocation failed")
+    return score, ops, ops_off, ops_len
+
+
+def rescore(a, b, ops, match=0, mismatch=1, gap=1):
+    """Cost of an edit script, and the two gapped rows it spells.
+
+    Raises ``ValueError`` if the script does not consume exactly ``a`` and ``b``.
+    """
+    a, b = bytes(a), bytes(b)
+    i = j = 0
+    cost = 0
+    ra, rb = bytearray(), bytearray()
+    for o in bytes(ops):
+        if o in (ord("M"), ord("X")):
+            if i >= len(a) or j >= len(b):
+                raise ValueError("script overruns the sequences")
+            eq = a[i] == b[j]
+            if (o == ord("M")) != eq:
+                raise ValueError("M/X label disagrees with the symbols")
+            cost += match if eq else mismatch
+            ra.append(a[i]); rb.append(b[j]); i += 1; j += 1
+        elif o == ord("D"):
+            if i >= len(a):
+                raise ValueError("script overruns a")
+            cost += gap
+            ra.append(a[i]); rb.append(ord("-")); i += 1
+        elif o == ord("I"):
+            if j >= len(b):
+                raise ValueError("script overruns b")
+            cost += gap
+            ra.append(ord("-")); rb.append(b[j]); j += 1
+        else:
+            raise ValueError(f"unknown op {o!r}")
+    if i != len(a) or j != len(b):
+        raise ValueError("script does not consume both sequences")
+    return cost, bytes(ra), bytes(rb)
+
+
+# ---------------------------------------------------------------------------
+# Brute force over all alignments (pure Python, tiny inputs only)
+# ---------------------------------------------------------------------------
+
+def brute_alignments(a, b):
+    """Yield every alignment of ``a`` and ``b`` as an op string over M/X/D/I.
+
+    The number of alignments is the Delannoy number D(m, n); keep m, n <= 6.
+    """
+    a, b = bytes(a), bytes(b)
+    out = []
+
+    def rec(i, j, acc):
+        if i == len(a) and j == len(b):
+            out.append(bytes(acc))
+            return
+        if i < len(a) and j < len(b):
+            acc.append(ord("M") if a[i] == b[j] else ord("X"))
+            rec(i + 1, j + 1, acc)
+            acc.pop()
+        if i < len(a):
+            acc.append(ord("D"))
+            rec(i + 1, j, acc)
+            acc.pop()
+        if j < len(b):
+            acc.append(ord("I"))
+            rec(i, j + 1, acc)
+            acc.pop()
+
+    rec(0, 0, bytearray())
+    return out
+
+
+def brute_best(a, b, match=0, mismatch=1, gap=1):
+    """Minimum cost over all alignments, and the optimal alignment whose
+    reversed op string is least under diagonal < up < left.
+
+    The greedy traceback that prefers diagonal, then up, then left, walking
+    back from (m, n), picks exactly that alignment: every move that attains
+    D[i][j] can be completed into an optimal alignment.
+    """
+    rank = {ord("M"): 0, ord("X"): 0, ord("D"): 1, ord("I"): 2}
+    best = None
+    best_key = None
+    for ops in brute_alignments(a, b):
+        c, _, _ = rescore(a, b, ops, match, mismatch, gap)
+        key = (c, [rank[o] for o in reversed(ops)])
+        if best_key is None or key < best_key:
+            best_key, best = key, ops
+    return best_key[0], best
+
+
+# ---------------------------------------------------------------------------
+# Learned band proposer: features and network (float64 on bf16 operands)
+# ---------------------------------------------------------------------------
+
+DNA = b"ACGT"
+
+
+def kmer_counts(seq, k: int = 4) -> np.ndarray:
+    """Counts of every DNA k-mer (4**k bins) over the len-k+1 windows of ``seq``.
+
+    The k-mer with symbols s_0..s_{k-1} (A=0, C=1, G=2, T=3) has bin
+    sum_t s_t * 4**(k-1-t).  Windows containing another byte are skipped.
+    """
+    seq = bytes(seq)
+    idx = {c: v for v, c in enumerate(DNA)}
+    out = np.zeros(4 ** k, dtype=np.int64)
+    for s in range(len(seq) - k + 1):
+        v = 0
+        ok = True
+        for t in range(k):
+            c = idx.get(seq[s + t])
+            if c is None:
+                ok = False
+                break
+            v = v * 4 + c
+        if ok:
+            out[v] += 1
+    return out
+
+
+def pair_feature(ca: np.ndarray, cb: np.ndarray, la: int, lb: int) -> np.ndarray:
+    """Pair feature |c_a - c_b| / ((len_a + len_b) / 2), rounded to bf16 (as float64).
+
+    The division is taken in float32, the precision of the GPU feature kernel,
+    and the result rounded to bf16.  parity unpinned beyond the invariants in
+    the tests (it is this project's definition, not the paper's).
+    """
+    diff = np.abs(ca.astype(np.int64) - cb.astype(np.int64)).astype(np.float32)
+    den = np.float32((la + lb) * 0.5)
+    if den == 0:
+        den = np.float32(1.0)
+    return bf16_round(diff / den)
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round float32 values to the nearest bf16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_bits(x) -> np.ndarray:
+    """bf16 bit patterns (uint16) of ``x`` after :func:`bf16_round`."""
+    r = bf16_round(x).astype(np.float32)
+    return (r.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def mlp_forward(params: dict, X: np.ndarray):
+    """Forward pass y = W3 relu(W2 relu(W1 x + b1) + b2) + b3.
+
+    ``params`` holds float64 arrays W1[256,128], b1[128], W2[128,64], b2[64],
+    W3[64,1], b3[1]; the weights and ``X`` are rounded to bf16 first, the
+    hidden activations are rounded to bf16 after ReLU, biases are used as
+    given; all arithmetic is float64.  Returns ``(y, cache)``.
+    """
+    W1, W2, W3 = (bf16_round(params[k]) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (np.asarray(params[k], dtype=np.float64) for k in ("b1", "b2", "b3"))
+    X = bf16_round(X)
+    z1 = X @ W1 + b1
+    h1 = bf16_round(np.maximum(z1, 0.0))
+    z2 = h1 @ W2 + b2
+    h2 = bf16_round(np.maximum(z2, 0.0))
+    y = (h2 @ W3)[:, 0] + b3[0]
+    cache = dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2, W1=W1, W2=W2, W3=W3)
+    return y, cache
+
+
+def pinball_loss(yhat: np.ndarray, y: np.ndarray, tau: float = 0.9):
+    """Mean quantile (pinball) loss and its derivative with respect to yhat.
+
+    rho(r) = tau * r for r = y - yhat > 0, (tau - 1) * r otherwise; the
+    derivative at r <= 0 is taken as (1 - tau) / B.
+    """
+    r = y - yhat
+    B = len(y)
+    loss = np.mean(np.where(r > 0, tau * r, (tau - 1.0) * r))
+    dy = np.where(r > 0, -tau, 1.0 - tau) / B
+    return float(loss), dy
+
+
+def mlp_backward(cache: dict, dy: np.ndarray) -> dict:
+    """Gradients of the loss with respect to every parameter, given dL/dy."""
+    X, z1, h1, z2, h2 = (cache[k] for k in ("X", "z1", "h1", "z2", "h2"))
+    W2, W3 = cache["W2"], cache["W3"]
+    dy = dy.reshape(-1, 1)
+    g = {}
+    g["W3"] = h2.T @ dy
+    g["b3"] = dy.sum(axis=0)
+    dh2 = (dy @ W3.T) * (z2 > 0)
+    g["W2"] = h1.T @ dh2
+    g["b2"] = dh2.sum(axis=0)
+    dh1 = (dh2 @ W2.T) * (z1 > 0)
+    g["W1"] = X.T @ dh1
+    g["b1"] = dh1.sum(axis=0)
+    return g
+
+
+def adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) on float64 master copies."""
+    out = {}
+    for k in params:
+        m[k] = beta1 * m[k] + (1 - beta1) * grads[k]
+        v[k] = beta2 * v[k] + (1 - beta2) * grads[k] ** 2
+        mh = m[k] / (1 - beta1 ** t)
+        vh = v[k] / (1 - beta2 ** t)
+        out[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return out, m, v
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 Partition and the post-order merge
+# ---------------------------------------------------------------------------
+
+MEDOID_SAMPLE = 256
+
+
+def medoid_candidates(members):
+    """Members over which the geometric median is taken (section "Clustering").
+
+    All of C when |C| <= 256, else the 256 members at positions
+    floor(k |C| / 256), k = 0..255, of C sorted by global index (the paper
+    allows "a smaller subset" without fixing it; this is the reading taken).
+    """
+    members = sorted(members)
+    if len(members) <= MEDOID_SAMPLE:
+        return members
+    n = len(members)
+    return [members[(k * n) // MEDOID_SAMPLE] for k in range(MEDOID_SAMPLE)]
+
+
+def partition(seqs, dist=None):
+    """Alg. 1 ``Partition`` applied from the root until every leaf is a singleton.
+
+    ``seqs`` is a list of distinct byte strings.  Returns the tree as a list of
+    nodes in breadth-first order; node k is a dict with ``members`` (sorted
+    global indices), ``center``, ``left``, ``right`` (node ids or -1) and
+    ``parent``.  Ties: the geometric median and both poles take the smallest
+    global index among equal values; ``f(l, x) == f(r, x)`` goes to L exactly
+    as Alg. 1 states.
+    """
+    if dist is None:
+        cache = {}
+
+        def dist(x, y):
+            key = (x, y) if x < y else (y, x)
+            if key not in cache:
+                cache[key] = lev(seqs[key[0]], seqs[key[1]])
+            return cache[key]
+
+    nodes = [dict(members=sorted(range(len(seqs))), center=-1, left=-1, right=-1, parent=-1)]
+    q = 0
+    while q < len(nodes):
+        node = nodes[q]
+        C = node["members"]
+        if len(C) == 1:
+            node["center"] = C[0]
+        else:
+            S = medoid_candidates(C)
+            sums = [(sum(dist(x, y) for y in S), x) for x in S]
+            c = min(sums)[1]
+            node["center"] = c
+            l = min((-dist(c, x), x) for x in C)[1]
+            r = min((-dist(l, x), x) for x in C)[1]
+            Lm = [x for x in C if dist(l, x) <= dist(r, x)]
+            Rm = [x for x in C if dist(r, x) < dist(l, x)]
+            assert Lm and Rm, "de-duplicated input guarantees both children are non-empty"
+            for side, mem in (("left", Lm), ("right", Rm)):
+                node[side] = len(nodes)
+                nodes.append(dict(members=mem, center=-1, left=-1, right=-1, parent=q))
+        q += 1
+    return nodes
+
+
+def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1):
+    """Post-order merge of section "Merging" over the tree from :func:`partition`.
+
+    A leaf is the one-row MSA of its sequence.  At an internal node the two
+    children's centers, as gapped rows of the children's MSAs, are aligned by
+    :func:`nw` with ``-`` an ordinary symbol; every ``I`` op inserts an all-gap
+    column into the left child's rows, every ``D`` op into the right child's;
+    the parent's rows are the left child's rows followed by the right
+    child's.  Returns ``(rows, order, merges)``: the root MSA rows (bytes), the
+    sequence index of each row, and per internal node the NW ``(score, ops)``.
+    """
+    msa = {}
+    merges = {}
+
+    def center_row(k):
+        rows, order = msa[k]
+        return rows[order.index(nodes[k]["center"])]
+
+    # children come after parents in BFS order, so reverse order is a valid post-order
+    for k in range(len(nodes) - 1, -1, -1):
+        nd = nodes[k]
+        if nd["left"] < 0:
+            s = nd["members"][0]
+            msa[k] = ([bytes(seqs[s])], [s])
+            continue
+        L, R = nd["left"], nd["right"]
+        score, ops = nw(center_row(L), center_row(R), match, mismatch, gap)
+        merges[k] = (score, ops)
+        rowsL, ordL = msa.pop(L)
+        rowsR, ordR = msa.pop(R)
+        newL = [bytearray() for _ in rowsL]
+        newR = [bytearray() for _ in rowsR]
+        i = j = 0
+        for o in ops:
+            if o in (ord("M"), ord("X"), ord("D")):
+                for t, r in enumerate(rowsL):
+                    newL[t].append(r[i])
+                i += 1
+            else:
+                for t in range(len(rowsL)):
+                    newL[t].append(ord("-"))
+            if o in (ord("M"), ord("X"), ord("I")):
+                for t, r in enumerate(rowsR):
+                    newR[t].append(r[j])
+                j += 1
+            else:
+                for t in range(len(rowsR)):
+                    newR[t].append(ord("-"))
+        msa[k] = ([bytes(r) for r in newL] + [bytes(r) for r in newR], ordL + ordR)
+    rows, order = msa[0]
+    return rows, order, merges

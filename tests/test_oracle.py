@@ -1,0 +1,303 @@
+"""Pins for the CPU oracle: facts that do not come from the oracle itself.
+
+Levenshtein: textbook values, metric axioms, closed forms, brute force over
+all alignments.  NW: brute force pins both the optimal cost and the exact
+tie-broken alignment; rescoring and de-gapping.  Partition: a closed-form
+line metric and the invariants Alg. 1 implies.  Merge: a worked example by
+hand and the postconditions of section "Merging".  MLP: finite differences,
+a library bf16 cast, the first Adam step in closed form.
+"""
+import itertools
+import os
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15458_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _golden_lev():
+    rows = []
+    with open(os.path.join(GOLDEN, "lev_textbook.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            a, b, d = line.split()
+            rows.append((b"" if a == "~" else a.encode(), b"" if b == "~" else b.encode(), int(d)))
+    return rows
+
+
+@pytest.mark.parametrize("a,b,d", _golden_lev())
+def test_lev_textbook(a, b, d):
+    assert oracle.lev(a, b) == d
+    assert oracle.lev(b, a) == d
+
+
+def _rand_dna(rng, n):
+    return rng.choice(list(b"ACGT"), size=n).astype(np.uint8).tobytes()
+
+
+def test_lev_metric_axioms():
+    rng = np.random.default_rng(11)
+    seqs = [_rand_dna(rng, int(rng.integers(0, 40))) for _ in range(25)]
+    for x in seqs:
+        assert oracle.lev(x, x) == 0
+    for x, y in itertools.combinations(seqs, 2):
+        d = oracle.lev(x, y)
+        assert d == oracle.lev(y, x)
+        assert abs(len(x) - len(y)) <= d <= max(len(x), len(y))
+        if x != y:
+            assert d > 0
+    for x, y, z in itertools.islice(itertools.combinations(seqs, 3), 400):
+        assert oracle.lev(x, z) <= oracle.lev(x, y) + oracle.lev(y, z)
+
+
+def test_lev_closed_forms():
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        b = _rand_dna(rng, int(rng.integers(0, 60)))
+        k = int(rng.integers(0, len(b) + 1))
+        assert oracle.lev(b"", b) == len(b)
+        assert oracle.lev(b[:k], b) == len(b) - k       # prefix
+        assert oracle.lev(b[k:], b) == k                # suffix
+        # Hamming bound: equal lengths, d <= number of mismatching positions
+        c = _rand_dna(rng, len(b))
+        assert oracle.lev(b, c) <= sum(x != y for x, y in zip(b, c))
+    # disjoint alphabets: d = max(m, n)
+    assert oracle.lev(b"AAAA", b"CCCCCC") == 6
+
+
+def test_lev_bruteforce_small():
+    rng = np.random.default_rng(13)
+    for _ in range(60):
+        a = _rand_dna(rng, int(rng.integers(0, 7)))
+        b = _rand_dna(rng, int(rng.integers(0, 7)))
+        best = min(oracle.rescore(a, b, ops)[0] for ops in oracle.brute_alignments(a, b))
+        assert oracle.lev(a, b) == best
+
+
+def test_brute_alignment_count_is_delannoy():
+    # number of alignments of strings of lengths m, n is the Delannoy number D(m, n)
+    delannoy = {(1, 1): 3, (2, 2): 13, (3, 3): 63, (2, 3): 25, (6, 6): 8989}
+    for (m, n), D in delannoy.items():
+        assert len(oracle.brute_alignments(b"A" * m, b"C" * n)) == D
+
+
+@pytest.mark.parametrize("costs", [(0, 1, 1), (0, 3, 2), (-1, 2, 3)])
+def test_nw_bruteforce_exact_alignment(costs):
+    rng = np.random.default_rng(14 + sum(costs))
+    for _ in range(80):
+        alpha = list(b"ACG-")
+        a = rng.choice(alpha, size=int(rng.integers(0, 7))).astype(np.uint8).tobytes()
+        b = rng.choice(alpha, size=int(rng.integers(0, 7))).astype(np.uint8).tobytes()
+        score, ops = oracle.nw(a, b, *costs)
+        bcost, bops = oracle.brute_best(a, b, *costs)
+        assert score == bcost
+        assert ops == bops
+
+
+def test_nw_rescore_and_degap():
+    rng = np.random.default_rng(15)
+    for _ in range(40):
+        a = _rand_dna(rng, int(rng.integers(0, 80)))
+        b = _rand_dna(rng, int(rng.integers(0, 80)))
+        score, ops = oracle.nw(a, b)
+        cost, ra, rb = oracle.rescore(a, b, ops)
+        assert cost == score
+        assert ra.replace(b"-", b"") == a and rb.replace(b"-", b"") == b
+        assert len(ra) == len(rb) == len(ops)
+        assert score == oracle.lev(a, b)                  # unit costs: NW cost == f
+
+
+def test_nw_worked_example():
+    # kitten -> sitting: k/s substitution, e/i substitution, insert g
+    score, ops = oracle.nw(b"kitten", b"sitting")
+    assert score == 3
+    assert ops == b"XMMMXMI"
+    # empty operands
+    assert oracle.nw(b"", b"ACG") == (3, b"III")
+    assert oracle.nw(b"AC", b"") == (2, b"DD")
+
+
+def test_pairs_versions_match_single():
+    ds = synth.small_dna(seed=1, n=12)
+    pairs = synth.all_pairs(ds.n)
+    d = oracle.lev_pairs(ds.arena, ds.offs, pairs, nthreads=3)
+    for (x, y), v in zip(pairs, d):
+        assert v == oracle.lev(ds.seq(x), ds.seq(y))
+    score, ops, off, ln = oracle.nw_pairs(ds.arena, ds.offs, pairs[:20], nthreads=2)
+    for p, (x, y) in enumerate(pairs[:20]):
+        s, o = oracle.nw(ds.seq(x), ds.seq(y))
+        assert s == score[p] and o == ops[off[p]:off[p] + ln[p]].tobytes()
+
+
+# ---------------------------------------------------------------------------
+# Partition (Alg. 1) and merge
+# ---------------------------------------------------------------------------
+
+def test_partition_line_metric_closed_form():
+    # "A"*k for k = 1..7: f(x, y) = |len x - len y|, so every step of Alg. 1
+    # follows from the line.  Derived by hand:
+    #   root {1..7}: medoid 4; l = argmax |4-x| -> tie 1, 7 -> smallest index -> 1;
+    #   r = argmax |1-x| = 7; L = {x : |x-1| <= |x-7|} = {1,2,3,4}, R = {5,6,7}
+    #   {1,2,3,4}: medoid sums 6,4,4,6 -> 2; l = 4; r = 1; L = {3,4}, R = {1,2}
+    #   {5,6,7}: medoid 6; l = 5 (tie 5,7); r = 7; L = {5,6}, R = {7}
+    seqs = [b"A" * k for k in range(1, 8)]
+    nodes = oracle.partition(seqs)
+    got = [(nd["members"], nd["center"]) for nd in nodes]
+    idx = lambda *ks: [k - 1 for k in ks]  # noqa: E731
+    assert got[0] == (idx(1, 2, 3, 4, 5, 6, 7), 3)
+    assert got[1] == (idx(1, 2, 3, 4), 1)
+    assert got[2] == (idx(5, 6, 7), 5)
+    assert got[3] == (idx(3, 4), 2)
+    assert got[4] == (idx(1, 2), 0)
+    assert got[5] == (idx(5, 6), 4)
+    assert got[6] == (idx(7), 6)
+
+
+def _check_tree(nodes, n):
+    leaves = [nd for nd in nodes if nd["left"] < 0]
+    assert sorted(x for nd in leaves for x in nd["members"]) == list(range(n))
+    for nd in leaves:
+        assert len(nd["members"]) == 1
+    for nd in nodes:
+        if nd["left"] >= 0:
+            L, R = nodes[nd["left"]]["members"], nodes[nd["right"]]["members"]
+            assert L and R
+            assert sorted(L + R) == nd["members"]
+            assert nd["center"] in nd["members"]
+
+
+def test_partition_invariants_random():
+    ds = synth.small_dna(seed=3, n=24)
+    nodes = oracle.partition(ds.seqs())
+    _check_tree(nodes, ds.n)
+    assert len(nodes) == 2 * ds.n - 1
+
+
+def test_medoid_sample_rule():
+    assert oracle.medoid_candidates(list(range(10))) == list(range(10))
+    c = oracle.medoid_candidates(list(range(1000, 0, -1)))
+    assert len(c) == 256 and c[0] == 1 and c == sorted(c)
+    assert c[1] == 1 + (1000 // 256)
+
+
+def test_merge_worked_example():
+    # seqs AC, A: root medoid tie -> index 0 (AC); l = 1 (A); r = 0;
+    # L = {1}, R = {0}; NW(A, AC) = 1 with script M then I (derived by hand);
+    # the left block gains a gap column at the end.
+    rows, order, merges = oracle.merge_tree([b"AC", b"A"], oracle.partition([b"AC", b"A"]))
+    assert order == [1, 0]
+    assert rows == [b"A-", b"AC"]
+    assert merges[0] == (1, b"MI")
+
+
+def test_merge_postconditions():
+    ds = synth.small_dna(seed=4, n=20)
+    seqs = ds.seqs()
+    nodes = oracle.partition(seqs)
+    rows, order, merges = oracle.merge_tree(seqs, nodes)
+    assert sorted(order) == list(range(ds.n))
+    w = len(rows[0])
+    assert all(len(r) == w for r in rows)
+    assert w >= max(len(s) for s in seqs)
+    for r, s in zip(rows, order):
+        assert r.replace(b"-", b"") == seqs[s]
+    assert len(merges) == ds.n - 1
+
+
+# ---------------------------------------------------------------------------
+# features and network
+# ---------------------------------------------------------------------------
+
+def test_kmer_counts_against_counter():
+    rng = np.random.default_rng(16)
+    for L in (0, 3, 4, 5, 57):
+        s = _rand_dna(rng, L)
+        c = oracle.kmer_counts(s)
+        ref = Counter(s[i:i + 4] for i in range(len(s) - 3))
+        assert c.sum() == max(0, L - 3)
+        for kmer, cnt in ref.items():
+            v = int("".join(str(b"ACGT".index(ch)) for ch in kmer), 4)
+            assert c[v] == cnt
+    assert oracle.kmer_counts(b"AAAA")[0] == 1
+    assert oracle.kmer_counts(b"ACGT")[0b00011011] == 1
+
+
+def test_kmer_l1_lower_bound():
+    # one edit changes at most 4 windows out and 4 in: ||c_a - c_b||_1 <= 8 f(a, b)
+    rng = np.random.default_rng(17)
+    for _ in range(30):
+        a = _rand_dna(rng, int(rng.integers(4, 120)))
+        b = _rand_dna(rng, int(rng.integers(4, 120)))
+        l1 = np.abs(oracle.kmer_counts(a) - oracle.kmer_counts(b)).sum()
+        assert l1 <= 8 * oracle.lev(a, b)
+
+
+def test_bf16_round_against_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(18)
+    x = np.concatenate([rng.standard_normal(1000).astype(np.float32) * 100,
+                        np.float32([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, np.pi, 0.0, -2.5])])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(x), ref)
+    assert oracle.bf16_round(np.float32(1 + 2 ** -8)) == 1.0          # tie to even
+    assert oracle.bf16_round(np.float32(1 + 3 * 2 ** -8)) == 1 + 2 ** -6
+
+
+def _params(rng, scale=0.2):
+    return dict(W1=rng.standard_normal((256, 128)) * scale / 4, b1=rng.standard_normal(128) * 0.1,
+                W2=rng.standard_normal((128, 64)) * scale, b2=rng.standard_normal(64) * 0.1,
+                W3=rng.standard_normal((64, 1)) * scale, b3=rng.standard_normal(1) * 0.1)
+
+
+def test_mlp_gradients_finite_differences(monkeypatch):
+    # with bf16 rounding replaced by the identity the network is smooth almost
+    # everywhere; central differences in float64 pin the analytic backward pass
+    monkeypatch.setattr(oracle, "bf16_round", lambda x: np.asarray(x, dtype=np.float64))
+    rng = np.random.default_rng(19)
+    P = _params(rng)
+    X = np.abs(rng.standard_normal((16, 256)))
+    # targets kept at least 0.5 away from the prediction: no pinball kink in reach
+    y0, _ = oracle.mlp_forward(P, X)
+    y = y0 + np.where(rng.random(16) < 0.5, -1.0, 1.0) * (0.5 + rng.random(16))
+
+    def loss_of(p):
+        yh, _ = oracle.mlp_forward(p, X)
+        return oracle.pinball_loss(yh, y)[0]
+
+    yh, cache = oracle.mlp_forward(P, X)
+    _, dy = oracle.pinball_loss(yh, y)
+    G = oracle.mlp_backward(cache, dy)
+    h = 1e-6
+    for k in P:
+        flat = P[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            Pp = {q: v.copy() for q, v in P.items()}
+            Pm = {q: v.copy() for q, v in P.items()}
+            Pp[k].reshape(-1)[idx] += h
+            Pm[k].reshape(-1)[idx] -= h
+            fd = (loss_of(Pp) - loss_of(Pm)) / (2 * h)
+            assert abs(fd - G[k].reshape(-1)[idx]) <= 1e-6 + 1e-4 * abs(fd), (k, idx)
+
+
+def test_pinball_closed_form():
+    loss, dy = oracle.pinball_loss(np.array([0.0, 2.0]), np.array([1.0, 1.0]), tau=0.9)
+    assert loss == pytest.approx((0.9 * 1.0 + 0.1 * 1.0) / 2)
+    np.testing.assert_allclose(dy, [-0.9 / 2, 0.1 / 2])
+
+
+def test_adam_first_step_closed_form():
+    # from zero moments the bias-corrected first step is -lr * g / (|g| + eps)
+    g = {"w": np.array([0.5, -2.0, 1e-3])}
+    p = {"w": np.zeros(3)}
+    m = {"w": np.zeros(3)}
+    v = {"w": np.zeros(3)}
+    out, _, _ = oracle.adam_step(p, g, m, v, t=1, lr=0.01)
+    np.testing.assert_allclose(out["w"], -0.01 * g["w"] / (np.abs(g["w"]) + 1e-8))
