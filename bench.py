@@ -1,0 +1,325 @@
+"""Benchmark of the batched alignment DP hot path on GB300.
+
+Default workload (N=1): 2,000 DNA sequences simulated down a random binary
+tree from a uniform root of length 1,500 (lengths ~1,200-1,800), all
+1,999,000 pairwise unit-cost Levenshtein distances in one call.  One step =
+pack the ASCII arena (A1) + the whole distance batch (A2, A3, A7).  The
+metric is GCUPS = sum over pairs of m*n cells / seconds / 1e9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own copy of the batch (pairs are
+independent; no collective on the data path), so scaling is weak and the
+value is the cells of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALU_OPS_PER_WORD = 11    # integer ops of one 32-row word step (bv_word)
+WORKLOAD = "tree_dna_allpairs_2000x1500"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=2000, help="sequences (default: the 2,000-sequence workload)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(n):
+    from paper_2601_15458_gb300 import synth
+    ds = synth.tree_dna(seed=2, n=n)
+    pairs = synth.all_pairs_balanced(ds.n)
+    lens = np.diff(ds.offs)
+    m = lens[pairs[:, 0]].astype(np.int64)
+    nn = lens[pairs[:, 1]].astype(np.int64)
+    cells = int((m * nn).sum())
+    words = int((((m + 31) // 32) * nn).sum())
+    return ds, pairs, cells, words
+
+
+def cpu_oracle_sample(ds, pairs, seconds, seed=7):
+    """Time the oracle on a seeded sample of pairs sized to about `seconds`."""
+    import oracle
+    threads = oracle.cpu_threads()
+    rng = np.random.default_rng(seed)
+    lens = np.diff(ds.offs)
+    calib = pairs[rng.choice(len(pairs), size=min(len(pairs), 4 * threads), replace=False)]
+    t0 = time.perf_counter()
+    oracle.lev_pairs(ds.arena, ds.offs, calib, nthreads=threads)
+    dt = time.perf_counter() - t0
+    per_pair = dt / len(calib)
+    k = int(max(threads, min(len(pairs), seconds / max(per_pair, 1e-9))))
+    sample = pairs[rng.choice(len(pairs), size=k, replace=False)]
+    t0 = time.perf_counter()
+    oracle.lev_pairs(ds.arena, ds.offs, sample, nthreads=threads)
+    dt = time.perf_counter() - t0
+    cells = int((lens[sample[:, 0]].astype(np.int64) * lens[sample[:, 1]]).sum())
+    return dict(value=cells / dt / 1e9, unit="GCUPS", cores=threads, kind="oracle",
+                sample=f"{k} random pairs of the workload ({cells:.3e} cells, {dt:.1f} s)"), cells, dt
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() in ("active", "1", "0x1"):
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in rows), sm_max_mhz=max(r["smax"] for r in rows),
+                    reasons=sorted(reasons), samples=len(rows),
+                    power_w_max=max(r["power"] for r in rows))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, sm_max_mhz=2070.0), "fallback"
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return
+    ds, pairs, cells, words = make_workload(args.n)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    total_cells = 0
+    total_t = 0.0
+    info = None
+    for s in range(args.warmup + args.steps):
+        info, c, dt = cpu_oracle_sample(ds, pairs, per_step, seed=100 + s)
+        if s >= args.warmup:
+            vals.append(info["value"])
+            total_cells += c
+            total_t += dt
+    value = total_cells / total_t / 1e9
+    line = dict(metric="GCUPS", value=value, unit="GCUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * total_t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="int32", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, n_seqs=ds.n, pairs=len(pairs), cells=cells,
+                            note="reference arm = the CPU oracle (full-matrix Wagner-Fischer) on seeded samples"),
+                cpu_baseline=dict(info, value=value),
+                e2e=dict(value=value, unit="GCUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2601_15458_gb300 import api, build
+    build.build()
+    ctx = api.Context(local, workspace_bytes=2 << 30)
+    ds, pairs, cells, words = make_workload(args.n)
+    stream = torch.cuda.current_stream()
+
+    # device-resident inputs
+    seqs = api.DeviceSeqs.from_host(ds.arena, ds.offs, ds.alphabet)
+    pairs_d = torch.from_numpy(pairs).cuda()
+    out = torch.empty(len(pairs), dtype=torch.int32, device="cuda")
+    api.pack(ctx, seqs)
+    api.lev_autotune(ctx, seqs, pairs_d, out)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        api.pack(ctx, seqs)
+        api.lev_batch(ctx, seqs, pairs_d, out)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    ctx.check()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.prof_read(reset=True)
+    ctx.prof_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)          # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier()
+    ctx.prof_enable(False)
+    dp_ms, launches = ctx.prof_read(reset=True)
+    ctx.check()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, dp_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, dp_ms = float(t[0]), float(t[1])
+    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
+
+    # end to end through the public API: host buffers, copies inside the timed region
+    h_arena = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [ds.arena, np.zeros((-len(ds.arena)) % 16 + 16, np.uint8)]))).pin_memory()
+    h_offs = torch.from_numpy(ds.offs.astype(np.int64)).pin_memory()
+    h_pairs = torch.from_numpy(pairs).pin_memory()
+    h_out = torch.empty(len(pairs), dtype=torch.int32).pin_memory()
+    d_ascii = torch.empty_like(h_arena, device="cuda")
+    d_offs = torch.empty_like(h_offs, device="cuda")
+    d_pairs = torch.empty_like(h_pairs, device="cuda")
+    e2e_seqs = api.DeviceSeqs(d_ascii, d_offs, "dna", int(np.diff(ds.offs).max()), int(ds.offs[-1]))
+
+    def e2e_step():
+        d_ascii.copy_(h_arena, non_blocking=True)
+        d_offs.copy_(h_offs, non_blocking=True)
+        d_pairs.copy_(h_pairs, non_blocking=True)
+        api.pack(ctx, e2e_seqs)
+        api.lev_batch(ctx, e2e_seqs, d_pairs, out)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    ctx.check()
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        eev[k][0].record(stream)
+        e2e_step()
+        eev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+    e2e_value = world * cells * args.steps / (e2e_ms / 1e3) / 1e9
+    h2d = h_arena.numel() + h_offs.numel() * 8 + h_pairs.numel() * 4
+    d2h = h_out.numel() * 4
+    ok = np.array_equal(h_out.numpy(), out.cpu().numpy())
+
+    # roofline of the DP kernels: integer issue bound
+    pk, pk_kind = peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e12   # T int32 lane-ops/s
+    alg_ops = words * ALU_OPS_PER_WORD
+    achieved = alg_ops * args.steps / (dp_ms / 1e3) / 1e12 if dp_ms > 0 else None
+    roof = dict(bound="alu", kernel="lev_lane_kernel (all length buckets)", achieved=achieved, peak=alu_peak,
+                unit="Tops/s (int32 lane-ops)", frac=(achieved / alu_peak) if achieved else None, traffic=None,
+                peak_source=f"{props.multi_processor_count} SMs x 4 issue/clk x 32 lanes x {sm_max:.0f} MHz "
+                            f"({pk_kind} max clock)",
+                algorithmic=f"{ALU_OPS_PER_WORD} ops per 32-row word per column; "
+                            f"{words:.4e} word-columns per launch set")
+
+    clocks = clk.summary()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_oracle_sample(ds, pairs, args.cpu_seconds)
+    if rank == 0:
+        line = dict(metric="GCUPS", value=value, unit="GCUPS", n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
+                    config=dict(workload=WORKLOAD, n_seqs=ds.n, pairs=len(pairs), cells=cells,
+                                pairs_per_s=world * len(pairs) * args.steps / (total_ms / 1e3),
+                                l2="flushed between timed steps (256 MB write)", step="msa_pack + msa_lev_batch"),
+                    roofline=roof, cpu_baseline=cpu,
+                    e2e=dict(value=e2e_value, unit="GCUPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                             output_matches_device=bool(ok)),
+                    gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps,
+                    wall_s_timed=t_wall, clocks=clocks)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * msa.h -- C ABI of the GB300 (sm_103a) batched alignment DP library that
+ * serves the hot path of MuSAlS (arXiv 2601.15458).
+ *
+ * The paper builds its guide tree by Alg. 1 ("Partition", section
+ * "Clustering"), which calls the Levenshtein distance f on one-to-many
+ * batches, and merges clusters bottom-up (section "Merging") by aligning two
+ * cluster centers with Needleman-Wunsch and noting where gaps go.  This
+ * library computes those two DPs in batches on one GPU.
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers owned by the caller, unless the
+ *    comment says "host".  The library never frees them.  It allocates only
+ *    its context workspace (msa_ctx_create) and never allocates inside a call.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) and returns a status synchronously for argument errors
+ *    (MSA_EINVAL: null pointer, negative count, unsupported alphabet, a size
+ *    beyond the workspace -> MSA_ENOMEM).  Errors found by a kernel (index out
+ *    of range, a symbol outside the alphabet, a length above max_len) are
+ *    recorded in a device status word; msa_ctx_check() synchronises the
+ *    stream and returns them.  Kernels never trap and never wait without a
+ *    bound.
+ *  - A pair (a, b) puts a on the DP rows (i = 0..m) and b on the columns
+ *    (j = 0..n).  Levenshtein is symmetric; NW output is defined for the
+ *    order given.
+ *  - Empty sequences are allowed; P = 0 is a no-op returning MSA_OK.
+ */
+#ifndef MSA_H
+#define MSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msa_ctx msa_ctx;
+typedef int32_t msa_status;
+
+#define MSA_OK            0
+#define MSA_EINVAL        1  /* bad argument (host-detected)                          */
+#define MSA_ENOMEM        2  /* workspace too small for this call / allocation failed */
+#define MSA_ECUDA         3  /* a CUDA runtime call failed                             */
+#define MSA_ETIMEOUT      4  /* a bounded device wait ran out                          */
+#define MSA_EUNSUPPORTED  5  /* configuration not built into this library              */
+#define MSA_EDATA         6  /* device-detected bad data (index, symbol, length)       */
+
+#define MSA_DNA      0       /* A C G T            -> codes 0..3,  gap code 4  */
+#define MSA_PROTEIN  1       /* ACDEFGHIKLMNPQRSTVWY -> codes 0..19, gap code 20 */
+
+/* Edit-script bytes written by msa_nw_align_batch (forward order). */
+#define MSA_OP_MATCH     'M' /* diagonal, a_i == b_j                  */
+#define MSA_OP_MISMATCH  'X' /* diagonal, a_i != b_j                  */
+#define MSA_OP_DEL       'D' /* up: a_i against a gap (consumes a)    */
+#define MSA_OP_INS       'I' /* left: b_j against a gap (consumes b)  */
+
+/*
+ * A set of sequences in one arena.  Sequence s occupies arena positions
+ * [offs[s], offs[s+1]).  `ascii` holds residues (one byte each, upper case);
+ * msa_pack() turns it into `codes` (one byte per position, 0..sigma-1) and
+ * `planes` (bit planes: for arena word w = position / 32 and plane p < B,
+ * planes[w * B + p] bit (position % 32) is bit p of the code; B = 2 for DNA,
+ * 5 for protein).  Both outputs are caller-allocated with the sizes given by
+ * msa_code_bytes() and msa_plane_words().
+ */
+typedef struct msa_seqset {
+    const uint8_t *ascii;   /* device, >= total bytes, 16-byte aligned             */
+    const int64_t *offs;    /* device, n_seqs + 1 entries, offs[0] = 0, ascending    */
+    uint8_t *codes;         /* device, msa_code_bytes(total) bytes (written by pack) */
+    uint32_t *planes;       /* device, msa_plane_words(total, alphabet) words        */
+    int64_t total;          /* host copy of offs[n_seqs]                             */
+    int32_t n_seqs;
+    int32_t alphabet;       /* MSA_DNA or MSA_PROTEIN                                */
+    int32_t max_len;        /* host: bound on every length, checked on the device    */
+    int32_t reserved;
+} msa_seqset;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on `device` with `workspace_bytes` of device scratch
+ * (<= 0 picks 1 GiB).  The workspace bounds the batch sizes of later calls. */
+msa_status msa_ctx_create(msa_ctx **out, int32_t device, int64_t workspace_bytes);
+void msa_ctx_destroy(msa_ctx *ctx);
+/* Synchronises `stream`, returns and clears the first device-recorded error. */
+msa_status msa_ctx_check(msa_ctx *ctx, void *stream);
+/* Text of the last error recorded on this context (host string, owned by ctx). */
+const char *msa_last_error(const msa_ctx *ctx);
+/* Library version string, e.g. "msa-gb300 0.1 sm_103a". */
+const char *msa_version(void);
+
+/* Launch accounting: when enabled, each DP call brackets its DP kernels (the
+ * distance / alignment kernels, not the scheduling ones) with CUDA events on
+ * its stream.  msa_prof_read waits for those events and returns the summed
+ * milliseconds and the number of kernels this context launched; reset != 0
+ * zeroes both. */
+msa_status msa_prof_enable(msa_ctx *ctx, int32_t on);
+msa_status msa_prof_read(msa_ctx *ctx, double *dp_kernel_ms, int64_t *launches, int32_t reset);
+
+/* ---- sizes (pure host arithmetic) --------------------------------------- */
+int64_t msa_code_bytes(int64_t total);
+int64_t msa_plane_words(int64_t total, int32_t alphabet);
+/* Workspace bytes msa_lev_batch needs for P pairs over n_seqs sequences. */
+int64_t msa_lev_workspace_bytes(int64_t P, int32_t n_seqs);
+
+/* ---- A1: packed-sequence loader ----------------------------------------- */
+/*
+ * Reads the ASCII arena once with 16-byte loads and writes the byte codes and
+ * the bit planes; checks every residue against the alphabet and every length
+ * against max_len (MSA_EDATA via msa_ctx_check otherwise).
+ */
+msa_status msa_pack(msa_ctx *ctx, const msa_seqset *s, void *stream);
+
+/* ---- A2/A3/A7: batched Levenshtein distance ----------------------------- */
+/*
+ * d_out[p] = f(seq[pairs[2p]], seq[pairs[2p+1]]), the unit-cost edit
+ * distance f of Alg. 1 (section "Clustering"), exactly.
+ * pairs: device int32 [P][2]; d_out: device int32 [P].  P < 2^31.
+ * Pairs are grouped by their first index on the device; a warp shares the
+ * bit-vector match masks of that first sequence, so listing many pairs with
+ * the same first index (one-to-many, as Alg. 1 does) is the fast case.
+ * Needs msa_lev_workspace_bytes(P, n_seqs) of workspace.
+ */
+msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
+                         int64_t P, int32_t *d_out, void *stream);
+
+/* Selects the kernel schedule of msa_lev_batch (lane-versus-warp threshold,
+ * targets per task) by running this batch under each candidate and timing it
+ * with CUDA events; the fastest is kept in ctx for later calls.  d_out ends
+ * up holding the distances, as after msa_lev_batch.  Synchronises `stream`. */
+msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
+                            int64_t P, int32_t *d_out, void *stream);
+
+/* ---- A5/A6: Needleman-Wunsch with traceback ----------------------------- */
+/*
+ * Global alignment of every pair (section "Merging", step 2: align the two
+ * children's centers and note where gaps were added).  Minimum-cost DP with
+ * a flat cost model:
+ *   D[i][0] = i*gap, D[0][j] = j*gap,
+ *   D[i][j] = min(D[i-1][j-1] + (a_i == b_j ? match : mismatch),
+ *                 D[i-1][j] + gap, D[i][j-1] + gap).
+ * Among the moves that attain D[i][j] the traceback takes diagonal, then up
+ * (a_i against a gap), then left (b_j against a gap); the paper fixes no
+ * tie-break and this order is the one this library defines.
+ * Sequences are byte strings compared by equality (any byte values: packed
+ * codes, gapped rows with a gap code, or ASCII).  Sequence s is
+ * codes[offs[s] .. offs[s+1]); offs has n_seqs + 1 entries within [0, total].
+ * pairs: device int32 [P][2] (a = pairs[2p], b = pairs[2p+1]).
+ * Outputs (device): score_out[p] = D[m][n]; ops_out[ops_off[p] ..
+ * ops_off[p] + ops_len_out[p]) = the edit script in forward order over the
+ * MSA_OP_* bytes.  ops_off (device, caller-filled) must give each pair at
+ * least m + n bytes.  max_len (host) bounds every length; the call uses
+ * msa_nw_workspace_bytes(max_len, warps) of workspace for as many warps as
+ * fit (at least 4), so it fails with MSA_ENOMEM only when 4 do not fit.
+ */
+msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                              int64_t total, int32_t max_len, const int32_t *pairs, int64_t P,
+                              int32_t match, int32_t mismatch, int32_t gap, int32_t *score_out,
+                              uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                              void *stream);
+/* Workspace bytes msa_nw_align_batch needs to run `warps` pairs at once. */
+int64_t msa_nw_workspace_bytes(int32_t max_len, int32_t warps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSA_H */

@@ -1,0 +1,214 @@
+"""Python entry points over the C ABI of ``include/msa.h``.
+
+PyTorch provides device memory and streams; every computation runs in the
+library's CUDA kernels.  All functions take device tensors and enqueue on the
+current (or given) CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MSA_DNA, MSA_PROTEIN, SeqSetC
+
+
+class MsaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"msa status {code}: {msg}")
+        self.code = code
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """Owns the library context: device workspace and the autotune table."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 1 << 30):
+        torch.cuda.init()
+        self.device = device
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            rc = _lib.lib().msa_ctx_create(ctypes.byref(self._h), device, int(workspace_bytes))
+        if rc != 0:
+            raise MsaError(rc, "msa_ctx_create failed")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def error(self) -> str:
+        return _lib.lib().msa_last_error(self._h).decode()
+
+    def raise_if(self, rc: int):
+        if rc != 0:
+            raise MsaError(rc, self.error())
+
+    def check(self, stream=None):
+        """Synchronise the stream and raise on any device-recorded error."""
+        self.raise_if(_lib.lib().msa_ctx_check(self._h, _stream(stream)))
+
+    def prof_enable(self, on: bool = True):
+        self.raise_if(_lib.lib().msa_prof_enable(self._h, 1 if on else 0))
+
+    def prof_read(self, reset: bool = True):
+        """(summed DP-kernel milliseconds, kernels launched) since the last reset."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self.raise_if(_lib.lib().msa_prof_read(self._h, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
+        return ms.value, n.value
+
+    def close(self):
+        if self._h:
+            _lib.lib().msa_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ALPHA = {"dna": MSA_DNA, "protein": MSA_PROTEIN}
+
+
+class DeviceSeqs:
+    """A sequence set resident on the GPU: ASCII arena, offsets, and the
+    packed codes / bit planes written by :func:`pack`."""
+
+    def __init__(self, ascii: torch.Tensor, offs: torch.Tensor, alphabet: str, max_len: int, total: int):
+        self.alphabet = alphabet
+        self.alpha = _ALPHA[alphabet]
+        self.ascii = ascii
+        self.offs = offs
+        self.n = offs.numel() - 1
+        self.total = int(total)
+        self.max_len = int(max_len)
+        L = _lib.lib()
+        self.codes = torch.empty(int(L.msa_code_bytes(self.total)), dtype=torch.uint8, device=ascii.device)
+        self.planes = torch.empty(int(L.msa_plane_words(self.total, self.alpha)), dtype=torch.int32,
+                                  device=ascii.device)
+        self.c = SeqSetC(_ptr(ascii), _ptr(offs), _ptr(self.codes), _ptr(self.planes), self.total,
+                         self.n, self.alpha, self.max_len, 0)
+
+    @staticmethod
+    def from_host(arena: np.ndarray, offs: np.ndarray, alphabet: str = "dna", device="cuda",
+                  pinned: bool = False) -> "DeviceSeqs":
+        """Copy a host arena (``synth.SeqSet`` layout) to the device (H2D only)."""
+        total = int(offs[-1]) if len(offs) else 0
+        buf = np.zeros(max(16, (total + 15) // 16 * 16), dtype=np.uint8)
+        buf[:total] = arena[:total]
+        a = torch.from_numpy(buf)
+        o = torch.from_numpy(np.ascontiguousarray(offs, dtype=np.int64))
+        if pinned:
+            a, o = a.pin_memory(), o.pin_memory()
+        lens = np.diff(offs)
+        max_len = int(lens.max()) if len(lens) else 0
+        return DeviceSeqs(a.to(device, non_blocking=pinned), o.to(device, non_blocking=pinned),
+                          alphabet, max_len, total)
+
+
+def pack(ctx: Context, seqs: DeviceSeqs, stream=None) -> DeviceSeqs:
+    """A1: ASCII -> byte codes + bit planes (msa_pack)."""
+    ctx.raise_if(_lib.lib().msa_pack(ctx.handle, ctypes.byref(seqs.c), _stream(stream)))
+    return seqs
+
+
+def upload_and_pack(ctx: Context, ds, stream=None, pinned=False) -> DeviceSeqs:
+    """Copy a ``synth.SeqSet`` to the device and pack it."""
+    seqs = DeviceSeqs.from_host(ds.arena, ds.offs, ds.alphabet, pinned=pinned)
+    return pack(ctx, seqs, stream)
+
+
+def _pairs_tensor(pairs) -> torch.Tensor:
+    if isinstance(pairs, np.ndarray):
+        pairs = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32))
+    if pairs.device.type != "cuda":
+        pairs = pairs.cuda()
+    return pairs.contiguous().view(-1, 2)
+
+
+def lev_batch(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """A2/A3: Levenshtein distance of every pair (msa_lev_batch); int32 [P]."""
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=pairs.device)
+    ctx.raise_if(_lib.lib().msa_lev_batch(ctx.handle, ctypes.byref(seqs.c), _ptr(pairs), P, _ptr(out),
+                                          _stream(stream)))
+    return out
+
+
+class ByteSeqs:
+    """Byte strings on the device for NW: ``codes[offs[s]:offs[s+1]]``."""
+
+    def __init__(self, codes: torch.Tensor, offs: torch.Tensor, max_len: int, total: int | None = None):
+        self.codes = codes
+        self.offs = offs
+        self.n = offs.numel() - 1
+        self.max_len = int(max_len)
+        self.total = int(codes.numel()) if total is None else int(total)
+
+    @staticmethod
+    def from_device_seqs(seqs: "DeviceSeqs") -> "ByteSeqs":
+        return ByteSeqs(seqs.codes, seqs.offs, seqs.max_len, seqs.total)
+
+    @staticmethod
+    def from_list(rows, device="cuda") -> "ByteSeqs":
+        lens = np.array([len(r) for r in rows], np.int64)
+        offs = np.zeros(len(rows) + 1, np.int64)
+        np.cumsum(lens, out=offs[1:])
+        arena = np.frombuffer(b"".join(bytes(r) for r in rows) + b"\0", np.uint8).copy()
+        return ByteSeqs(torch.from_numpy(arena).to(device), torch.from_numpy(offs).to(device),
+                        int(lens.max()) if len(lens) else 0, int(offs[-1]))
+
+
+def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_off: torch.Tensor | None = None,
+                   stream=None):
+    """A5/A6: NW score, edit script (forward order, bytes M/X/D/I) per pair.
+
+    Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64, ops_len[P] int32)``.
+    ``seqs`` is a :class:`ByteSeqs` or a packed :class:`DeviceSeqs` (its byte codes).
+    """
+    if isinstance(seqs, DeviceSeqs):
+        seqs = ByteSeqs.from_device_seqs(seqs)
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    dev = pairs.device
+    if ops_off is None:
+        lens = seqs.offs[1:] - seqs.offs[:-1]
+        cap = lens[pairs[:, 0].long()] + lens[pairs[:, 1].long()]
+        ops_off = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(cap, 0, out=ops_off[1:])
+    cap_total = int(ops_off[-1].item()) if P else 0
+    ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
+    score = torch.empty(P, dtype=torch.int32, device=dev)
+    ops_len = torch.empty(P, dtype=torch.int32, device=dev)
+    ctx.raise_if(_lib.lib().msa_nw_align_batch(ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total,
+                                               seqs.max_len, _ptr(pairs), P, match, mismatch, gap, _ptr(score),
+                                               _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    return score, ops, ops_off, ops_len
+
+
+def lev_autotune(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None = None, stream=None):
+    """A7: choose the schedule for batches like this one; returns the distances."""
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=pairs.device)
+    ctx.raise_if(_lib.lib().msa_lev_autotune(ctx.handle, ctypes.byref(seqs.c), _ptr(pairs), P, _ptr(out),
+                                             _stream(stream)))
+    return out

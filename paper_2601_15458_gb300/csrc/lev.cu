@@ -1,0 +1,368 @@
+// Batched Levenshtein distance: device-side schedule (A7) and the C entry
+// points msa_lev_batch / msa_lev_autotune.
+//
+// Schedule of one call, all on the device (no host round trip, so the whole
+// call can be captured in a CUDA graph):
+//   1. count pairs per first index q (the query), checking every index;
+//   2. exclusive scan -> group starts; scatter (target, pair id) by query;
+//   3. per query pick a kernel configuration from its word count
+//      W = ceil(m / 32) and its number of targets c_q: the lane kernel
+//      (one warp per query, a lane per target) when W <= 64 and c_q is large
+//      enough, otherwise the warp kernel (32 lanes per target); split the
+//      query into ceil(c_q / per_task) tasks and append them to the bucket of
+//      that configuration;
+//   4. one persistent launch per bucket; warps pull tasks from the bucket's
+//      counter and, inside a task, targets from the query's shared cursor.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "lev_kernels.cuh"
+#include "msa_internal.cuh"
+
+namespace msa {
+
+constexpr int kMaxBuckets = 64;
+
+struct Tune {
+    int lane_min_targets = 12;  // below this a query goes to the warp kernel
+    int lane_per_task = 256;    // targets per task, lane kernel
+    int warp_per_task = 4;      // targets per task, warp kernel
+    int occupancy[2][kMaxBuckets] = {};  // blocks per SM, per alphabet and bucket
+};
+
+Tune *create_tune() { return new Tune(); }
+void destroy_tune(Tune *t) { delete t; }
+
+struct Registry {
+    const LevKernelInfo *lane;
+    int nlane;
+    const LevKernelInfo *warp;
+    int nwarp;
+    int count() const { return nlane + nwarp; }
+    const LevKernelInfo &at(int b) const { return b < nlane ? lane[b] : warp[b - nlane]; }
+};
+
+static Registry registry(int alphabet) {
+    if (alphabet == MSA_DNA) return {kLevLaneDna, kLevLaneDnaCount, kLevWarpDna, kLevWarpDnaCount};
+    return {kLevLaneProt, kLevLaneProtCount, kLevWarpProt, kLevWarpProtCount};
+}
+
+struct PlanParams {
+    int nlane, nwarp;
+    int lane_words[32];
+    int warp_words[32];
+    int lane_min_targets;
+    int lane_per_task;
+    int warp_per_task;
+};
+
+__device__ __forceinline__ int pick_bucket(const PlanParams &pp, int W, int c) {
+    if (W <= pp.lane_words[pp.nlane - 1] && c >= pp.lane_min_targets) {
+        for (int b = 0; b < pp.nlane; ++b)
+            if (pp.lane_words[b] >= W) return b;
+    }
+    for (int b = 0; b < pp.nwarp; ++b)
+        if (32 * pp.warp_words[b] >= W) return pp.nlane + b;
+    return -1;
+}
+
+// A sequence index is usable when it is in range and its offsets lie inside
+// the arena in order (so no kernel can read outside the arena).
+__device__ __forceinline__ bool seq_ok(const int64_t *__restrict__ offs, int32_t n, int64_t total, int s) {
+    if (s < 0 || s >= n) return false;
+    const int64_t a = offs[s], b = offs[s + 1];
+    return a >= 0 && a <= b && b <= total;
+}
+
+__global__ void count_kernel(const int32_t *__restrict__ pairs, int64_t P, int32_t n,
+                             const int64_t *__restrict__ offs, int64_t total,
+                             int32_t *__restrict__ qcount, int32_t *err) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+        if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) {
+            record_error(err, kErrIndex, p, seq_ok(offs, n, total, q) ? t : q);
+            continue;
+        }
+        atomicAdd(qcount + q, 1);
+    }
+}
+
+// Exclusive scan of n ints by one block of 1024 threads (chunked).
+__global__ void __launch_bounds__(1024) scan_kernel(const int32_t *__restrict__ in, int32_t n,
+                                                    int32_t *__restrict__ out) {
+    __shared__ int32_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t lo = tid * chunk, hi = min((int64_t)n, lo + chunk);
+    int32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += in[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int32_t v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = tid ? part[tid - 1] : 0;
+    for (int64_t i = lo; i < hi; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (tid == 1023) out[n] = part[1023];
+}
+
+__global__ void scatter_kernel(const int32_t *__restrict__ pairs, int64_t P, int32_t n,
+                               const int64_t *__restrict__ offs, int64_t total,
+                               const int32_t *__restrict__ qstart, int32_t *__restrict__ qfill,
+                               int32_t *__restrict__ sorted_t, int32_t *__restrict__ sorted_p) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+        if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) continue;
+        const int pos = qstart[q] + atomicAdd(qfill + q, 1);
+        sorted_t[pos] = t;
+        sorted_p[pos] = (int32_t)p;
+    }
+}
+
+// pass 0: count tasks per bucket; pass 1: write them (bucket offsets by a
+// scan over <= kMaxBuckets counts done redundantly by every block).
+template <int PASS>
+__global__ void __launch_bounds__(256) task_kernel(const int64_t *__restrict__ offs, int32_t n,
+                                                   const int32_t *__restrict__ qstart, PlanParams pp,
+                                                   int32_t *__restrict__ bcount, int32_t *__restrict__ bfill,
+                                                   int32_t *__restrict__ boff, int2 *__restrict__ tasks,
+                                                   int32_t *err) {
+    __shared__ int32_t sboff[kMaxBuckets];
+    const int NB = pp.nlane + pp.nwarp;
+    if (PASS == 1) {
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int b = 0; b < NB; ++b) {
+                sboff[b] = run;
+                run += bcount[b];
+            }
+        }
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x < NB) boff[threadIdx.x] = sboff[threadIdx.x];
+    }
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = qstart[q + 1] - qstart[q];
+        if (c == 0) continue;
+        const int m = (int)(offs[q + 1] - offs[q]);
+        const int W = max(1, (m + 31) / 32);
+        const int b = pick_bucket(pp, W, c);
+        if (b < 0) {
+            if (PASS == 0) record_error(err, kErrLength, q, m);
+            continue;
+        }
+        const int per = b < pp.nlane ? pp.lane_per_task : pp.warp_per_task;
+        const int parts = (c + per - 1) / per;
+        if (PASS == 0) {
+            atomicAdd(bcount + b, parts);
+        } else {
+            const int base = sboff[b] + atomicAdd(bfill + b, parts);
+            for (int i = 0; i < parts; ++i) tasks[base + i] = make_int2((int)q, i);
+        }
+    }
+}
+
+static int grid_for(int blocks) { return blocks < 1 ? 1 : blocks; }
+
+int64_t lev_workspace(int64_t P, int32_t n) {
+    auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
+    return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 2 + r(8 * (P + n + 1)) +
+           r(4 * kMaxBuckets) * 4;
+}
+
+static PlanParams plan_params(const Registry &R, const Tune &T) {
+    PlanParams pp{};
+    pp.nlane = R.nlane;
+    pp.nwarp = R.nwarp;
+    for (int b = 0; b < R.nlane; ++b) pp.lane_words[b] = R.lane[b].words;
+    for (int b = 0; b < R.nwarp; ++b) pp.warp_words[b] = R.warp[b].words;
+    pp.lane_min_targets = T.lane_min_targets;
+    pp.lane_per_task = T.lane_per_task;
+    pp.warp_per_task = T.warp_per_task;
+    return pp;
+}
+
+static msa_status ensure_occupancy(msa_ctx *ctx, const Registry &R, int alphabet) {
+    Tune &T = *ctx->tune;
+    for (int b = 0; b < R.count(); ++b) {
+        if (T.occupancy[alphabet][b] > 0) continue;
+        const LevKernelInfo &K = R.at(b);
+        const size_t smem = K.smem_per_warp * 4;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "cudaFuncSetAttribute");
+        }
+        int blocks = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, K.fn, 128, smem);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "occupancy query");
+        T.occupancy[alphabet][b] = blocks > 0 ? blocks : 1;
+    }
+    return MSA_OK;
+}
+
+// Launches the whole schedule.  `max_len` (host) bounds the buckets launched.
+static msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
+                          int32_t *d_out, cudaStream_t st) {
+    const Registry R = registry(s->alphabet);
+    msa_status rc = ensure_occupancy(ctx, R, s->alphabet);
+    if (rc) return rc;
+    const Tune &T = *ctx->tune;
+    const int32_t n = s->n_seqs;
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    int32_t *qcount = ar.take<int32_t>(n);
+    int32_t *qfill = ar.take<int32_t>(n);
+    int32_t *qcursor = ar.take<int32_t>(n);
+    int32_t *qstart = ar.take<int32_t>(int64_t(n) + 1);
+    int32_t *sorted_t = ar.take<int32_t>(P);
+    int32_t *sorted_p = ar.take<int32_t>(P);
+    int2 *tasks = ar.take<int2>(P + n + 1);
+    int32_t *bcount = ar.take<int32_t>(kMaxBuckets);
+    int32_t *bfill = ar.take<int32_t>(kMaxBuckets);
+    int32_t *boff = ar.take<int32_t>(kMaxBuckets);
+    int32_t *bcounter = ar.take<int32_t>(kMaxBuckets);
+    if (!bcounter)
+        return set_error(ctx, MSA_ENOMEM, "msa_lev_batch: needs %lld workspace bytes, context has %lld",
+                         (long long)lev_workspace(P, n), (long long)ctx->ws_bytes);
+    // the three per-query arrays are contiguous: one memset
+    cudaError_t e = cudaMemsetAsync(qcount, 0, (char *)qstart - (char *)qcount, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bcount, 0, (char *)bcounter - (char *)bcount + 4 * kMaxBuckets, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_batch memset");
+
+    const int gP = grid_for((int)std::min<int64_t>((P + 255) / 256, ctx->sm_count * 8));
+    const int gN = grid_for((int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8));
+    ctx->launches += 5;
+    count_kernel<<<gP, 256, 0, st>>>(pairs, P, n, s->offs, s->total, qcount, ctx->dev_err);
+    scan_kernel<<<1, 1024, 0, st>>>(qcount, n, qstart);
+    scatter_kernel<<<gP, 256, 0, st>>>(pairs, P, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
+    const PlanParams pp = plan_params(R, T);
+    task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
+    task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
+
+    LevArgs a{};
+    a.planes = s->planes;
+    a.codes = s->codes;
+    a.offs = s->offs;
+    a.sorted_t = sorted_t;
+    a.sorted_p = sorted_p;
+    a.qstart = qstart;
+    a.qcursor = qcursor;
+    a.tasks = tasks;
+    a.boff = boff;
+    a.bcount = bcount;
+    a.bcounter = bcounter;
+    a.d_out = d_out;
+    a.err = ctx->dev_err;
+    // buckets that no sequence of this set can reach are not launched
+    const int Wmax = std::max(1, (s->max_len + 31) / 32);
+    int lane_last = R.nlane - 1;
+    for (int b = 0; b < R.nlane; ++b)
+        if (R.lane[b].words >= Wmax) {
+            lane_last = b;
+            break;
+        }
+    int warp_last = R.nwarp - 1;
+    for (int b = 0; b < R.nwarp; ++b)
+        if (32 * R.warp[b].words >= Wmax) {
+            warp_last = b;
+            break;
+        }
+    ProfScope prof(ctx, st);
+    for (int b = 0; b < R.count(); ++b) {
+        const bool is_lane = b < R.nlane;
+        if (is_lane && b > lane_last) continue;
+        if (!is_lane && b - R.nlane > warp_last) continue;
+        a.bucket = b;
+        const int grid = grid_for(ctx->sm_count * T.occupancy[s->alphabet][b]);
+        R.at(b).launch(a, grid, st);
+        ++ctx->launches;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "msa_lev_batch launch");
+}
+
+static msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
+                               const void *out, const char *who) {
+    if (!ctx || !s) return MSA_EINVAL;
+    if (P < 0 || P >= (int64_t(1) << 31)) return set_error(ctx, MSA_EINVAL, "%s: P=%lld out of range", who, (long long)P);
+    if (s->alphabet != MSA_DNA && s->alphabet != MSA_PROTEIN)
+        return set_error(ctx, MSA_EINVAL, "%s: unknown alphabet %d", who, s->alphabet);
+    if (P > 0 && (!pairs || !out || !s->offs || !s->codes || !s->planes))
+        return set_error(ctx, MSA_EINVAL, "%s: null pointer", who);
+    if (s->n_seqs < 0 || s->max_len < 0) return set_error(ctx, MSA_EINVAL, "%s: negative size", who);
+    if (s->max_len > 32 * 32 * 16)
+        return set_error(ctx, MSA_EUNSUPPORTED, "%s: max_len %d above the 16384 this build supports", who, s->max_len);
+    return MSA_OK;
+}
+
+}  // namespace msa
+
+using namespace msa;
+
+extern "C" {
+
+int64_t msa_lev_workspace_bytes(int64_t P, int32_t n_seqs) { return lev_workspace(P, n_seqs); }
+
+msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                         void *stream) {
+    msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_batch");
+    if (rc || P == 0) return rc;
+    if (s->n_seqs == 0) return set_error(ctx, MSA_EINVAL, "msa_lev_batch: pairs given for an empty set");
+    return lev_run(ctx, s, pairs, P, d_out, (cudaStream_t)stream);
+}
+
+msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                            void *stream) {
+    msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_autotune");
+    if (rc || P == 0) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *scratch = d_out;
+    Tune &T = *ctx->tune;
+    const Tune keep = T;
+    struct Cand {
+        int lane_min, lane_per, warp_per;
+    };
+    const Cand cands[] = {{12, 256, 4}, {4, 256, 4}, {32, 256, 4}, {12, 128, 4}, {12, 512, 4},
+                          {12, 256, 1}, {12, 256, 16}, {1 << 30, 256, 4}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick = {keep.lane_min_targets, keep.lane_per_task, keep.warp_per_task};
+    for (const Cand &c : cands) {
+        T.lane_min_targets = c.lane_min;
+        T.lane_per_task = c.lane_per;
+        T.warp_per_task = c.warp_per;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3 && rc == MSA_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = lev_run(ctx, s, pairs, P, scratch, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        if (rc) break;
+        if (ms_best < best) {
+            best = ms_best;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    T.lane_min_targets = pick.lane_min;
+    T.lane_per_task = pick.lane_per;
+    T.warp_per_task = pick.warp_per;
+    if (rc) return rc;
+    return msa_ctx_check(ctx, stream);
+}
+
+}  // extern "C"

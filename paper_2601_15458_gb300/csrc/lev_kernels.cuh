@@ -1,0 +1,325 @@
+// Bit-vector Levenshtein kernels (A2 match masks, A3 distance).
+//
+// Column j of the edit-distance matrix D of a (rows) against b (columns) is
+// held as vertical deltas D[i][j] - D[i-1][j] in {-1, 0, +1}, one bit per
+// row in two masks Pv (+1) and Mv (-1) (Myers 1999, "A fast bit-vector
+// algorithm for approximate string matching based on dynamic programming";
+// global-distance form after Hyyro 2001).  With Eq the rows whose symbol
+// equals b_j, the horizontal deltas of column j follow from
+//     Xh = (((Eq & Pv) + Pv) ^ Pv) | Eq        (one carry chain over all rows)
+//     Ph = Mv | ~(Xh | Pv),  Mh = Pv & Xh
+// and the next vertical deltas from the horizontal ones shifted down a row,
+// with row 0 contributing +1 (D[0][j] = j):
+//     Pv' = Mh<< | ~(Xv | Ph<<),  Mv' = Ph<< & Xv,  Xv = Eq | Mv.
+// The carry of the addition out of row i equals Mh[i], so a vector longer
+// than one 32-bit word is handled by feeding the top bit of the previous
+// word's Mh into the next word's addition and both top bits into its shifts.
+// After the last column, D[m][n] = n + popc(Pv) - popc(Mv) over rows 1..m.
+//
+// Rows beyond m (padding up to the kernel's word capacity) never influence
+// rows <= m: information only moves to higher rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "msa_internal.cuh"
+
+namespace msa {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct LevArgs {
+    const uint32_t *planes;   // bit planes of the arena
+    const uint8_t *codes;     // byte codes of the arena
+    const int64_t *offs;      // [n_seqs + 1]
+    const int32_t *sorted_t;  // targets, grouped by query
+    const int32_t *sorted_p;  // original pair id of each grouped entry
+    const int32_t *qstart;    // [n_seqs + 1] group starts
+    int32_t *qcursor;         // [n_seqs] next entry to hand out, per query
+    const int2 *tasks;        // all tasks, bucket-major
+    const int32_t *boff;      // [NB] first task of each bucket
+    const int32_t *bcount;    // [NB] tasks per bucket
+    int32_t *bcounter;        // [NB] tasks handed out per bucket
+    int32_t *d_out;
+    int32_t *err;
+    int32_t bucket;
+};
+
+// 32 match bits of the query for rows 32k+1 .. 32k+32 and every symbol c.
+// planes: B bit planes per 32-position arena word.  Bits for rows > m are 0.
+template <int B>
+__device__ __forceinline__ void query_planes(const uint32_t *__restrict__ planes, int64_t qpos, int m,
+                                             int k, uint32_t (&pl)[B], uint32_t &mask) {
+    const int rem = m - 32 * k;
+    if (rem <= 0) {
+        mask = 0u;
+#pragma unroll
+        for (int p = 0; p < B; ++p) pl[p] = 0u;
+        return;
+    }
+    mask = rem >= 32 ? kFull : ((1u << rem) - 1u);
+    const int64_t bit = qpos + 32 * (int64_t)k;
+    const int64_t wi = bit >> 5;
+    const int r = (int)(bit & 31);
+#pragma unroll
+    for (int p = 0; p < B; ++p) {
+        uint32_t lo = __ldg(planes + wi * B + p);
+        uint32_t hi = __ldg(planes + (wi + 1) * B + p);
+        pl[p] = __funnelshift_r(lo, hi, r);
+    }
+}
+
+template <int B, int SIGMA>
+__device__ __forceinline__ uint32_t match_mask(const uint32_t (&pl)[B], uint32_t mask, int c) {
+    uint32_t eq = mask;
+#pragma unroll
+    for (int p = 0; p < B; ++p) eq &= ((c >> p) & 1) ? pl[p] : ~pl[p];
+    return eq;
+}
+
+// One 32-row word of one column.  ph_in/mh_in: top bits of the previous
+// word's Ph/Mh (row 0: ph_in = 1, mh_in = 0); they are replaced by this
+// word's top bits on return.
+__device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv, uint32_t &ph_in,
+                                        uint32_t &mh_in) {
+    const uint32_t sum = (eq & pv) + pv + mh_in;
+    const uint32_t xh = (sum ^ pv) | eq;
+    const uint32_t ph = mv | ~(xh | pv);
+    const uint32_t mh = pv & xh;
+    const uint32_t phs = (ph << 1) | ph_in;
+    const uint32_t mhs = (mh << 1) | mh_in;
+    ph_in = ph >> 31;
+    mh_in = mh >> 31;
+    const uint32_t xv = eq | mv;
+    pv = mhs | ~(xv | phs);
+    mv = phs & xv;
+}
+
+__device__ __forceinline__ int next_task(int32_t *counter, int lane) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1);
+    return __shfl_sync(kFull, t, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Lane kernel: one warp per query, each lane streams its own targets.
+// Match masks of the query live in shared memory, layout [k][c] so lanes that
+// read different symbols hit different banks.  Pv/Mv: WC words in registers.
+// ---------------------------------------------------------------------------
+template <int WC, int B, int SIGMA>
+__global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *sPeq = smem + (threadIdx.x >> 5) * (WC * SIGMA);
+    const int ntasks = a.bcount[a.bucket];
+    const int2 *tasks = a.tasks + a.boff[a.bucket];
+    int32_t *counter = a.bcounter + a.bucket;
+
+    for (int task = next_task(counter, lane); task < ntasks; task = next_task(counter, lane)) {
+        const int q = tasks[task].x;
+        const int64_t qpos = a.offs[q];
+        const int m = (int)(a.offs[q + 1] - qpos);
+        __syncwarp();
+        for (int k = lane; k < WC; k += 32) {
+            uint32_t pl[B], mask;
+            query_planes<B>(a.planes, qpos, m, k, pl, mask);
+#pragma unroll
+            for (int c = 0; c < SIGMA; ++c) sPeq[k * SIGMA + c] = match_mask<B, SIGMA>(pl, mask, c);
+        }
+        __syncwarp();
+        const int cbeg = a.qstart[q];
+        const int cnt = a.qstart[q + 1] - cbeg;
+
+        uint32_t Pv[WC], Mv[WC];
+#pragma unroll
+        for (int k = 0; k < WC; ++k) {
+            Pv[k] = kFull;
+            Mv[k] = 0u;
+        }
+        int n = 0, j = 0, pid = -1;
+        const uint8_t *tc = nullptr;
+        while (true) {
+            if (j == n) {
+                if (pid >= 0) {
+                    int d = n;
+#pragma unroll
+                    for (int k = 0; k < WC; ++k) {
+                        const int rem = m - 32 * k;
+                        const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                        d += __popc(Pv[k] & mk) - __popc(Mv[k] & mk);
+                    }
+                    a.d_out[pid] = d;
+                }
+                const int idx = atomicAdd(a.qcursor + q, 1);
+                if (idx >= cnt) break;
+                const int t = a.sorted_t[cbeg + idx];
+                pid = a.sorted_p[cbeg + idx];
+                const int64_t tp = a.offs[t];
+                n = (int)(a.offs[t + 1] - tp);
+                tc = a.codes + tp;
+                j = 0;
+#pragma unroll
+                for (int k = 0; k < WC; ++k) {
+                    Pv[k] = kFull;
+                    Mv[k] = 0u;
+                }
+                continue;
+            }
+            const uint32_t *row = sPeq + __ldg(tc + j);
+            uint32_t ph_in = 1u, mh_in = 0u;
+#pragma unroll
+            for (int k = 0; k < WC; ++k) bv_word(row[k * SIGMA], Pv[k], Mv[k], ph_in, mh_in);
+            ++j;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp kernel: one warp per (query, target); lane g holds words
+// g*WPL .. g*WPL+WPL-1 and works on column s - g at step s, receiving the
+// top bits of lane g-1's Ph/Mh for that column through __shfl_up_sync.
+// Targets of the same query follow back to back: lane 0 pulls the next one
+// into a small ring in shared memory and every lane reaches it g steps later.
+// The distance is summed down the pipeline and written by lane 31.
+// Match masks: layout [w][c][lane], conflict-free for any mix of symbols.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 32;
+
+template <int WPL, int B, int SIGMA>
+__global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    uint32_t *sPeq = smem + wid * (WPL * SIGMA * 32 + 3 * kRing + 2);
+    int32_t *ring_t = reinterpret_cast<int32_t *>(sPeq + WPL * SIGMA * 32);
+    int32_t *ring_p = ring_t + kRing;
+    int32_t *ring_n = ring_p + kRing;
+    volatile int32_t *end_step = ring_n + kRing;
+    const int ntasks = a.bcount[a.bucket];
+    const int2 *tasks = a.tasks + a.boff[a.bucket];
+    int32_t *counter = a.bcounter + a.bucket;
+
+    for (int task = next_task(counter, lane); task < ntasks; task = next_task(counter, lane)) {
+        const int q = tasks[task].x;
+        const int64_t qpos = a.offs[q];
+        const int m = (int)(a.offs[q + 1] - qpos);
+        const int cbeg = a.qstart[q];
+        const int cnt = a.qstart[q + 1] - cbeg;
+        __syncwarp();
+        uint32_t maskw[WPL];
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) {
+            uint32_t pl[B], mask;
+            query_planes<B>(a.planes, qpos, m, lane * WPL + w, pl, mask);
+            maskw[w] = mask;
+#pragma unroll
+            for (int c = 0; c < SIGMA; ++c) sPeq[(w * SIGMA + c) * 32 + lane] = match_mask<B, SIGMA>(pl, mask, c);
+        }
+        if (lane == 0) *end_step = 0x3fffffff;
+        __syncwarp();
+
+        uint32_t Pv[WPL], Mv[WPL];
+        int seq = -1;          // ring slot of the current target of this lane
+        int n = 0, j = 0, pid = -1;
+        const uint8_t *tc = nullptr;
+        bool started = false, finished = false;
+        int msg = 0;
+        for (int s = 0;; ++s) {
+            // lane 0 feeds the ring whenever it needs a target
+            if (lane == 0 && !finished && j == n) {
+                int nn = 0, t = -1, p = -1;
+                while (true) {
+                    const int idx = atomicAdd(a.qcursor + q, 1);
+                    if (idx >= cnt) break;
+                    t = a.sorted_t[cbeg + idx];
+                    p = a.sorted_p[cbeg + idx];
+                    nn = (int)(a.offs[t + 1] - a.offs[t]);
+                    if (nn > 0) break;
+                    a.d_out[p] = m;   // empty target: f = m
+                    t = -1;
+                }
+                const int slot = (seq + 1) & (kRing - 1);
+                ring_t[slot] = t;
+                ring_p[slot] = p;
+                ring_n[slot] = nn;
+                if (t < 0) *end_step = s;
+            }
+            __syncwarp();
+            if (s >= *end_step + 32) break;
+            const int msg_in = __shfl_up_sync(kFull, msg, 1);
+            msg = 0;
+            if (!finished && s >= lane) {
+                if (!started || j == n) {
+                    seq = (seq + 1) & (kRing - 1);
+                    const int t = ring_t[seq];
+                    if (t < 0) {
+                        finished = true;
+                    } else {
+                        pid = ring_p[seq];
+                        n = ring_n[seq];
+                        const int64_t tp = a.offs[t];
+                        tc = a.codes + tp;
+                        j = 0;
+                        started = true;
+#pragma unroll
+                        for (int w = 0; w < WPL; ++w) {
+                            Pv[w] = kFull;
+                            Mv[w] = 0u;
+                        }
+                    }
+                }
+                if (!finished) {
+                    const int c = __ldg(tc + j);
+                    uint32_t ph_in = lane == 0 ? 1u : (uint32_t)(msg_in & 1);
+                    uint32_t mh_in = lane == 0 ? 0u : (uint32_t)((msg_in >> 1) & 1);
+                    const uint32_t *col = sPeq + c * 32 + lane;
+#pragma unroll
+                    for (int w = 0; w < WPL; ++w) bv_word(col[w * SIGMA * 32], Pv[w], Mv[w], ph_in, mh_in);
+                    msg = (int)(ph_in | (mh_in << 1));
+                    ++j;
+                    if (j == n) {
+                        int part = lane == 0 ? 0 : (msg_in >> 2);
+#pragma unroll
+                        for (int w = 0; w < WPL; ++w) part += __popc(Pv[w] & maskw[w]) - __popc(Mv[w] & maskw[w]);
+                        msg |= part << 2;
+                        if (lane == 31) a.d_out[pid] = n + part;
+                    }
+                }
+            }
+        }
+    }
+}
+
+using LevLauncher = void (*)(const LevArgs &, int grid, cudaStream_t);
+
+struct LevKernelInfo {
+    int kind;       // 0 = lane, 1 = warp
+    int words;      // WC (lane) or WPL (warp)
+    int alphabet;
+    size_t smem_per_warp;
+    LevLauncher launch;
+    const void *fn;
+};
+
+template <int WC, int B, int SIGMA>
+void launch_lane(const LevArgs &a, int grid, cudaStream_t st) {
+    lev_lane_kernel<WC, B, SIGMA><<<grid, 128, 4 * WC * SIGMA * sizeof(uint32_t), st>>>(a);
+}
+
+template <int WPL, int B, int SIGMA>
+void launch_warp(const LevArgs &a, int grid, cudaStream_t st) {
+    lev_warp_kernel<WPL, B, SIGMA><<<grid, 128, 4 * (WPL * SIGMA * 32 + 3 * kRing + 2) * sizeof(uint32_t), st>>>(a);
+}
+
+// Registries defined in the instantiation units.
+extern const LevKernelInfo kLevLaneDna[];
+extern const int kLevLaneDnaCount;
+extern const LevKernelInfo kLevLaneProt[];
+extern const int kLevLaneProtCount;
+extern const LevKernelInfo kLevWarpDna[];
+extern const int kLevWarpDnaCount;
+extern const LevKernelInfo kLevWarpProt[];
+extern const int kLevWarpProtCount;
+
+}  // namespace msa

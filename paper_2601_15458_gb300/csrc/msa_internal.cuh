@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "msa.h"
+
+namespace msa {
+
+constexpr int kDeviceErrWords = 4;  // [code, detail0, detail1, detail2]
+
+// Device error codes recorded by kernels (the first one wins).
+constexpr int kErrIndex = 1;     // pair index outside [0, n_seqs)
+constexpr int kErrSymbol = 2;    // residue outside the alphabet
+constexpr int kErrLength = 3;    // sequence longer than max_len / bad offsets
+constexpr int kErrTimeout = 4;   // a bounded wait ran out
+constexpr int kErrCapacity = 5;  // a device-side capacity bound was exceeded
+
+struct Tune;  // autotune table (lev_plan.cu)
+
+}  // namespace msa
+
+struct msa_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    char *ws = nullptr;          // workspace base
+    int64_t ws_bytes = 0;
+    int32_t *dev_err = nullptr;  // kDeviceErrWords ints
+    std::string last_error;
+    msa::Tune *tune = nullptr;
+    // launch accounting and optional event timing of the DP kernels
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    double prof_ms = 0.0;
+};
+
+namespace msa {
+
+msa_status set_error(msa_ctx *ctx, msa_status code, const char *fmt, ...);
+msa_status cuda_check(msa_ctx *ctx, cudaError_t e, const char *what);
+
+// Records a device error (first one wins).
+__device__ __forceinline__ void record_error(int32_t *err, int code, long long d0, long long d1) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = (int32_t)d0;
+        err[2] = (int32_t)(d0 >> 32);
+        err[3] = (int32_t)d1;
+    }
+}
+
+// Bump allocator over the context workspace for one call.
+struct Arena {
+    char *base;
+    int64_t cap;
+    int64_t used = 0;
+    template <class T>
+    T *take(int64_t count) {
+        int64_t bytes = (count * (int64_t)sizeof(T) + 255) & ~int64_t(255);
+        if (used + bytes > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// Brackets the DP kernels of one call with events when profiling is on.
+struct ProfScope {
+    msa_ctx *ctx;
+    cudaStream_t st;
+    cudaEvent_t e1 = nullptr;
+    ProfScope(msa_ctx *c, cudaStream_t s) : ctx(c), st(s) {
+        if (!ctx->prof) return;
+        cudaEvent_t e0;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        ctx->prof_events.push_back({e0, e1});
+    }
+    ~ProfScope() {
+        if (e1) cudaEventRecord(e1, st);
+    }
+};
+
+inline int bits_of(int alphabet) { return alphabet == MSA_DNA ? 2 : 5; }
+inline int sigma_of(int alphabet) { return alphabet == MSA_DNA ? 4 : 20; }
+
+}  // namespace msa

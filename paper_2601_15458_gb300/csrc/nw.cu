@@ -1,0 +1,262 @@
+// Needleman-Wunsch with traceback (A5 fill, A6 device traceback) and the
+// C entry point msa_nw_align_batch.
+//
+// Minimum-cost global alignment with a flat cost model (match, mismatch,
+// gap): D[i][0] = i*gap, D[0][j] = j*gap,
+//   D[i][j] = min(D[i-1][j-1] + cost(a_i, b_j), D[i-1][j] + gap, D[i][j-1] + gap).
+// Each cell also records which move attains D[i][j], preferring diagonal,
+// then up (a_i against a gap), then left (b_j against a gap); the traceback
+// from (m, n) follows those codes, so it returns the same alignment as the
+// plain rule "take the first of diagonal, up, left that attains D".
+//
+// One warp per pair (persistent, pairs pulled from an atomic counter).  Rows
+// are cut into tiles of 32 lanes x 16 rows; lane l holds rows
+// tile*512 + 16l + 1 .. +16 and works on column j at step j + l, taking the
+// value of the row above its first row from lane l-1 by __shfl_up_sync.  The
+// bottom row of a tile is kept in the warp's slab for the next tile.  The 16
+// two-bit codes of a lane's rows in one column form one 32-bit word, stored
+// in the warp's slab at [tile][lane][column]; lane 0 then walks back from
+// (m, n) through those words and emits the edit script.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "msa_internal.cuh"
+
+namespace msa {
+
+constexpr int kNwR = 16;                 // rows per lane
+constexpr int kNwTile = 32 * kNwR;       // rows per tile
+constexpr int kNwWarps = 4;              // warps per block
+
+struct NwArgs {
+    const uint8_t *codes;
+    const int64_t *offs;
+    int32_t n_seqs;
+    int64_t total;
+    const int32_t *pairs;
+    int64_t P;
+    int32_t match, mismatch, gap;
+    int32_t *score;
+    uint8_t *ops;
+    const int64_t *ops_off;
+    int32_t *ops_len;
+    char *slabs;            // per-warp scratch
+    int64_t slab_bytes;
+    int32_t max_len;        // slab capacity in rows / columns
+    int32_t *counter;
+    int32_t *err;
+};
+
+__device__ __forceinline__ int64_t nw_tb_words(int max_len) {
+    return (int64_t)((max_len + kNwTile - 1) / kNwTile) * 32 * max_len;
+}
+
+__global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kNwWarps + (threadIdx.x >> 5);
+    char *slab = a.slabs + (int64_t)gw * a.slab_bytes;
+    int32_t *brow = reinterpret_cast<int32_t *>(slab);
+    uint32_t *tb = reinterpret_cast<uint32_t *>(slab + (((int64_t)a.max_len + 1) * 4 + 255) / 256 * 256);
+    const int gap = a.gap, match = a.match, mismatch = a.mismatch;
+
+    while (true) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(a.counter, 1);
+        p = __shfl_sync(FULL, p, 0);
+        if (p >= a.P) break;
+        const int x = a.pairs[2 * p], y = a.pairs[2 * p + 1];
+        bool ok = x >= 0 && x < a.n_seqs && y >= 0 && y < a.n_seqs;
+        int64_t xa = 0, xb = 0, ya = 0, yb = 0;
+        if (ok) {
+            xa = a.offs[x], xb = a.offs[x + 1], ya = a.offs[y], yb = a.offs[y + 1];
+            ok = xa >= 0 && xa <= xb && xb <= a.total && ya >= 0 && ya <= yb && yb <= a.total;
+        }
+        if (!ok) {
+            if (lane == 0) record_error(a.err, kErrIndex, p, x);
+            continue;
+        }
+        const int m = (int)(xb - xa), n = (int)(yb - ya);
+        const uint8_t *A = a.codes + xa;
+        const uint8_t *Bq = a.codes + ya;
+        const int64_t o0 = a.ops_off[p];
+        if (a.ops_off[p + 1] - o0 < (int64_t)m + n) {
+            if (lane == 0) record_error(a.err, kErrCapacity, p, m + n);
+            continue;
+        }
+        if (m > a.max_len || n > a.max_len) {
+            if (lane == 0) record_error(a.err, kErrLength, p, max(m, n));
+            continue;
+        }
+        uint8_t *ops = a.ops + o0;
+        if (m == 0 || n == 0) {
+            for (int k = lane; k < m + n; k += 32) ops[k] = m == 0 ? 'I' : 'D';
+            if (lane == 0) {
+                a.score[p] = (m + n) * gap;
+                a.ops_len[p] = m + n;
+            }
+            continue;
+        }
+
+        // ---- fill -------------------------------------------------------
+        for (int j = lane; j <= n; j += 32) brow[j] = j * gap;
+        __syncwarp();
+        const int ntiles = (m + kNwTile - 1) / kNwTile;
+        int32_t H[kNwR];
+        for (int t = 0; t < ntiles; ++t) {
+            const int i_first = t * kNwTile + lane * kNwR + 1;     // first row of this lane
+            int ac[kNwR];
+#pragma unroll
+            for (int r = 0; r < kNwR; ++r) {
+                const int i = i_first + r;
+                ac[r] = i <= m ? (int)A[i - 1] : -1;
+                H[r] = i * gap;                                      // column 0
+            }
+            int prev_top = (i_first - 1) * gap;                      // D[i_first-1][0]
+            int last = H[kNwR - 1];
+            uint32_t *tbl = tb + ((int64_t)t * 32 + lane) * n;
+            for (int s = 1; s <= n + 31; ++s) {
+                const int up_in = __shfl_up_sync(FULL, last, 1);
+                const int j = s - lane;
+                if (j >= 1 && j <= n) {
+                    const int top = lane == 0 ? brow[j] : up_in;
+                    const int bj = Bq[j - 1];
+                    int diag = prev_top, up = top;
+                    uint32_t code = 0;
+#pragma unroll
+                    for (int r = 0; r < kNwR; ++r) {
+                        const int dg = diag + (ac[r] == bj ? match : mismatch);
+                        const int u = up + gap;
+                        const int lf = H[r] + gap;
+                        const int d = min(dg, min(u, lf));
+                        const uint32_t c = d == dg ? 0u : (d == u ? 1u : 2u);
+                        code |= c << (2 * r);
+                        diag = H[r];
+                        H[r] = d;
+                        up = d;
+                    }
+                    prev_top = top;
+                    last = H[kNwR - 1];
+                    tbl[j - 1] = code;
+                    if (lane == 31) brow[j] = last;
+                }
+            }
+            __syncwarp();
+        }
+        // D[m][n]: lane holding row m, after the last column
+        {
+            const int lm = ((m - 1) % kNwTile) / kNwR, rm = (m - 1) % kNwR;
+            if (lane == lm) {
+                int v = 0;
+#pragma unroll
+                for (int r = 0; r < kNwR; ++r)
+                    if (r == rm) v = H[r];
+                a.score[p] = v;
+            }
+        }
+        __syncwarp();
+
+        // ---- traceback (lane 0), script written backwards from o0 + m + n - 1
+        int L = 0;
+        if (lane == 0) {
+            int i = m, j = n;
+            int64_t w = (int64_t)m + n - 1;
+            while (i > 0 && j > 0) {
+                const int t = (i - 1) / kNwTile, l = ((i - 1) % kNwTile) / kNwR, r = (i - 1) % kNwR;
+                const uint32_t c = (tb[((int64_t)t * 32 + l) * n + (j - 1)] >> (2 * r)) & 3u;
+                if (c == 0) {
+                    ops[w--] = A[i - 1] == Bq[j - 1] ? 'M' : 'X';
+                    --i;
+                    --j;
+                } else if (c == 1) {
+                    ops[w--] = 'D';
+                    --i;
+                } else {
+                    ops[w--] = 'I';
+                    --j;
+                }
+            }
+            while (i > 0) {
+                ops[w--] = 'D';
+                --i;
+            }
+            while (j > 0) {
+                ops[w--] = 'I';
+                --j;
+            }
+            L = (int)((int64_t)m + n - 1 - w);
+            a.ops_len[p] = L;
+        }
+        L = __shfl_sync(FULL, L, 0);
+        __syncwarp();
+        // move the script to the front (forward order), 32 lanes, in chunks
+        // that never overlap their own source
+        const int shift = m + n - L;
+        if (shift > 0) {
+            for (int base = 0; base < L; base += 32) {
+                const int k = base + lane;
+                uint8_t v = 0;
+                if (k < L) v = ops[shift + k];
+                __syncwarp();
+                if (k < L) ops[k] = v;
+                __syncwarp();
+            }
+        }
+    }
+}
+
+int64_t nw_slab_bytes(int max_len) {
+    const int64_t brow = (((int64_t)max_len + 1) * 4 + 255) / 256 * 256;
+    const int64_t tiles = (max_len + kNwTile - 1) / kNwTile;
+    const int64_t tbw = tiles * 32 * (int64_t)std::max(max_len, 1) * 4;
+    return brow + (tbw + 255) / 256 * 256;
+}
+
+}  // namespace msa
+
+using namespace msa;
+
+extern "C" {
+
+int64_t msa_nw_workspace_bytes(int32_t max_len, int32_t warps) {
+    return 256 + (int64_t)warps * nw_slab_bytes(max_len);
+}
+
+msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                              int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t match,
+                              int32_t mismatch, int32_t gap, int32_t *score_out, uint8_t *ops_out,
+                              const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
+    if (!ctx) return MSA_EINVAL;
+    if (P < 0 || P >= (int64_t(1) << 31) || n_seqs < 0 || max_len < 0 || total < 0)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: negative or oversized count");
+    if (P == 0) return MSA_OK;
+    if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_kernel, kNwWarps * 32, 0);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "nw occupancy");
+        if (occ < 1) occ = 1;
+    }
+    const int64_t slab = nw_slab_bytes(max_len);
+    const int64_t avail = ctx->ws_bytes - 256;
+    int64_t warps = std::min<int64_t>((int64_t)ctx->sm_count * occ * kNwWarps, avail / slab);
+    warps = std::min<int64_t>(warps, ((P + kNwWarps - 1) / kNwWarps) * kNwWarps);
+    warps = warps / kNwWarps * kNwWarps;
+    if (warps < kNwWarps)
+        return set_error(ctx, MSA_ENOMEM, "msa_nw_align_batch: max_len %d needs %lld workspace bytes per warp group",
+                         max_len, (long long)(slab * kNwWarps + 256));
+    int32_t *counter = reinterpret_cast<int32_t *>(ctx->ws);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
+    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, gap, score_out, ops_out, ops_off,
+             ops_len_out, ctx->ws + 256, slab, max_len, counter, ctx->dev_err};
+    ProfScope prof(ctx, st);
+    nw_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a);
+    ++ctx->launches;
+    return cuda_check(ctx, cudaGetLastError(), "nw launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""Parity of the bit-vector Levenshtein path (A1-A3, A7) with the oracle.
+
+Integer work: every distance must equal the oracle's exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_15458_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_15458_gb300 import build
+    build.build()
+    c = api.Context(0, workspace_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _run(ctx, ds, pairs):
+    seqs = api.upload_and_pack(ctx, ds)
+    out = api.lev_batch(ctx, seqs, pairs)
+    ctx.check()
+    return out.cpu().numpy()
+
+
+def test_small_dna_all_pairs(ctx):
+    ds = synth.small_dna(seed=1)
+    pairs = synth.all_pairs(ds.n)
+    assert len(pairs) == 2016
+    got = _run(ctx, ds, pairs)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_textbook_protein_alphabet(ctx):
+    ds = synth.SeqSet.from_list([b"KITTEN", b"SITTING", b"", b"GAMMA"], "protein")
+    pairs = np.array([[0, 1], [1, 0], [2, 1], [0, 2], [2, 2], [3, 0]], np.int32)
+    got = _run(ctx, ds, pairs)
+    np.testing.assert_array_equal(got, [3, 3, 7, 6, 0, oracle.lev(b"GAMMA", b"KITTEN")])
+
+
+EDGE = [1, 31, 32, 33, 63, 64, 65, 1023, 1024, 1025, 2047, 2048, 2049, 10000]
+
+
+@pytest.mark.parametrize("alphabet", ["dna", "protein"])
+def test_edge_lengths_both_kernels(ctx, alphabet):
+    rng = np.random.default_rng(7)
+    letters = np.frombuffer(synth.DNA if alphabet == "dna" else synth.PROTEIN, np.uint8)
+    seqs = [letters[rng.integers(0, len(letters), L)].tobytes() for L in EDGE]
+    # mutated partners and a few random extra targets
+    partners = []
+    for s in seqs:
+        a = np.frombuffer(s, np.uint8).copy()
+        k = max(1, len(a) // 10)
+        a[rng.integers(0, len(a), k)] = letters[rng.integers(0, len(letters), k)]
+        partners.append(a[: max(0, len(a) - int(rng.integers(0, 5)))].tobytes())
+    extra = [letters[rng.integers(0, len(letters), L)].tobytes() for L in (0, 5, 700, 3000)]
+    allseq = seqs + partners + extra
+    ds = synth.SeqSet.from_list(allseq, alphabet)
+    n = len(seqs)
+    pairs = [[i, n + i] for i in range(n)]                      # one target per query: warp kernel
+    for i in range(n):                                          # many targets per query: lane kernel
+        pairs += [[i, j] for j in range(len(allseq))]
+    pairs = np.array(pairs, np.int32)
+    got = _run(ctx, ds, pairs)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_random_pairs_schedule_independent(ctx):
+    ds = synth.tree_dna(seed=9, n=120, root_len=400)
+    pairs = synth.random_pairs(5, ds.n, 3000)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    seqs = api.upload_and_pack(ctx, ds)
+    got = api.lev_autotune(ctx, seqs, pairs)
+    ctx.check()
+    np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    np.testing.assert_array_equal(api.lev_batch(ctx, seqs, pairs).cpu().numpy(), ref)
+
+
+def test_protein_families_to_centers_sample(ctx):
+    members, roots = synth.protein_families(seed=3, n_fam=6, per_fam=40)
+    allseq = synth.SeqSet.from_list(members.seqs() + roots.seqs(), "protein")
+    nm = members.n
+    pairs = np.array([[nm + c, x] for c in range(roots.n) for x in range(nm)], np.int32)
+    got = _run(ctx, allseq, pairs)
+    ref = oracle.lev_pairs(allseq.arena, allseq.offs, pairs)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_bad_index_reports_edata(ctx):
+    ds = synth.small_dna(seed=1, n=4)
+    seqs = api.upload_and_pack(ctx, ds)
+    api.lev_batch(ctx, seqs, np.array([[0, 1], [0, 9]], np.int32))
+    with pytest.raises(api.MsaError) as e:
+        ctx.check()
+    assert e.value.code == 6
+    ctx.check()    # cleared
+
+
+def test_bad_symbol_reports_edata(ctx):
+    ds = synth.SeqSet.from_list([b"ACGT", b"ACNT"], "dna")
+    api.upload_and_pack(ctx, ds)
+    with pytest.raises(api.MsaError, match="outside the alphabet"):
+        ctx.check()
+
+
+def test_tree_dna_full_size_sampled(ctx):
+    """The 2,000-sequence all-pairs workload, checked on a seeded sample."""
+    ds = synth.tree_dna(seed=2)
+    pairs = synth.all_pairs_balanced(ds.n)
+    assert len(pairs) == ds.n * (ds.n - 1) // 2
+    got = _run(ctx, ds, pairs)
+    rng = np.random.default_rng(123)
+    idx = rng.choice(len(pairs), size=1500, replace=False)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs[idx])
+    np.testing.assert_array_equal(got[idx], ref)
+    # properties that hold at any size
+    lens = np.diff(ds.offs)
+    a, b = lens[pairs[:, 0]], lens[pairs[:, 1]]
+    assert np.all(got >= np.abs(a - b)) and np.all(got <= np.maximum(a, b)) and np.all(got > 0)

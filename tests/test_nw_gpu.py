@@ -1,0 +1,105 @@
+"""Parity of Needleman-Wunsch fill + device traceback (A5, A6) with the oracle.
+
+Scores and edit scripts must equal the oracle's byte for byte.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_15458_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_15458_gb300 import build
+    build.build()
+    c = api.Context(0, workspace_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _nw(ctx, rows, pairs, costs=(0, 1, 1)):
+    seqs = api.ByteSeqs.from_list(rows)
+    score, ops, off, ln = api.nw_align_batch(ctx, seqs, pairs, *costs)
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    return score, [ops[off[p]:off[p] + ln[p]].tobytes() for p in range(len(pairs))]
+
+
+def _check(ctx, rows, pairs, costs=(0, 1, 1)):
+    pairs = np.asarray(pairs, np.int32).reshape(-1, 2)
+    score, scripts = _nw(ctx, rows, pairs, costs)
+    ds = synth.SeqSet.from_list(rows)
+    rs, rops, roff, rln = oracle.nw_pairs(ds.arena, ds.offs, pairs, *costs)
+    for p, (x, y) in enumerate(pairs):
+        ref = rops[roff[p]:roff[p] + rln[p]].tobytes()
+        assert score[p] == rs[p], (p, len(rows[x]), len(rows[y]))
+        assert scripts[p] == ref, (p, len(rows[x]), len(rows[y]))
+        cost, ra, rb = oracle.rescore(rows[x], rows[y], scripts[p], *costs)
+        assert cost == score[p]
+    return score
+
+
+def test_small_dna_pairs(ctx):
+    ds = synth.small_dna(seed=1)
+    pairs = synth.all_pairs(ds.n)[::7]
+    _check(ctx, ds.seqs(), pairs)
+
+
+@pytest.mark.parametrize("costs", [(0, 1, 1), (0, 3, 2), (-1, 2, 3)])
+def test_bruteforce_tiny(ctx, costs):
+    rng = np.random.default_rng(sum(costs) + 40)
+    rows = [rng.choice(list(b"ACG-"), size=int(rng.integers(0, 7))).astype(np.uint8).tobytes() for _ in range(40)]
+    pairs = np.array([[i, (i * 7 + 3) % 40] for i in range(40)], np.int32)
+    score, scripts = _nw(ctx, rows, pairs, costs)
+    for p, (x, y) in enumerate(pairs):
+        c, best = oracle.brute_best(rows[x], rows[y], *costs)
+        assert score[p] == c and scripts[p] == best
+
+
+EDGE = [0, 1, 15, 16, 17, 511, 512, 513, 1024, 1500, 3000]
+
+
+def test_edge_lengths_and_gapped_rows(ctx):
+    rng = np.random.default_rng(41)
+    rows = []
+    for L in EDGE:
+        rows.append(rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes())
+    for L in EDGE:
+        a = np.frombuffer(rows[EDGE.index(L)], np.uint8).copy()
+        if L:
+            a[rng.integers(0, L, max(1, L // 8))] = ord("-")          # gapped center rows
+        rows.append(a.tobytes())
+    n = len(EDGE)
+    pairs = [[i, n + j] for i in range(n) for j in range(n)]
+    _check(ctx, rows, pairs)
+
+
+def test_unit_cost_score_equals_levenshtein(ctx):
+    ds = synth.tree_dna(seed=8, n=40, root_len=700)
+    pairs = synth.random_pairs(3, ds.n, 60)
+    seqs = api.upload_and_pack(ctx, ds)
+    score, _, _, _ = api.nw_align_batch(ctx, seqs, pairs)
+    d = api.lev_batch(ctx, seqs, pairs)
+    ctx.check()
+    np.testing.assert_array_equal(score.cpu().numpy(), d.cpu().numpy())
+    # and both against the oracle
+    np.testing.assert_array_equal(d.cpu().numpy(), oracle.lev_pairs(ds.arena, ds.offs, pairs))
+
+
+def test_protein_center_rows(ctx):
+    members, roots = synth.protein_families(seed=3, n_fam=4, per_fam=10)
+    rows = members.seqs() + roots.seqs()
+    pairs = [[members.n + f, f * 10 + k] for f in range(4) for k in range(10)]
+    _check(ctx, rows, pairs)
+
+
+def test_capacity_error(ctx):
+    seqs = api.ByteSeqs.from_list([b"ACGT", b"ACG"])
+    off = torch.tensor([0, 3], dtype=torch.int64, device="cuda")      # needs 7
+    api.nw_align_batch(ctx, seqs, np.array([[0, 1]], np.int32), ops_off=off)
+    with pytest.raises(api.MsaError):
+        ctx.check()
