@@ -131,6 +131,24 @@ msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs
 msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
                             int64_t P, int32_t *d_out, void *stream);
 
+/* ---- A4: banded Levenshtein with an exactness certificate --------------- */
+/*
+ * Same result as msa_lev_batch: d_out[p] = f(a, b) exactly.  Each pair
+ * starts from the Ukkonen band k0[p] (device int32 [P]): the DP is restricted
+ * to the diagonals with |j - i| + |(n - j) - (m - i)| <= k, which contain
+ * every optimal path whenever f(a, b) <= k.  The banded result is accepted
+ * only when it is <= the band it was computed with; otherwise the band
+ * doubles, and pairs whose band reaches the whole matrix (or the largest
+ * window this build holds in registers) are computed by the full DP of
+ * msa_lev_batch.  k_used_out[p] (device int32 [P]) receives the band that
+ * certified the pair (>= k0[p]), or max(m, n) when the full DP decided it.
+ * Any k0 (even 0) gives the exact distance; a good k0 only saves work.
+ * Needs msa_lev_banded_workspace_bytes(P, n_seqs) of workspace.
+ */
+msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
+                                const int32_t *k0, int32_t *d_out, int32_t *k_used_out, void *stream);
+int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs);
+
 /* ---- A5/A6: Needleman-Wunsch with traceback ----------------------------- */
 /*
  * Global alignment of every pair (section "Merging", step 2: align the two

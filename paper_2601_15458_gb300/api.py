@@ -152,6 +152,26 @@ def lev_batch(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None = 
     return out
 
 
+def lev_banded_batch(ctx: Context, seqs: DeviceSeqs, pairs, k0, out: torch.Tensor | None = None,
+                     k_used: torch.Tensor | None = None, stream=None):
+    """A4: exact distances by certified Ukkonen bands starting at ``k0``.
+
+    Returns ``(d[P], k_used[P])`` (int32).
+    """
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    if isinstance(k0, np.ndarray):
+        k0 = torch.from_numpy(np.ascontiguousarray(k0, dtype=np.int32))
+    k0 = k0.to(device=pairs.device, dtype=torch.int32).contiguous()
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=pairs.device)
+    if k_used is None:
+        k_used = torch.empty(P, dtype=torch.int32, device=pairs.device)
+    ctx.raise_if(_lib.lib().msa_lev_banded_batch(ctx.handle, ctypes.byref(seqs.c), _ptr(pairs), P, _ptr(k0),
+                                                 _ptr(out), _ptr(k_used), _stream(stream)))
+    return out, k_used
+
+
 class ByteSeqs:
     """Byte strings on the device for NW: ``codes[offs[s]:offs[s+1]]``."""
 

@@ -78,11 +78,22 @@ __device__ __forceinline__ bool seq_ok(const int64_t *__restrict__ offs, int32_t
     return a >= 0 && a <= b && b <= total;
 }
 
-__global__ void count_kernel(const int32_t *__restrict__ pairs, int64_t P, int32_t n,
-                             const int64_t *__restrict__ offs, int64_t total,
+// Pair list: all of pairs[0..P) or, with idx, pairs[idx[0 .. *count)).
+struct PairList {
+    const int32_t *pairs;
+    int64_t P;
+    const int32_t *idx;
+    const int32_t *count;
+    __device__ __forceinline__ int64_t size() const { return idx ? (int64_t)*count : P; }
+    __device__ __forceinline__ int64_t id(int64_t k) const { return idx ? (int64_t)idx[k] : k; }
+};
+
+__global__ void count_kernel(PairList L, int32_t n, const int64_t *__restrict__ offs, int64_t total,
                              int32_t *__restrict__ qcount, int32_t *err) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+    const int64_t P = L.size();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = L.id(k);
+        const int q = L.pairs[2 * p], t = L.pairs[2 * p + 1];
         if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) {
             record_error(err, kErrIndex, p, seq_ok(offs, n, total, q) ? t : q);
             continue;
@@ -116,12 +127,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int32_t *__restrict__ 
     if (tid == 1023) out[n] = part[1023];
 }
 
-__global__ void scatter_kernel(const int32_t *__restrict__ pairs, int64_t P, int32_t n,
-                               const int64_t *__restrict__ offs, int64_t total,
+__global__ void scatter_kernel(PairList L, int32_t n, const int64_t *__restrict__ offs, int64_t total,
                                const int32_t *__restrict__ qstart, int32_t *__restrict__ qfill,
                                int32_t *__restrict__ sorted_t, int32_t *__restrict__ sorted_p) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+    const int64_t P = L.size();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = L.id(k);
+        const int q = L.pairs[2 * p], t = L.pairs[2 * p + 1];
         if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) continue;
         const int pos = qstart[q] + atomicAdd(qfill + q, 1);
         sorted_t[pos] = t;
@@ -209,15 +221,22 @@ static msa_status ensure_occupancy(msa_ctx *ctx, const Registry &R, int alphabet
     return MSA_OK;
 }
 
+}  // namespace msa
+
+namespace msa {
+
 // Launches the whole schedule.  `max_len` (host) bounds the buckets launched.
-static msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
-                          int32_t *d_out, cudaStream_t st) {
+// With idx != nullptr the batch is pairs[idx[0 .. *count_dev)), at most P of
+// them; the workspace is taken from `ar` (the whole context workspace if null).
+msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer) {
     const Registry R = registry(s->alphabet);
     msa_status rc = ensure_occupancy(ctx, R, s->alphabet);
     if (rc) return rc;
     const Tune &T = *ctx->tune;
     const int32_t n = s->n_seqs;
-    Arena ar{ctx->ws, ctx->ws_bytes};
+    Arena own{ctx->ws, ctx->ws_bytes};
+    Arena &ar = outer ? *outer : own;
     int32_t *qcount = ar.take<int32_t>(n);
     int32_t *qfill = ar.take<int32_t>(n);
     int32_t *qcursor = ar.take<int32_t>(n);
@@ -240,9 +259,10 @@ static msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
     const int gP = grid_for((int)std::min<int64_t>((P + 255) / 256, ctx->sm_count * 8));
     const int gN = grid_for((int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8));
     ctx->launches += 5;
-    count_kernel<<<gP, 256, 0, st>>>(pairs, P, n, s->offs, s->total, qcount, ctx->dev_err);
+    const PairList L{pairs, P, idx, count_dev};
+    count_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qcount, ctx->dev_err);
     scan_kernel<<<1, 1024, 0, st>>>(qcount, n, qstart);
-    scatter_kernel<<<gP, 256, 0, st>>>(pairs, P, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
+    scatter_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
     const PlanParams pp = plan_params(R, T);
     task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
     task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
@@ -288,7 +308,7 @@ static msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
     return cuda_check(ctx, cudaGetLastError(), "msa_lev_batch launch");
 }
 
-static msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
+msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
                                const void *out, const char *who) {
     if (!ctx || !s) return MSA_EINVAL;
     if (P < 0 || P >= (int64_t(1) << 31)) return set_error(ctx, MSA_EINVAL, "%s: P=%lld out of range", who, (long long)P);
@@ -315,7 +335,7 @@ msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs
     msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_batch");
     if (rc || P == 0) return rc;
     if (s->n_seqs == 0) return set_error(ctx, MSA_EINVAL, "msa_lev_batch: pairs given for an empty set");
-    return lev_run(ctx, s, pairs, P, d_out, (cudaStream_t)stream);
+    return lev_run(ctx, s, pairs, P, d_out, (cudaStream_t)stream, nullptr, nullptr, nullptr);
 }
 
 msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
@@ -343,7 +363,7 @@ msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pa
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3 && rc == MSA_OK; ++rep) {
             cudaEventRecord(e0, st);
-            rc = lev_run(ctx, s, pairs, P, scratch, st);
+            rc = lev_run(ctx, s, pairs, P, scratch, st, nullptr, nullptr, nullptr);
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             float ms = 0;

@@ -89,6 +89,12 @@ struct ProfScope {
     }
 };
 
+msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer);
+msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const void *out,
+                        const char *who);
+int64_t lev_workspace(int64_t P, int32_t n);
+
 inline int bits_of(int alphabet) { return alphabet == MSA_DNA ? 2 : 5; }
 inline int sigma_of(int alphabet) { return alphabet == MSA_DNA ? 4 : 20; }
 

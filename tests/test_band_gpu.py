@@ -1,0 +1,78 @@
+"""Banded Levenshtein with certificate (A4): every distance equals the
+oracle's whatever the starting band, and the band that certified it bounds
+the distance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15458_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_15458_gb300 import build
+    build.build()
+    c = api.Context(0, workspace_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pairs_ds():
+    ds = synth.divergent_pairs(seed=40, n_pairs=160, len_lo=200, len_hi=4000)
+    pairs = np.stack([np.arange(0, ds.n, 2), np.arange(1, ds.n, 2)], axis=1).astype(np.int32)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    return ds, pairs, ref
+
+
+@pytest.mark.parametrize("mode", ["zero", "exact", "below", "above", "huge", "random"])
+def test_band_exact_for_any_start(ctx, pairs_ds, mode):
+    ds, pairs, ref = pairs_ds
+    rng = np.random.default_rng(5)
+    lens = np.diff(ds.offs)
+    mx = np.maximum(lens[pairs[:, 0]], lens[pairs[:, 1]])
+    k0 = {"zero": np.zeros_like(ref), "exact": ref, "below": np.maximum(ref - 1, 0), "above": ref + 40,
+          "huge": mx * 2, "random": rng.integers(0, 2000, len(ref))}[mode].astype(np.int32)
+    seqs = api.upload_and_pack(ctx, ds)
+    d, k_used = api.lev_banded_batch(ctx, seqs, pairs, k0)
+    ctx.check()
+    d, k_used = d.cpu().numpy(), k_used.cpu().numpy()
+    np.testing.assert_array_equal(d, ref)
+    assert np.all(k_used >= ref)
+    assert np.all((k_used >= np.minimum(k0, mx)) | (k_used == mx))
+
+
+def test_band_long_and_short_mix(ctx):
+    rng = np.random.default_rng(6)
+    seqs = []
+    for L in (1, 31, 33, 64, 65, 700, 2048, 2049, 10000):
+        a = rng.choice(list(b"ACGT"), size=L).astype(np.uint8)
+        b = a.copy()
+        k = max(1, L // 20)
+        b[rng.integers(0, L, k)] = rng.choice(list(b"ACGT"), size=k).astype(np.uint8)
+        b = np.concatenate([b[: L // 2], b[L // 2 + min(3, L // 3):]])
+        seqs += [a.tobytes(), b.tobytes()]
+    ds = synth.SeqSet.from_list(seqs)
+    pairs = np.array([[2 * i, 2 * i + 1] for i in range(len(seqs) // 2)] +
+                     [[2 * i + 1, 2 * i] for i in range(len(seqs) // 2)], np.int32)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    sq = api.upload_and_pack(ctx, ds)
+    for k0 in (0, 16, 100, 5000):
+        d, _ = api.lev_banded_batch(ctx, sq, pairs, np.full(len(pairs), k0, np.int32))
+        ctx.check()
+        np.testing.assert_array_equal(d.cpu().numpy(), ref)
+
+
+def test_band_protein(ctx):
+    members, roots = synth.protein_families(seed=3, n_fam=5, per_fam=20)
+    rows = members.seqs() + roots.seqs()
+    ds = synth.SeqSet.from_list(rows, "protein")
+    pairs = np.array([[members.n + f, f * 20 + k] for f in range(5) for k in range(20)], np.int32)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    sq = api.upload_and_pack(ctx, ds)
+    for k0 in (0, 50, 400):
+        d, _ = api.lev_banded_batch(ctx, sq, pairs, np.full(len(pairs), k0, np.int32))
+        ctx.check()
+        np.testing.assert_array_equal(d.cpu().numpy(), ref)
