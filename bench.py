@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=2000, help="sequences (default: the 2,000-sequence workload)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (for profiling)")
+    ap.add_argument("--no-band", action="store_true", help="skip the learned-band measurement")
+    ap.add_argument("--band-pairs", type=int, default=100000)
     return ap.parse_args()
 
 
@@ -147,6 +150,77 @@ def peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, sm_max_mhz=2070.0), "fallback"
 
 
+def band_bench(ctx, args, stream):
+    """Learned band vs full DP on 100,000 fresh DNA pairs (lengths 1,000-10,000,
+    divergence U(1%, 30%)), every distance checked against the full DP."""
+    import torch
+    from paper_2601_15458_gb300 import api, learned_band, synth
+    t0 = time.perf_counter()
+    X, y, tinfo = learned_band.training_set(ctx, seed=4, n_per_tree=710)
+    model, minfo = learned_band.train(ctx, X, y, epochs=8, batch=4096, lr=2e-3, tau=0.9)
+    del X, y
+    # the band margin is picked on held-out pairs of another seed, never on the evaluation pairs
+    val = synth.divergent_pairs(seed=41, n_pairs=5000)
+    vs = api.upload_and_pack(ctx, val)
+    vprof = api.kmer_profile(ctx, vs)
+    vp = torch.from_numpy(np.stack([np.arange(0, val.n, 2), np.arange(1, val.n, 2)], 1).astype(np.int32)).cuda()
+    gamma, _ = learned_band.pick_gamma(ctx, model, vs, vprof, vp)
+    setup_s = time.perf_counter() - t0
+    ev = synth.divergent_pairs(seed=40, n_pairs=args.band_pairs)
+    es = api.upload_and_pack(ctx, ev)
+    prof = api.kmer_profile(ctx, es)
+    P = ev.n // 2
+    pairs = torch.from_numpy(np.stack([np.arange(0, ev.n, 2), np.arange(1, ev.n, 2)], 1).astype(np.int32)).cuda()
+    lens = np.diff(ev.offs)
+    cells = int((lens[0::2].astype(np.int64) * lens[1::2]).sum())
+    d_full = api.lev_batch(ctx, es, pairs)
+    yhat, k = model.predict_band(es, prof, pairs, gamma=gamma, margin=8)
+    d_band, k_used = api.lev_banded_batch(ctx, es, pairs, k)
+    # non-learned start: the 4-mer L1 lower bound, ceil(L1 / 8) <= f
+    Xe = api.pair_features(ctx, es, prof, pairs)
+    meanlen = torch.from_numpy(((lens[0::2] + lens[1::2]) / 2).astype(np.float32)).cuda()
+    l1 = (Xe.float() * meanlen[:, None]).sum(1)
+    dl = torch.from_numpy(np.abs(lens[0::2] - lens[1::2]).astype(np.int32)).cuda()
+    k_l1 = torch.maximum(dl, torch.ceil(l1 / 8).int())
+    d_l1, _ = api.lev_banded_batch(ctx, es, pairs, k_l1)
+    ctx.check()
+    mism = int((d_band != d_full).sum().item()) + int((d_l1 != d_full).sum().item())
+    first = float((k_used.cpu().numpy() < np.maximum(lens[0::2], lens[1::2])).mean())
+    import oracle
+    rng = np.random.default_rng(9)
+    samp = np.sort(rng.choice(P, size=48, replace=False))
+    host_pairs = pairs.cpu().numpy()
+    ref = oracle.lev_pairs(ev.arena, ev.offs, host_pairs[samp])
+    mism += int((ref != d_full.cpu().numpy()[samp]).sum())
+
+    def timed(fn, reps):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    reps = max(2, min(args.steps, 5))
+    t_full = timed(lambda: api.lev_batch(ctx, es, pairs, d_full), reps)
+    t_band = timed(lambda: (model.predict_band(es, prof, pairs, gamma=gamma, margin=8),
+                            api.lev_banded_batch(ctx, es, pairs, k, d_band, k_used)), reps)
+    t_l1 = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_l1, d_l1), reps)
+    ctx.check()
+    return dict(workload=f"divergent_dna_pairs_{P}_len1000-10000_div1-30pct", pairs=P, cells=cells,
+                pairs_per_s_learned=P / (t_band / 1e3), pairs_per_s_full=P / (t_full / 1e3),
+                pairs_per_s_l1_bound=P / (t_l1 / 1e3), speedup_learned_vs_full=t_full / t_band,
+                speedup_learned_vs_l1_bound=t_l1 / t_band,
+                gcups_full=cells / (t_full / 1e3) / 1e9, gcups_equiv_learned=cells / (t_band / 1e3) / 1e9,
+                ms_learned=t_band, ms_full=t_full, mismatches=mism, oracle_sample=len(samp),
+                certified_by_band=first, gamma=gamma, train_pairs=tinfo["pairs"], train_steps=minfo["steps"],
+                val_pinball=minfo["val_loss"], setup_s=setup_s)
+
+
 def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores: each step a bounded sample."""
     if rank != 0:
@@ -197,7 +271,8 @@ def main():
     pairs_d = torch.from_numpy(pairs).cuda()
     out = torch.empty(len(pairs), dtype=torch.int32, device="cuda")
     api.pack(ctx, seqs)
-    api.lev_autotune(ctx, seqs, pairs_d, out)
+    if not args.no_autotune:
+        api.lev_autotune(ctx, seqs, pairs_d, out)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
@@ -299,6 +374,9 @@ def main():
                             f"{words:.4e} word-columns per launch set")
 
     clocks = clk.summary()
+    band = None
+    if not args.no_band:
+        band = band_bench(ctx, args, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(ds, pairs, args.cpu_seconds)
@@ -312,7 +390,7 @@ def main():
                     roofline=roof, cpu_baseline=cpu,
                     e2e=dict(value=e2e_value, unit="GCUPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                              output_matches_device=bool(ok)),
-                    gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps,
+                    gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps, band=band,
                     wall_s_timed=t_wall, clocks=clocks)
         print(json.dumps(line), flush=True)
     ctx.close()

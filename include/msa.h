@@ -149,6 +149,61 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
                                 const int32_t *k0, int32_t *d_out, int32_t *k_used_out, void *stream);
 int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs);
 
+/* ---- A8-A10: learned band proposer -------------------------------------- */
+/*
+ * The paper has no learned component; this proposer only chooses the
+ * starting band k0 of msa_lev_banded_batch, whose certificate keeps every
+ * distance exact.  Features: 4-mer count profiles of DNA (256 bins, k-mer
+ * s0 s1 s2 s3 of codes A=0 C=1 G=2 T=3 in bin 64 s0 + 16 s1 + 4 s2 + s3,
+ * counted over the len - 3 windows), and for a pair (a, b) the 256 values
+ * |c_a - c_b| / ((len_a + len_b) / 2), divided in fp32 and rounded to bf16.
+ * Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with W1 128x256,
+ * W2 64x128, W3 1x64; bf16 weights and activations, fp32 accumulation on the
+ * tensor cores; target y = f(a, b) / max(m, n).
+ *
+ * Model state: one device buffer of msa_mlp_state_bytes() bytes that starts
+ * with the msa_mlp_num_params() fp32 parameters in the order
+ * W1 (out-major, [128][256]), b1, W2 ([64][128]), b2, W3 [64], b3; the rest
+ * (Adam moments, gradient, bf16 copies) is private.  After writing the
+ * parameters, call msa_mlp_sync() (bf16 copies, zero moments and step).
+ */
+int32_t msa_mlp_num_params(void);
+int64_t msa_mlp_state_bytes(void);
+msa_status msa_mlp_sync(msa_ctx *ctx, void *state, void *stream);
+/* prof: device uint16 [n_seqs][256]; DNA sets only, lengths <= 65535. */
+msa_status msa_kmer_profile(msa_ctx *ctx, const msa_seqset *s, uint16_t *prof, void *stream);
+/* X: device bf16 (as uint16 bits) [P][256], the pair features of `pairs`. */
+msa_status msa_pair_features(msa_ctx *ctx, const msa_seqset *s, const uint16_t *prof, const int32_t *pairs,
+                             int64_t P, uint16_t *X, void *stream);
+/* yhat[p] = network output for feature row p (X bf16 [P][256]). */
+msa_status msa_mlp_forward(msa_ctx *ctx, const void *state, const uint16_t *X, int64_t P, float *yhat,
+                           void *stream);
+/*
+ * One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, fp32 master
+ * weights, bf16 copies refreshed) on the minibatch rows idx[0..B) of
+ * (X bf16 [N][256], y fp32 [N]; indices outside [0, N) count as zero rows),
+ * minimising the mean pinball loss of quantile tau:
+ * rho(r) = tau r for r = y - yhat > 0, (tau - 1) r otherwise.
+ * loss_out (device float, may be null) receives the batch loss before the
+ * update.  lr = 0 computes loss and gradient only (the gradient is then left
+ * in the state and can be read with msa_mlp_read_grad).
+ * Needs msa_mlp_train_workspace_bytes(B) of workspace.
+ */
+msa_status msa_mlp_train_step(msa_ctx *ctx, void *state, const uint16_t *X, const float *y, int64_t N,
+                              const int32_t *idx, int32_t B, float lr, float tau, float *loss_out, void *stream);
+int64_t msa_mlp_train_workspace_bytes(int32_t B);
+/* Copies the current gradient (fp32, parameter order) to grad_out and zeroes it. */
+msa_status msa_mlp_read_grad(msa_ctx *ctx, void *state, float *grad_out, void *stream);
+/*
+ * Fused features + forward + band policy for each pair:
+ *   yhat[p] = network output, k_out[p] = max(|m - n|,
+ *   ceil((1 + gamma) * max(yhat, 0) * max(m, n)) + margin).
+ * prof from msa_kmer_profile of the same set.
+ */
+msa_status msa_band_predict(msa_ctx *ctx, const void *state, const msa_seqset *s, const uint16_t *prof,
+                            const int32_t *pairs, int64_t P, float gamma, int32_t margin, float *yhat,
+                            int32_t *k_out, void *stream);
+
 /* ---- A5/A6: Needleman-Wunsch with traceback ----------------------------- */
 /*
  * Global alignment of every pair (section "Merging", step 2: align the two
@@ -178,6 +233,53 @@ msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t 
                               void *stream);
 /* Workspace bytes msa_nw_align_batch needs to run `warps` pairs at once. */
 int64_t msa_nw_workspace_bytes(int32_t max_len, int32_t warps);
+
+/* ---- A11: guide tree by Alg. 1 (Partition) ------------------------------ */
+/*
+ * Builds the binary cluster tree of Alg. 1 (section "Clustering") over the
+ * whole set, every cluster split until it is a singleton.  For a cluster C:
+ * centre c = geometric median of C, taken over all of C when |C| <= 256 and
+ * otherwise over the 256 members at positions floor(k |C| / 256),
+ * k = 0..255, of C sorted by index (the paper allows "a smaller subset"
+ * without fixing one; this is the rule of this library); l = argmax f(c, x),
+ * r = argmax f(l, x) over x in C; L = {x : f(l, x) <= f(r, x)},
+ * R = {x : f(r, x) < f(l, x)}.  Every argmin / argmax tie goes to the
+ * smallest index.  Sequences must be distinct (the paper de-duplicates its
+ * input first); a cluster that does not split returns MSA_EDATA.
+ * Outputs: order (device int32 [n]) lists the sequences so that every node k
+ * covers order[lo[k] .. hi[k]) and each node's range is its left child's
+ * range followed by its right child's; lo, hi, center, left, right, parent
+ * are HOST int32 arrays with room for 2n - 1 nodes, in breadth-first order
+ * (node 0 = root; -1 = none).  *n_nodes (host) receives 2n - 1.
+ * Synchronous: the host reads the left-child sizes once per tree level.
+ */
+msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order, int32_t *lo, int32_t *hi,
+                              int32_t *center, int32_t *left, int32_t *right, int32_t *parent,
+                              int32_t *n_nodes, void *stream);
+
+/* ---- A12: bottom-up merge along the guide tree -------------------------- */
+/*
+ * Section "Merging": a leaf is the one-row MSA of its sequence; a parent
+ * aligns its two children's centres, each as the gapped row it has in its
+ * child's MSA, by NW (msa_nw_align_batch semantics; the gap is an ordinary
+ * symbol, gap code 4 for DNA and 20 for protein), inserts an all-gap column
+ * into the left child's rows for every MSA_OP_INS and into the right child's
+ * rows for every MSA_OP_DEL, and stacks the left rows over the right rows.
+ * All merges of one tree height run as one batch.
+ * Inputs: the tree of msa_clam_partition (order device, the rest host).
+ * Outputs: pos (device int32, one entry per arena position): pos[offs[s]+k]
+ * = column of residue k of sequence s in the root MSA; width / score (HOST
+ * int32 [n_nodes]): MSA width of every node and, for internal nodes, the NW
+ * cost of its merge (-1 for leaves).  Synchronous (one read-back per height).
+ */
+msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                          const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
+                          int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t *pos,
+                          int32_t *width, int32_t *score, void *stream);
+/* Writes the MSA rows (ASCII, '-' for gaps) in `order`: row r (W bytes at
+ * rows + r*W, device) is sequence order[r]; W = width of the root. */
+msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,
+                        uint8_t *rows, void *stream);
 
 #ifdef __cplusplus
 }

@@ -390,6 +390,34 @@ def medoid_candidates(members):
     return [members[(k * n) // MEDOID_SAMPLE] for k in range(MEDOID_SAMPLE)]
 
 
+def _default_dist(seqs):
+    cache = {}
+
+    def dist(x, y):
+        key = (x, y) if x < y else (y, x)
+        if key not in cache:
+            cache[key] = lev(seqs[key[0]], seqs[key[1]])
+        return cache[key]
+    return dist
+
+
+def partition_step(members, dist):
+    """One application of Alg. 1 to the cluster ``members`` (|C| > 1).
+
+    Returns ``(c, l, r, L, R)``: the centre (geometric median over
+    :func:`medoid_candidates`), the two poles and the two children (sorted).
+    """
+    C = sorted(members)
+    S = medoid_candidates(C)
+    sums = [(sum(dist(x, y) for y in S), x) for x in S]
+    c = min(sums)[1]
+    l = min((-dist(c, x), x) for x in C)[1]
+    r = min((-dist(l, x), x) for x in C)[1]
+    Lm = [x for x in C if dist(l, x) <= dist(r, x)]
+    Rm = [x for x in C if dist(r, x) < dist(l, x)]
+    return c, l, r, Lm, Rm
+
+
 def partition(seqs, dist=None):
     """Alg. 1 ``Partition`` applied from the root until every leaf is a singleton.
 
@@ -401,14 +429,7 @@ def partition(seqs, dist=None):
     as Alg. 1 states.
     """
     if dist is None:
-        cache = {}
-
-        def dist(x, y):
-            key = (x, y) if x < y else (y, x)
-            if key not in cache:
-                cache[key] = lev(seqs[key[0]], seqs[key[1]])
-            return cache[key]
-
+        dist = _default_dist(seqs)
     nodes = [dict(members=sorted(range(len(seqs))), center=-1, left=-1, right=-1, parent=-1)]
     q = 0
     while q < len(nodes):
@@ -417,14 +438,8 @@ def partition(seqs, dist=None):
         if len(C) == 1:
             node["center"] = C[0]
         else:
-            S = medoid_candidates(C)
-            sums = [(sum(dist(x, y) for y in S), x) for x in S]
-            c = min(sums)[1]
+            c, l, r, Lm, Rm = partition_step(C, dist)
             node["center"] = c
-            l = min((-dist(c, x), x) for x in C)[1]
-            r = min((-dist(l, x), x) for x in C)[1]
-            Lm = [x for x in C if dist(l, x) <= dist(r, x)]
-            Rm = [x for x in C if dist(r, x) < dist(l, x)]
             assert Lm and Rm, "de-duplicated input guarantees both children are non-empty"
             for side, mem in (("left", Lm), ("right", Rm)):
                 node[side] = len(nodes)

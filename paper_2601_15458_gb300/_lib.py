@@ -48,6 +48,26 @@ SIGNATURES = {
     "msa_lev_banded_batch": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_int64, c_void_p, c_void_p,
                                        c_void_p, c_void_p]),
     "msa_lev_banded_workspace_bytes": (c_int64, [c_int64, c_int32]),
+    "msa_mlp_num_params": (c_int32, []),
+    "msa_mlp_state_bytes": (c_int64, []),
+    "msa_mlp_sync": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "msa_kmer_profile": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p]),
+    "msa_pair_features": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int64, c_void_p,
+                                    c_void_p]),
+    "msa_mlp_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "msa_mlp_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_float,
+                                     c_float, c_void_p, c_void_p]),
+    "msa_mlp_train_workspace_bytes": (c_int64, [c_int32]),
+    "msa_mlp_read_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "msa_band_predict": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int64,
+                                   c_float, c_int32, c_void_p, c_void_p, c_void_p]),
+    "msa_clam_partition": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "msa_merge_tree": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                 c_void_p, c_void_p]),
+    "msa_msa_rows": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int32, c_void_p,
+                               c_void_p]),
 }
 
 

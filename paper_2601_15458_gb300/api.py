@@ -232,3 +232,159 @@ def lev_autotune(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None
     ctx.raise_if(_lib.lib().msa_lev_autotune(ctx.handle, ctypes.byref(seqs.c), _ptr(pairs), P, _ptr(out),
                                              _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned band proposer (A8-A10)
+# ---------------------------------------------------------------------------
+
+MLP_SHAPES = (("W1", (128, 256)), ("b1", (128,)), ("W2", (64, 128)), ("b2", (64,)), ("W3", (64,)), ("b3", (1,)))
+
+
+def mlp_init_params(seed: int = 0) -> dict:
+    """He-initialised parameters (numpy float32), in the library's layout."""
+    rng = np.random.default_rng(seed)
+    return dict(W1=(rng.standard_normal((128, 256)) * np.sqrt(2 / 256)).astype(np.float32),
+                b1=np.zeros(128, np.float32),
+                W2=(rng.standard_normal((64, 128)) * np.sqrt(2 / 128)).astype(np.float32),
+                b2=np.zeros(64, np.float32),
+                W3=(rng.standard_normal(64) * np.sqrt(1 / 64)).astype(np.float32),
+                b3=np.zeros(1, np.float32))
+
+
+def flatten_params(params: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(params[k], np.float32).reshape(-1) for k, _ in MLP_SHAPES])
+
+
+def unflatten_params(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for k, shp in MLP_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+class BandModel:
+    """Device state of the band-proposer network (parameters, Adam moments)."""
+
+    def __init__(self, ctx: Context, params: dict | None = None, seed: int = 0):
+        L = _lib.lib()
+        self.ctx = ctx
+        self.np = int(L.msa_mlp_num_params())
+        self.state = torch.zeros(int(L.msa_mlp_state_bytes()) // 4, dtype=torch.float32, device="cuda")
+        self.set_params(params if params is not None else mlp_init_params(seed))
+
+    def set_params(self, params: dict, stream=None):
+        flat = torch.from_numpy(flatten_params(params)).cuda()
+        assert flat.numel() == self.np
+        self.state[: self.np].copy_(flat)
+        self.ctx.raise_if(_lib.lib().msa_mlp_sync(self.ctx.handle, _ptr(self.state), _stream(stream)))
+
+    def params(self) -> dict:
+        return unflatten_params(self.state[: self.np].cpu().numpy().copy())
+
+    def forward(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        P = X.shape[0]
+        y = torch.empty(P, dtype=torch.float32, device=X.device)
+        self.ctx.raise_if(_lib.lib().msa_mlp_forward(self.ctx.handle, _ptr(self.state), _ptr(X), P, _ptr(y),
+                                                     _stream(stream)))
+        return y
+
+    def train_step(self, X: torch.Tensor, y: torch.Tensor, idx: torch.Tensor, lr: float, tau: float = 0.9,
+                   stream=None) -> torch.Tensor:
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self.ctx.raise_if(_lib.lib().msa_mlp_train_step(self.ctx.handle, _ptr(self.state), _ptr(X), _ptr(y),
+                                                        int(X.shape[0]), _ptr(idx), int(idx.numel()), float(lr),
+                                                        float(tau),
+                                                        _ptr(loss), _stream(stream)))
+        return loss
+
+    def read_grad(self, stream=None) -> dict:
+        g = torch.empty(self.np, dtype=torch.float32, device="cuda")
+        self.ctx.raise_if(_lib.lib().msa_mlp_read_grad(self.ctx.handle, _ptr(self.state), _ptr(g), _stream(stream)))
+        return unflatten_params(g.cpu().numpy())
+
+    def predict_band(self, seqs: DeviceSeqs, prof: torch.Tensor, pairs, gamma: float = 0.1, margin: int = 8,
+                     stream=None):
+        """Fused features + forward + band policy: returns ``(yhat[P], k[P])``."""
+        pairs = _pairs_tensor(pairs)
+        P = pairs.shape[0]
+        yhat = torch.empty(P, dtype=torch.float32, device=pairs.device)
+        k = torch.empty(P, dtype=torch.int32, device=pairs.device)
+        self.ctx.raise_if(_lib.lib().msa_band_predict(self.ctx.handle, _ptr(self.state), ctypes.byref(seqs.c),
+                                                      _ptr(prof), _ptr(pairs), P, float(gamma), int(margin),
+                                                      _ptr(yhat), _ptr(k), _stream(stream)))
+        return yhat, k
+
+
+def kmer_profile(ctx: Context, seqs: DeviceSeqs, stream=None) -> torch.Tensor:
+    """A8: uint16 [n][256] 4-mer counts (returned as int16 storage)."""
+    prof = torch.empty((seqs.n, 256), dtype=torch.int16, device="cuda")
+    ctx.raise_if(_lib.lib().msa_kmer_profile(ctx.handle, ctypes.byref(seqs.c), _ptr(prof), _stream(stream)))
+    return prof
+
+
+def pair_features(ctx: Context, seqs: DeviceSeqs, prof: torch.Tensor, pairs, stream=None) -> torch.Tensor:
+    """bf16 [P][256] pair features (as bfloat16 tensor)."""
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    X = torch.empty((P, 256), dtype=torch.bfloat16, device="cuda")
+    ctx.raise_if(_lib.lib().msa_pair_features(ctx.handle, ctypes.byref(seqs.c), _ptr(prof), _ptr(pairs), P,
+                                              _ptr(X), _stream(stream)))
+    return X
+
+
+# ---------------------------------------------------------------------------
+# guide tree (A11) and merge (A12)
+# ---------------------------------------------------------------------------
+
+class Tree:
+    """Cluster tree of Alg. 1: ``order`` (device) and host node arrays in BFS order."""
+
+    def __init__(self, n: int):
+        cap = max(1, 2 * n - 1)
+        self.n = n
+        self.order = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        self.lo, self.hi, self.center, self.left, self.right, self.parent = (
+            np.full(cap, -1, np.int32) for _ in range(6))
+        self.n_nodes = 0
+
+    def members(self, k: int, order_host: np.ndarray | None = None) -> list:
+        o = self.order.cpu().numpy() if order_host is None else order_host
+        return sorted(int(x) for x in o[self.lo[k]:self.hi[k]])
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def clam_partition(ctx: Context, seqs: DeviceSeqs, stream=None) -> Tree:
+    """A11: build the guide tree (msa_clam_partition)."""
+    t = Tree(seqs.n)
+    nn = ctypes.c_int32(0)
+    ctx.raise_if(_lib.lib().msa_clam_partition(ctx.handle, ctypes.byref(seqs.c), _ptr(t.order), _np_ptr(t.lo),
+                                               _np_ptr(t.hi), _np_ptr(t.center), _np_ptr(t.left), _np_ptr(t.right),
+                                               _np_ptr(t.parent), ctypes.byref(nn), _stream(stream)))
+    t.n_nodes = nn.value
+    return t
+
+
+def merge_tree(ctx: Context, seqs: DeviceSeqs, tree: Tree, match=0, mismatch=1, gap=1, stream=None):
+    """A12: bottom-up merge; returns ``(pos tensor, width[n_nodes], score[n_nodes])``."""
+    pos = torch.empty(max(seqs.total, 1), dtype=torch.int32, device="cuda")
+    width = np.zeros(max(tree.n_nodes, 1), np.int32)
+    score = np.zeros(max(tree.n_nodes, 1), np.int32)
+    ctx.raise_if(_lib.lib().msa_merge_tree(ctx.handle, ctypes.byref(seqs.c), _ptr(tree.order), _np_ptr(tree.lo),
+                                           _np_ptr(tree.hi), _np_ptr(tree.center), _np_ptr(tree.left),
+                                           _np_ptr(tree.right), tree.n_nodes, match, mismatch, gap, _ptr(pos),
+                                           _np_ptr(width), _np_ptr(score), _stream(stream)))
+    return pos, width[: tree.n_nodes], score[: tree.n_nodes]
+
+
+def msa_rows(ctx: Context, seqs: DeviceSeqs, tree: Tree, pos: torch.Tensor, W: int, stream=None) -> torch.Tensor:
+    """The MSA as uint8 [n, W] rows in tree order (ASCII, '-' for gaps)."""
+    rows = torch.empty((max(seqs.n, 1), max(W, 1)), dtype=torch.uint8, device="cuda")
+    ctx.raise_if(_lib.lib().msa_msa_rows(ctx.handle, ctypes.byref(seqs.c), _ptr(tree.order), _ptr(pos), int(W),
+                                         _ptr(rows), _stream(stream)))
+    return rows[: seqs.n, :W]

@@ -109,11 +109,11 @@ __global__ void __launch_bounds__(256) kmer_kernel(const uint8_t *__restrict__ c
 // Pair features of 16 pairs into a warp's shared tile X[16][kS1] (bf16).
 __device__ __forceinline__ void features_tile(__nv_bfloat16 *X, const uint16_t *__restrict__ prof,
                                               const int64_t *__restrict__ offs, const int32_t *__restrict__ pairs,
-                                              int64_t row0, int64_t P, int lane) {
+                                              int64_t row0, int64_t P, int32_t n, int lane) {
     for (int r = 0; r < 16; ++r) {
         const int64_t p = row0 + r;
-        if (p < P) {
-            const int a = pairs[2 * p], b = pairs[2 * p + 1];
+        const int a = p < P ? pairs[2 * p] : -1, b = p < P ? pairs[2 * p + 1] : -1;
+        if (a >= 0 && a < n && b >= 0 && b < n) {
             const float den0 = 0.5f * (float)((offs[a + 1] - offs[a]) + (offs[b + 1] - offs[b]));
             const float den = den0 > 0.f ? den0 : 1.f;
             const uint16_t *ca = prof + (int64_t)a * 256, *cb = prof + (int64_t)b * 256;
@@ -249,6 +249,7 @@ struct FwdArgs {
     const int64_t *offs;
     const int32_t *pairs;
     int64_t P;
+    int32_t n_seqs;
     float *yhat;                 // [P]
     int32_t *k_out;              // [P] band, or null
     float gamma;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_forward_kernel(FwdArgs a) 
                     X[r * kS1 + k] = p < a.P ? a.X[p * kF + k] : __float2bfloat16_rn(0.f);
             }
         } else {
-            features_tile(X, a.prof, a.offs, a.pairs, row0, a.P, lane);
+            features_tile(X, a.prof, a.offs, a.pairs, row0, a.P, a.n_seqs, lane);
         }
         __syncwarp();
         float y0, y1;
@@ -293,6 +294,10 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_forward_kernel(FwdArgs a) 
                 a.yhat[p] = y;
                 if (a.k_out) {
                     const int x = a.pairs[2 * p], z = a.pairs[2 * p + 1];
+                    if (x < 0 || x >= a.n_seqs || z < 0 || z >= a.n_seqs) {
+                        a.k_out[p] = 0;
+                        continue;
+                    }
                     const int lx = (int)(a.offs[x + 1] - a.offs[x]), lz = (int)(a.offs[z + 1] - a.offs[z]);
                     const int mx = max(lx, lz);
                     const float kf = ceilf((1.f + a.gamma) * fmaxf(y, 0.f) * (float)mx);
@@ -316,6 +321,7 @@ struct TrainArgs {
     const __nv_bfloat16 *Xall;   // [N][256]
     const float *yall;           // [N]
     const int32_t *idx;          // [B] rows of this minibatch
+    int64_t N;                   // rows of Xall / yall
     int32_t B, Bp;               // batch and its padded stride (multiple of 16)
     float tau;
     __nv_bfloat16 *XT;           // [256][Bp]
@@ -345,7 +351,8 @@ __global__ void __launch_bounds__(kMlpWarps * 32) train_fwd_bwd_kernel(TrainArgs
         const int row0 = tile * 16;
         for (int r = 0; r < 16; ++r) {
             const int b = row0 + r;
-            const int64_t src = b < a.B ? (int64_t)a.idx[b] : -1;
+            int64_t src = b < a.B ? (int64_t)a.idx[b] : -1;
+            if (src >= a.N) src = -1;
             for (int k = lane * 8; k < lane * 8 + 8; ++k) {
                 const __nv_bfloat16 v = src >= 0 ? a.Xall[src * kF + k] : __float2bfloat16_rn(0.f);
                 X[r * kS1 + k] = v;
@@ -361,7 +368,8 @@ __global__ void __launch_bounds__(kMlpWarps * 32) train_fwd_bwd_kernel(TrainArgs
         for (int h = 0; h < 2; ++h) {
             const int b = row0 + g + 8 * h;
             if (b < a.B) {
-                const float r = a.yall[a.idx[b]] - (h ? y1 : y0);
+                const int64_t src = a.idx[b];
+                const float r = (src >= 0 && src < a.N ? a.yall[src] : 0.f) - (h ? y1 : y0);
                 dy[h] = (r > 0.f ? -a.tau : 1.f - a.tau) / (float)a.B;
                 loss += (r > 0.f ? a.tau * r : (a.tau - 1.f) * r) / (float)a.B;
             }
@@ -598,7 +606,7 @@ msa_status msa_mlp_forward(msa_ctx *ctx, const void *state, const uint16_t *X, i
     msa_status rc = ensure_mlp_smem(ctx);
     if (rc) return rc;
     FwdArgs a{state_of(const_cast<void *>(state)), reinterpret_cast<const __nv_bfloat16 *>(X), nullptr, nullptr,
-              nullptr, P, yhat, nullptr, 0.f, 0};
+              nullptr, P, 0, yhat, nullptr, 0.f, 0};
     const int blocks = (int)std::min<int64_t>((P + 16 * kMlpWarps - 1) / (16 * kMlpWarps), ctx->sm_count);
     mlp_forward_kernel<<<blocks, kMlpWarps * 32, kMlpSmem, (cudaStream_t)stream>>>(a);
     ++ctx->launches;
@@ -615,7 +623,8 @@ msa_status msa_band_predict(msa_ctx *ctx, const void *state, const msa_seqset *s
         return set_error(ctx, MSA_EINVAL, "msa_band_predict: null pointer");
     msa_status rc = ensure_mlp_smem(ctx);
     if (rc) return rc;
-    FwdArgs a{state_of(const_cast<void *>(state)), nullptr, prof, s->offs, pairs, P, yhat, k_out, gamma, margin};
+    FwdArgs a{state_of(const_cast<void *>(state)), nullptr, prof, s->offs, pairs, P, s->n_seqs, yhat, k_out, gamma,
+              margin};
     const int blocks = (int)std::min<int64_t>((P + 16 * kMlpWarps - 1) / (16 * kMlpWarps), ctx->sm_count);
     ProfScope prof_scope(ctx, (cudaStream_t)stream);
     mlp_forward_kernel<<<blocks, kMlpWarps * 32, kMlpSmem, (cudaStream_t)stream>>>(a);
@@ -628,8 +637,8 @@ int64_t msa_mlp_train_workspace_bytes(int32_t B) {
     return ((int64_t)(kF + kH1 + kH2 + kH1 + kH2) * Bp * 2 + Bp * 4 + 4096);
 }
 
-msa_status msa_mlp_train_step(msa_ctx *ctx, void *state, const uint16_t *X, const float *y, const int32_t *idx,
-                              int32_t B, float lr, float tau, float *loss_out, void *stream) {
+msa_status msa_mlp_train_step(msa_ctx *ctx, void *state, const uint16_t *X, const float *y, int64_t N,
+                              const int32_t *idx, int32_t B, float lr, float tau, float *loss_out, void *stream) {
     if (!ctx || !state) return MSA_EINVAL;
     if (B <= 0 || !X || !y || !idx) return set_error(ctx, MSA_EINVAL, "msa_mlp_train_step: bad batch");
     msa_status rc = ensure_mlp_smem(ctx);
@@ -642,6 +651,7 @@ msa_status msa_mlp_train_step(msa_ctx *ctx, void *state, const uint16_t *X, cons
     a.Xall = reinterpret_cast<const __nv_bfloat16 *>(X);
     a.yall = y;
     a.idx = idx;
+    a.N = N;
     a.B = B;
     a.Bp = Bp;
     a.tau = tau;
@@ -677,3 +687,12 @@ msa_status msa_mlp_train_step(msa_ctx *ctx, void *state, const uint16_t *X, cons
 }
 
 }  // extern "C"
+
+extern "C" msa_status msa_mlp_read_grad(msa_ctx *ctx, void *state, float *grad_out, void *stream) {
+    if (!ctx || !state || !grad_out) return MSA_EINVAL;
+    MlpState st = state_of(state);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(grad_out, st.g, kNP * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.g, 0, kNP * sizeof(float), s);
+    return cuda_check(ctx, e, "msa_mlp_read_grad");
+}

@@ -160,6 +160,14 @@ msa_status msa_ctx_create(msa_ctx **out, int32_t device, int64_t workspace_bytes
         return st;
     }
     ctx->tune = create_tune();
+    bool ok = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < msa_ctx::kSide && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        msa_ctx_destroy(ctx);
+        return MSA_ECUDA;
+    }
     *out = ctx;
     return MSA_OK;
 }
@@ -171,6 +179,11 @@ void msa_ctx_destroy(msa_ctx *ctx) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
+    for (int k = 0; k < msa_ctx::kSide; ++k) {
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+        if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dev_err) cudaFree(ctx->dev_err);
     destroy_tune(ctx->tune);

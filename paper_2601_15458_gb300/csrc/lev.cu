@@ -29,7 +29,7 @@ constexpr int kMaxBuckets = 64;
 
 struct Tune {
     int lane_min_targets = 12;  // below this a query goes to the warp kernel
-    int lane_per_task = 256;    // targets per task, lane kernel
+    int lane_per_task = 0;      // targets per task, lane kernel (0: from the batch size)
     int warp_per_task = 4;      // targets per task, warp kernel
     int occupancy[2][kMaxBuckets] = {};  // blocks per SM, per alphabet and bucket
 };
@@ -191,14 +191,21 @@ int64_t lev_workspace(int64_t P, int32_t n) {
            r(4 * kMaxBuckets) * 4;
 }
 
-static PlanParams plan_params(const Registry &R, const Tune &T) {
+static PlanParams plan_params(const Registry &R, const Tune &T, int64_t P, int sm_count) {
     PlanParams pp{};
     pp.nlane = R.nlane;
     pp.nwarp = R.nwarp;
     for (int b = 0; b < R.nlane; ++b) pp.lane_words[b] = R.lane[b].words;
     for (int b = 0; b < R.nwarp; ++b) pp.warp_words[b] = R.warp[b].words;
     pp.lane_min_targets = T.lane_min_targets;
-    pp.lane_per_task = T.lane_per_task;
+    if (T.lane_per_task > 0) {
+        pp.lane_per_task = T.lane_per_task;
+    } else {
+        // about four tasks per resident warp (16 per SM), 32..512 targets each
+        int64_t per = P / ((int64_t)sm_count * 16 * 4);
+        per = std::max<int64_t>(32, std::min<int64_t>(512, per));
+        pp.lane_per_task = (int)(per / 32 * 32);
+    }
     pp.warp_per_task = T.warp_per_task;
     return pp;
 }
@@ -263,7 +270,7 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     count_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qcount, ctx->dev_err);
     scan_kernel<<<1, 1024, 0, st>>>(qcount, n, qstart);
     scatter_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
-    const PlanParams pp = plan_params(R, T);
+    const PlanParams pp = plan_params(R, T, P, ctx->sm_count);
     task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
     task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
 
@@ -281,6 +288,8 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     a.bcounter = bcounter;
     a.d_out = d_out;
     a.err = ctx->dev_err;
+    a.one = 1u;
+    a.two = 2u;
     // buckets that no sequence of this set can reach are not launched
     const int Wmax = std::max(1, (s->max_len + 31) / 32);
     int lane_last = R.nlane - 1;
@@ -295,16 +304,24 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
             warp_last = b;
             break;
         }
-    ProfScope prof(ctx, st);
+    // the buckets are independent: run them side by side so that small or
+    // uneven buckets do not leave the GPU idle one after another
+    std::vector<int> launch_list;
     for (int b = 0; b < R.count(); ++b) {
         const bool is_lane = b < R.nlane;
         if (is_lane && b > lane_last) continue;
         if (!is_lane && b - R.nlane > warp_last) continue;
-        a.bucket = b;
-        const int grid = grid_for(ctx->sm_count * T.occupancy[s->alphabet][b]);
-        R.at(b).launch(a, grid, st);
-        ++ctx->launches;
+        launch_list.push_back(b);
     }
+    ProfScope prof(ctx, st);
+    e = run_concurrent(ctx, st, (int)launch_list.size(), [&](int i, cudaStream_t s2) {
+        LevArgs ai = a;
+        ai.bucket = launch_list[i];
+        const int grid = grid_for(ctx->sm_count * T.occupancy[s->alphabet][ai.bucket]);
+        R.at(ai.bucket).launch(ai, grid, s2);
+    });
+    ctx->launches += (int64_t)launch_list.size();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_batch launch");
     return cuda_check(ctx, cudaGetLastError(), "msa_lev_batch launch");
 }
 
@@ -349,8 +366,8 @@ msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pa
     struct Cand {
         int lane_min, lane_per, warp_per;
     };
-    const Cand cands[] = {{12, 256, 4}, {4, 256, 4}, {32, 256, 4}, {12, 128, 4}, {12, 512, 4},
-                          {12, 256, 1}, {12, 256, 16}, {1 << 30, 256, 4}};
+    const Cand cands[] = {{12, 0, 4},   {4, 0, 4},    {32, 0, 4},   {12, 64, 4},       {12, 128, 4},
+                          {12, 256, 4}, {12, 512, 4}, {12, 0, 1},   {12, 0, 16},  {1 << 30, 0, 4}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

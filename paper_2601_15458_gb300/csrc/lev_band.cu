@@ -58,6 +58,7 @@ struct BandArgs {
     int32_t *next_list;       // failures
     int32_t *next_count;
     int32_t bucket;
+    uint32_t one, two;        // 1 and 2, as runtime values (see bv_word)
 };
 
 template <int WB, int B>
@@ -66,66 +67,57 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
     const int32_t *list = a.blist + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
     constexpr int KW = 32 * (WB - 1) - 1;
+    const uint32_t one = a.one, two = a.two;
     uint32_t Pv[WB], Mv[WB], Pl[WB][B];
-    // per-lane pair state; one flat loop so that lanes with pairs of different
-    // lengths never wait for each other except at the very end
-    int p = -1, m = 0, n = 0, j = 0, wlo = 0, wmax = 0, dmax = 0, T = 0;
-    bool full = true;
+    // per-lane pair state; a warp-synchronous loop (a vote over the whole
+    // warp each iteration) so that lanes with pairs of different lengths and
+    // window phases rejoin before every column
+    int p = -1, m = 0, n = 0, j = 0, wlo = 0, wmax = 0, dmax = 0, T = 0, c_next = 0;
+    bool full = true, has = false, more = true;
     int64_t qa = 0;
     const uint8_t *tc = nullptr;
     while (true) {
-        if (j == n) {
-            if (p >= 0) {
-                // T = D[32 wlo][n] (exactly n while the window still starts at row 0)
-                int d = T;
+        if (!has && more) {
+            const int k = atomicAdd(counter, 1);
+            if (k >= cnt) {
+                more = false;
+            } else {
+                p = list[k];
+                const int q = a.pairs[2 * p], t = a.pairs[2 * p + 1];
+                int64_t qb = a.offs[q + 1], ta = a.offs[t], tb = a.offs[t + 1];
+                qa = a.offs[q];
+                if (qb - qa < tb - ta) {     // longer sequence on the rows
+                    int64_t y = qa; qa = ta; ta = y;
+                    y = qb; qb = tb; tb = y;
+                }
+                m = (int)(qb - qa);
+                n = (int)(tb - ta);
+                const int W = max(1, (m + 31) / 32);
+                full = W <= WB;                        // the window holds the whole column: plain DP
+                dmax = (n - m + KW) >> 1;              // floor((n - m + k_w) / 2), may be negative
+                wmax = full ? 0 : W - WB;
+                tc = a.codes + ta;
+                wlo = 0;
+                T = 0;
+                j = 0;
+                c_next = n > 0 ? __ldg(tc) : 0;
 #pragma unroll
                 for (int s = 0; s < WB; ++s) {
-                    const int rem = m - 32 * (wlo + s);
-                    const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-                    d += __popc(Pv[s] & mk) - __popc(Mv[s] & mk);
-                }
-                if (full || d <= KW) {
-                    a.d_out[p] = d;
-                    a.k_used[p] = full ? max(m, n) : KW;
-                } else {
-                    a.k_cur[p] = 2 * KW + 1;
-                    a.next_list[atomicAdd(a.next_count, 1)] = p;
-                }
-            }
-            const int k = atomicAdd(counter, 1);
-            if (k >= cnt) break;
-            p = list[k];
-            int q = a.pairs[2 * p], t = a.pairs[2 * p + 1];
-            int64_t qb = a.offs[q + 1], ta = a.offs[t], tb = a.offs[t + 1];
-            qa = a.offs[q];
-            if (qb - qa < tb - ta) {     // longer sequence on the rows
-                int64_t y = qa; qa = ta; ta = y;
-                y = qb; qb = tb; tb = y;
-            }
-            m = (int)(qb - qa);
-            n = (int)(tb - ta);
-            const int W = max(1, (m + 31) / 32);
-            full = W <= WB;                        // the window holds the whole column: plain DP
-            dmax = (n - m + KW) >> 1;              // floor((n - m + k_w) / 2), may be negative
-            wmax = full ? 0 : W - WB;
-            tc = a.codes + ta;
-            wlo = 0;
-            T = 0;
-            j = 0;
+                    Pv[s] = kFull;
+                    Mv[s] = 0u;
+                    uint32_t mask;
+                    uint32_t pl[B];
+                    query_planes<B>(a.planes, qa, m, s, pl, mask);
 #pragma unroll
-            for (int s = 0; s < WB; ++s) {
-                Pv[s] = kFull;
-                Mv[s] = 0u;
-                uint32_t mask;
-                uint32_t pl[B];
-                query_planes<B>(a.planes, qa, m, s, pl, mask);
-#pragma unroll
-                for (int b = 0; b < B; ++b) Pl[s][b] = pl[b];
+                    for (int b = 0; b < B; ++b) Pl[s][b] = pl[b];
+                }
+                has = true;
             }
-            continue;
         }
-        ++j;
-        {
+        if (!__any_sync(kFull, has)) break;
+        if (!has) continue;
+        if (j < n) {
+            ++j;
             const int num = j - dmax - 1;
             const int target = num < 0 ? 0 : min(num >> 5, wmax);
             if (target > wlo) {
@@ -146,19 +138,38 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
 #pragma unroll
                 for (int b = 0; b < B; ++b) Pl[WB - 1][b] = pl[b];
             }
+            T += 1;
+            const int c = c_next;
+            if (j < n) c_next = __ldg(tc + j);
+            uint32_t x[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) x[b] = ((c >> b) & 1) ? 0u : kFull;
+            uint32_t ph_in = 1u, mh_in = 0u;
+#pragma unroll
+            for (int s = 0; s < WB; ++s) {
+                uint32_t eq = Pl[s][0] ^ x[0];
+#pragma unroll
+                for (int b = 1; b < B; ++b) eq &= Pl[s][b] ^ x[b];
+                bv_word(eq, Pv[s], Mv[s], ph_in, mh_in, one, two);
+            }
         }
-        T += 1;
-        const int c = __ldg(tc + j - 1);
-        uint32_t x[B];
+        if (j == n) {
+            // T = D[32 wlo][n] (exactly n while the window still starts at row 0)
+            int d = T;
 #pragma unroll
-        for (int b = 0; b < B; ++b) x[b] = ((c >> b) & 1) ? 0u : kFull;
-        uint32_t ph_in = 1u, mh_in = 0u;
-#pragma unroll
-        for (int s = 0; s < WB; ++s) {
-            uint32_t eq = Pl[s][0] ^ x[0];
-#pragma unroll
-            for (int b = 1; b < B; ++b) eq &= Pl[s][b] ^ x[b];
-            bv_word(eq, Pv[s], Mv[s], ph_in, mh_in);
+            for (int s = 0; s < WB; ++s) {
+                const int rem = m - 32 * (wlo + s);
+                const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                d += __popc(Pv[s] & mk) - __popc(Mv[s] & mk);
+            }
+            if (full || d <= KW) {
+                a.d_out[p] = d;
+                a.k_used[p] = full ? max(m, n) : KW;
+            } else {
+                a.k_cur[p] = 2 * KW + 1;
+                a.next_list[atomicAdd(a.next_count, 1)] = p;
+            }
+            has = false;
         }
     }
 }
@@ -346,14 +357,16 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
                                                             nb, ctx->dev_err);
         ctx->launches += 2;
         BandArgs a{s->planes, s->codes, s->offs, pairs, blist, boff, bcount, bcounter, k_cur, d_out, k_used_out,
-                   nxt, nxt_count, 0};
+                   nxt, nxt_count, 0, 1u, 2u};
         {
             ProfScope prof(ctx, st);
-            for (int b = 0; b <= last; ++b) {
-                a.bucket = b;
-                launch[b](a, ctx->sm_count * occ[s->alphabet][b], st);
-                ++ctx->launches;
-            }
+            e = run_concurrent(ctx, st, last + 1, [&](int b, cudaStream_t s2) {
+                BandArgs ab = a;
+                ab.bucket = b;
+                launch[b](ab, ctx->sm_count * occ[s->alphabet][b], s2);
+            });
+            ctx->launches += last + 1;
+            if (e != cudaSuccess) return cuda_check(ctx, e, "band launch");
         }
         cur = nxt;
         cur_count = nxt_count;

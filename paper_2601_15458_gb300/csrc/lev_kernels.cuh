@@ -44,6 +44,7 @@ struct LevArgs {
     int32_t *d_out;
     int32_t *err;
     int32_t bucket;
+    uint32_t one, two;        // 1 and 2, as runtime values (see bv_word)
 };
 
 // 32 match bits of the query for rows 32k+1 .. 32k+32 and every symbol c.
@@ -81,8 +82,37 @@ __device__ __forceinline__ uint32_t match_mask(const uint32_t (&pl)[B], uint32_t
 // One 32-row word of one column.  ph_in/mh_in: top bits of the previous
 // word's Ph/Mh (row 0: ph_in = 1, mh_in = 0); they are replaced by this
 // word's top bits on return.
+//
+// The carry of the addition into the word's first row equals mh_in, and it
+// is folded into Eq for the addition only (Xh of the first row is
+// Eq | Mh[row above]; Xv keeps the plain Eq).  The adds, the shifts by one
+// and the top-bit extractions are issued as integer multiply-adds
+// (x * 1 + y, x * 2 + b, hi(x * 2)) with the factors in registers, so that
+// they run on the FMA pipe beside the logic ops on the ALU pipe.  Three
+// variants are kept for measurement (MSA_BV_VARIANT): 0 (default) all ALU;
+// 1 also the top bits as hi(x * 2); 2 add and shifts by one on the FMA pipe.
+// Measured on GB300 (2,000 x 1,500 all pairs): 48.9 / 45.4 / 47.5 TCUPS:
+// the multiply-adds lengthen the carry chain more than they relieve the
+// ALU pipe at the occupancy the register arrays allow.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t imul_hi(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+#ifndef MSA_BV_VARIANT
+#define MSA_BV_VARIANT 0
+#endif
+
 __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv, uint32_t &ph_in,
-                                        uint32_t &mh_in) {
+                                        uint32_t &mh_in, uint32_t one, uint32_t two) {
+#if MSA_BV_VARIANT == 0
+    // all logic, adds and shifts on the ALU pipe
     const uint32_t sum = (eq & pv) + pv + mh_in;
     const uint32_t xh = (sum ^ pv) | eq;
     const uint32_t ph = mv | ~(xh | pv);
@@ -91,9 +121,31 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
     const uint32_t mhs = (mh << 1) | mh_in;
     ph_in = ph >> 31;
     mh_in = mh >> 31;
-    const uint32_t xv = eq | mv;
-    pv = mhs | ~(xv | phs);
-    mv = phs & xv;
+#elif MSA_BV_VARIANT == 1
+    // adds, shifts and top-bit extractions as integer multiply-adds
+    const uint32_t eqc = eq | mh_in;
+    const uint32_t sum = imad(eqc & pv, one, pv);
+    const uint32_t xh = (sum ^ pv) | eqc;
+    const uint32_t ph = mv | ~(xh | pv);
+    const uint32_t mh = pv & xh;
+    const uint32_t phs = imad(ph, two, ph_in);
+    const uint32_t mhs = imad(mh, two, mh_in);
+    ph_in = imul_hi(ph, two);
+    mh_in = imul_hi(mh, two);
+#else
+    // the add and the two shifts by one as multiply-adds, top bits by shifts
+    const uint32_t eqc = eq | mh_in;
+    const uint32_t sum = imad(eqc & pv, one, pv);
+    const uint32_t xh = (sum ^ pv) | eqc;
+    const uint32_t ph = mv | ~(xh | pv);
+    const uint32_t mh = pv & xh;
+    const uint32_t phs = imad(ph, two, ph_in);
+    const uint32_t mhs = imad(mh, two, mh_in);
+    ph_in = ph >> 31;
+    mh_in = mh >> 31;
+#endif
+    pv = mhs | ~(eq | mv | phs);
+    mv = phs & (eq | mv);
 }
 
 __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
@@ -112,6 +164,7 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
     uint32_t *sPeq = smem + (threadIdx.x >> 5) * (WC * SIGMA);
+    const uint32_t one = a.one, two = a.two;
     const int ntasks = a.bcount[a.bucket];
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
@@ -131,17 +184,51 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
         const int cbeg = a.qstart[q];
         const int cnt = a.qstart[q + 1] - cbeg;
 
+        // warp-synchronous stream: every iteration starts with a vote over
+        // the whole warp, so lanes that switch targets rejoin the others
+        // before the next column instead of running it separately
         uint32_t Pv[WC], Mv[WC];
 #pragma unroll
         for (int k = 0; k < WC; ++k) {
             Pv[k] = kFull;
             Mv[k] = 0u;
         }
-        int n = 0, j = 0, pid = -1;
+        int n = 0, j = 0, pid = -1, c_next = 0;
+        bool has = false, more = true;
         const uint8_t *tc = nullptr;
         while (true) {
-            if (j == n) {
-                if (pid >= 0) {
+            if (!has && more) {
+                const int idx = atomicAdd(a.qcursor + q, 1);
+                if (idx >= cnt) {
+                    more = false;
+                } else {
+                    const int t = a.sorted_t[cbeg + idx];
+                    pid = a.sorted_p[cbeg + idx];
+                    const int64_t tp = a.offs[t];
+                    n = (int)(a.offs[t + 1] - tp);
+                    tc = a.codes + tp;
+                    j = 0;
+                    c_next = n > 0 ? __ldg(tc) : 0;
+#pragma unroll
+                    for (int k = 0; k < WC; ++k) {
+                        Pv[k] = kFull;
+                        Mv[k] = 0u;
+                    }
+                    has = true;
+                }
+            }
+            if (!__any_sync(kFull, has)) break;
+            if (has) {
+                if (j < n) {
+                    const int c = c_next;
+                    if (j + 1 < n) c_next = __ldg(tc + j + 1);
+                    const uint32_t *row = sPeq + c;
+                    uint32_t ph_in = 1u, mh_in = 0u;
+#pragma unroll
+                    for (int k = 0; k < WC; ++k) bv_word(row[k * SIGMA], Pv[k], Mv[k], ph_in, mh_in, one, two);
+                    ++j;
+                }
+                if (j == n) {
                     int d = n;
 #pragma unroll
                     for (int k = 0; k < WC; ++k) {
@@ -150,27 +237,9 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
                         d += __popc(Pv[k] & mk) - __popc(Mv[k] & mk);
                     }
                     a.d_out[pid] = d;
+                    has = false;
                 }
-                const int idx = atomicAdd(a.qcursor + q, 1);
-                if (idx >= cnt) break;
-                const int t = a.sorted_t[cbeg + idx];
-                pid = a.sorted_p[cbeg + idx];
-                const int64_t tp = a.offs[t];
-                n = (int)(a.offs[t + 1] - tp);
-                tc = a.codes + tp;
-                j = 0;
-#pragma unroll
-                for (int k = 0; k < WC; ++k) {
-                    Pv[k] = kFull;
-                    Mv[k] = 0u;
-                }
-                continue;
             }
-            const uint32_t *row = sPeq + __ldg(tc + j);
-            uint32_t ph_in = 1u, mh_in = 0u;
-#pragma unroll
-            for (int k = 0; k < WC; ++k) bv_word(row[k * SIGMA], Pv[k], Mv[k], ph_in, mh_in);
-            ++j;
         }
     }
 }
@@ -196,6 +265,7 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
     int32_t *ring_p = ring_t + kRing;
     int32_t *ring_n = ring_p + kRing;
     volatile int32_t *end_step = ring_n + kRing;
+    const uint32_t one = a.one, two = a.two;
     const int ntasks = a.bcount[a.bucket];
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
@@ -275,7 +345,8 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
                     uint32_t mh_in = lane == 0 ? 0u : (uint32_t)((msg_in >> 1) & 1);
                     const uint32_t *col = sPeq + c * 32 + lane;
 #pragma unroll
-                    for (int w = 0; w < WPL; ++w) bv_word(col[w * SIGMA * 32], Pv[w], Mv[w], ph_in, mh_in);
+                    for (int w = 0; w < WPL; ++w)
+                        bv_word(col[w * SIGMA * 32], Pv[w], Mv[w], ph_in, mh_in, one, two);
                     msg = (int)(ph_in | (mh_in << 1));
                     ++j;
                     if (j == n) {

@@ -40,6 +40,12 @@ struct msa_ctx {
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     double prof_ms = 0.0;
+    // side streams for running independent bucket kernels concurrently
+    // (fork / join through events, so stream capture still works)
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kSide] = {};
 };
 
 namespace msa {
@@ -94,6 +100,31 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
 msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const void *out,
                         const char *who);
 int64_t lev_workspace(int64_t P, int32_t n);
+msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
+                  int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
+                  int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                  cudaStream_t st);
+
+// Runs launch(i, stream) for i < count, spread over the context's side
+// streams after a fork from `st`, and makes `st` wait for all of them.
+template <class F>
+cudaError_t run_concurrent(msa_ctx *ctx, cudaStream_t st, int count, F launch) {
+    if (count <= 1 || !ctx->fork_ev) {
+        for (int i = 0; i < count; ++i) launch(i, st);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    const int used = count < msa_ctx::kSide ? count : msa_ctx::kSide;
+    for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < count; ++i) launch(i, ctx->side[i % used]);
+    for (int k = 0; k < used && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(ctx->join_ev[k], ctx->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[k], 0);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
 inline int bits_of(int alphabet) { return alphabet == MSA_DNA ? 2 : 5; }
 inline int sigma_of(int alphabet) { return alphabet == MSA_DNA ? 4 : 20; }

@@ -213,6 +213,41 @@ int64_t nw_slab_bytes(int max_len) {
     return brow + (tbw + 255) / 256 * 256;
 }
 
+msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
+                  int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
+                  int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                  cudaStream_t st) {
+    if (P < 0 || P >= (int64_t(1) << 31) || n_seqs < 0 || max_len < 0 || total < 0)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: negative or oversized count");
+    if (P == 0) return MSA_OK;
+    if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: null pointer");
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_kernel, kNwWarps * 32, 0);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "nw occupancy");
+        if (occ < 1) occ = 1;
+    }
+    int32_t *counter = ar.take<int32_t>(64);
+    const int64_t slab = nw_slab_bytes(max_len);
+    const int64_t avail = counter ? ar.cap - ar.used : 0;
+    int64_t warps = std::min<int64_t>((int64_t)ctx->sm_count * occ * kNwWarps, avail / slab);
+    warps = std::min<int64_t>(warps, ((P + kNwWarps - 1) / kNwWarps) * kNwWarps);
+    warps = warps / kNwWarps * kNwWarps;
+    if (warps < kNwWarps)
+        return set_error(ctx, MSA_ENOMEM, "msa_nw_align_batch: max_len %d needs %lld workspace bytes per warp group",
+                         max_len, (long long)(slab * kNwWarps + 256));
+    char *slabs = ar.take<char>(warps * slab);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
+    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, gap, score_out, ops_out, ops_off,
+             ops_len_out, slabs, slab, max_len, counter, ctx->dev_err};
+    ProfScope prof(ctx, st);
+    nw_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a);
+    ++ctx->launches;
+    return cuda_check(ctx, cudaGetLastError(), "nw launch");
+}
+
 }  // namespace msa
 
 using namespace msa;
@@ -228,35 +263,9 @@ msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t 
                               int32_t mismatch, int32_t gap, int32_t *score_out, uint8_t *ops_out,
                               const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
     if (!ctx) return MSA_EINVAL;
-    if (P < 0 || P >= (int64_t(1) << 31) || n_seqs < 0 || max_len < 0 || total < 0)
-        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: negative or oversized count");
-    if (P == 0) return MSA_OK;
-    if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
-        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: null pointer");
-    cudaStream_t st = (cudaStream_t)stream;
-    static int occ = 0;
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_kernel, kNwWarps * 32, 0);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "nw occupancy");
-        if (occ < 1) occ = 1;
-    }
-    const int64_t slab = nw_slab_bytes(max_len);
-    const int64_t avail = ctx->ws_bytes - 256;
-    int64_t warps = std::min<int64_t>((int64_t)ctx->sm_count * occ * kNwWarps, avail / slab);
-    warps = std::min<int64_t>(warps, ((P + kNwWarps - 1) / kNwWarps) * kNwWarps);
-    warps = warps / kNwWarps * kNwWarps;
-    if (warps < kNwWarps)
-        return set_error(ctx, MSA_ENOMEM, "msa_nw_align_batch: max_len %d needs %lld workspace bytes per warp group",
-                         max_len, (long long)(slab * kNwWarps + 256));
-    int32_t *counter = reinterpret_cast<int32_t *>(ctx->ws);
-    cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
-    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, gap, score_out, ops_out, ops_off,
-             ops_len_out, ctx->ws + 256, slab, max_len, counter, ctx->dev_err};
-    ProfScope prof(ctx, st);
-    nw_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a);
-    ++ctx->launches;
-    return cuda_check(ctx, cudaGetLastError(), "nw launch");
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    return nw_run(ctx, ar, codes, offs, n_seqs, total, max_len, pairs, P, match, mismatch, gap, score_out, ops_out,
+                  ops_off, ops_len_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,108 @@
+"""Learned band proposer pipeline (A8-A10): training data from the exact
+kernels, the training loop, and the band-width margin choice.
+
+The network only proposes the starting band of ``msa_lev_banded_batch``;
+the band's certificate (accept d_k only when d_k <= k, else double k) keeps
+every distance exact whatever the network predicts.  All arithmetic runs in
+the library's kernels; this module only orders the calls.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import api, synth
+
+
+def training_set(ctx: api.Context, seed: int = 4, n_per_tree: int = 710,
+                 scales=(0.1, 0.25, 0.5, 1.0), root_len: int = 1500):
+    """Exact distances on DNA simulated down Yule trees (the 2,000-sequence
+    workload's recipe, root length 1,500, per-branch substitution
+    U(0.005, 0.05) x scale, indels 0.2x), all pairs of each tree.
+
+    The rate scales spread the targets y = f / max(m, n) over the range of
+    the evaluation pairs (close relatives are rare among all pairs of one
+    tree).  Four trees of 710 leaves give 1,006,780 pairs.
+    Returns ``(X bf16 [N, 256], y fp32 [N], info)`` on the device.
+    """
+    Xs, ys = [], []
+    t0 = time.perf_counter()
+    for i, sc in enumerate(scales):
+        ds = synth.tree_dna(seed=seed * 100 + i, n=n_per_tree, root_len=root_len,
+                            sub_lo=0.005 * sc, sub_hi=0.05 * sc)
+        sq = api.upload_and_pack(ctx, ds)
+        prof = api.kmer_profile(ctx, sq)
+        pairs = torch.from_numpy(synth.all_pairs(ds.n)).cuda()
+        Xs.append(api.pair_features(ctx, sq, prof, pairs))
+        d = api.lev_batch(ctx, sq, pairs)
+        lens = torch.from_numpy(np.diff(ds.offs)).cuda()
+        mx = torch.maximum(lens[pairs[:, 0].long()], lens[pairs[:, 1].long()]).clamp(min=1)
+        ys.append((d.double() / mx.double()).float())
+    ctx.check()
+    X, y = torch.cat(Xs), torch.cat(ys)
+    return X, y, dict(pairs=int(y.numel()), seconds=time.perf_counter() - t0)
+
+
+def train(ctx: api.Context, X: torch.Tensor, y: torch.Tensor, epochs: float = 4.0, batch: int = 4096,
+          lr: float = 1e-3, tau: float = 0.9, seed: int = 0, val_frac: float = 0.1):
+    """Adam on the pinball loss, minibatches drawn by a seeded permutation.
+
+    Returns ``(model, info)`` with the validation loss and the validation row
+    indices (a held-out 10% that training never sees).
+    """
+    rng = np.random.default_rng(seed)
+    N = y.numel()
+    perm = rng.permutation(N)
+    nval = int(N * val_frac)
+    val_idx, tr_idx = perm[:nval], perm[nval:]
+    model = api.BandModel(ctx, seed=seed)
+    steps = max(1, int(epochs * len(tr_idx) / batch))
+    t0 = time.perf_counter()
+    order = rng.permutation(tr_idx)
+    pos = 0
+    idx_dev = torch.empty(batch, dtype=torch.int32, device="cuda")
+    losses = []
+    for s in range(steps):
+        if pos + batch > len(order):
+            order = rng.permutation(tr_idx)
+            pos = 0
+        idx_dev.copy_(torch.from_numpy(order[pos:pos + batch].astype(np.int32)))
+        pos += batch
+        loss = model.train_step(X, y, idx_dev, lr=lr, tau=tau)
+        if s % 50 == 0 or s == steps - 1:
+            losses.append(loss)
+    ctx.check()
+    t_train = time.perf_counter() - t0
+    # validation loss: gradient-only steps over the held-out rows
+    vl = []
+    for c0 in range(0, nval, batch):
+        vi = torch.from_numpy(val_idx[c0:c0 + batch].astype(np.int32)).cuda()
+        vl.append(model.train_step(X, y, vi, lr=0.0, tau=tau).item() * vi.numel())
+        model.read_grad()
+    info = dict(steps=steps, batch=batch, seconds=t_train, train_loss=[float(v) for v in losses[-3:]],
+                val_loss=sum(vl) / max(1, nval), val_idx=val_idx)
+    return model, info
+
+
+def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof: torch.Tensor,
+               pairs: torch.Tensor, candidates=(0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 2):
+    """The band margin gamma with the fastest certified banded run on a
+    validation batch (timed with CUDA events; all candidates are exact)."""
+    best, best_t = candidates[0], float("inf")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for g in candidates:
+        _, k = model.predict_band(seqs, prof, pairs, gamma=g, margin=margin)
+        api.lev_banded_batch(ctx, seqs, pairs, k)
+        ts = []
+        for _ in range(reps):
+            ev0.record()
+            api.lev_banded_batch(ctx, seqs, pairs, k)
+            ev1.record()
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        t = min(ts)
+        if t < best_t:
+            best, best_t = g, t
+    return best, best_t

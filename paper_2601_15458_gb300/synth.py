@@ -64,6 +64,8 @@ def _codes(seq: np.ndarray, alphabet: bytes) -> np.ndarray:
 
 def random_seq(rng, length: int, probs: np.ndarray) -> np.ndarray:
     """``length`` symbol codes drawn i.i.d. from ``probs``."""
+    if np.all(probs == probs[0]):
+        return rng.integers(0, len(probs), size=length).astype(np.uint8)
     return rng.choice(len(probs), size=length, p=probs).astype(np.uint8)
 
 
@@ -73,10 +75,12 @@ def mutate(rng, seq: np.ndarray, sub_rate: float, indel_rate: float, probs: np.n
     Each site is substituted with probability ``sub_rate`` by a symbol drawn
     from the background ``probs`` conditioned on differing from the current
     one.  Independently, an indel event starts at a site with probability
-    ``indel_rate``; it is an insertion (of background symbols) or a deletion
-    with probability 1/2 each, of length Geometric(p=0.5) on {1, 2, ...}.
+    ``indel_rate``; it is an insertion or a deletion with probability 1/2
+    each, of length Geometric(p=0.5) on {1, 2, ...}.  A deletion at site i of
+    length L removes sites i .. i+L-1 (overlapping deletions remove their
+    union); an insertion at site i puts L background symbols before site i
+    (several at one site are concatenated, the site itself may be deleted).
     """
-    k = len(probs)
     out = seq.copy()
     n = len(out)
     if n == 0:
@@ -84,7 +88,6 @@ def mutate(rng, seq: np.ndarray, sub_rate: float, indel_rate: float, probs: np.n
     sub = rng.random(n) < sub_rate
     idx = np.nonzero(sub)[0]
     if len(idx):
-        # draw from the background conditioned on != current symbol
         cur = out[idx]
         new = random_seq(rng, len(idx), probs)
         bad = new == cur
@@ -95,21 +98,31 @@ def mutate(rng, seq: np.ndarray, sub_rate: float, indel_rate: float, probs: np.n
     ev = np.nonzero(rng.random(n) < indel_rate)[0]
     if len(ev) == 0:
         return out
-    kinds = rng.random(len(ev)) < 0.5
-    lengths = rng.geometric(0.5, size=len(ev))
-    pieces = []
-    prev = 0
-    for pos, ins, L in zip(ev, kinds, lengths):
-        if pos < prev:
-            continue                      # inside a previous deletion
-        pieces.append(out[prev:pos])
-        if ins:
-            pieces.append(random_seq(rng, int(L), probs))
-            prev = pos
-        else:
-            prev = min(n, pos + int(L))
-    pieces.append(out[prev:])
-    return np.concatenate(pieces).astype(np.uint8)
+    ins = rng.random(len(ev)) < 0.5
+    lengths = rng.geometric(0.5, size=len(ev)).astype(np.int64)
+    # deletions: coverage by a difference array
+    cover = np.zeros(n + 1, np.int64)
+    dpos, dlen = ev[~ins], lengths[~ins]
+    np.add.at(cover, dpos, 1)
+    np.add.at(cover, np.minimum(dpos + dlen, n), -1)
+    keep = (np.cumsum(cover[:n]) == 0).astype(np.int64)
+    # insertions: symbols placed before their site
+    ins_at = np.zeros(n, np.int64)
+    np.add.at(ins_at, ev[ins], lengths[ins])
+    contrib = ins_at + keep
+    start = np.cumsum(contrib) - contrib
+    total = int(contrib.sum())
+    res = np.empty(total, np.uint8)
+    kept = np.nonzero(keep)[0]
+    res[start[kept] + ins_at[kept]] = out[kept]
+    tot_ins = int(ins_at.sum())
+    if tot_ins:
+        sites = np.nonzero(ins_at)[0]
+        reps = ins_at[sites]
+        base = np.repeat(start[sites], reps)
+        within = np.arange(tot_ins) - np.repeat(np.cumsum(reps) - reps, reps)
+        res[base + within] = random_seq(rng, tot_ins, probs)
+    return res
 
 
 def yule_tree(rng, n_leaves: int):
@@ -265,24 +278,59 @@ def protein_families(seed: int = 3, n_fam: int = 100, per_fam: int = 100,
             _to_seqset(roots, PROTEIN, "protein_roots", dict(background=probs)))
 
 
+_C_LIB = None
+
+
+def _c_lib():
+    """The compiled pair generator (``synth_c/synth_pairs.c``), built with gcc on first use."""
+    global _C_LIB
+    if _C_LIB is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "synth_c")
+        src, so = os.path.join(here, "synth_pairs.c"), os.path.join(here, "libsynth_pairs.so")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            tmp = so + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", src, "-o", tmp])
+            os.replace(tmp, so)
+        L = ctypes.CDLL(so)
+        L.synth_divergent_pairs.restype = ctypes.c_int32
+        L.synth_divergent_pairs.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32]
+        L.synth_compact_pairs.restype = None
+        L.synth_compact_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+        _C_LIB = L
+    return _C_LIB
+
+
 def divergent_pairs(seed: int = 40, n_pairs: int = 100000, len_lo: int = 1000,
                     len_hi: int = 10000, div_lo: float = 0.01, div_hi: float = 0.30,
-                    indel_share: float = 0.2) -> SeqSet:
+                    indel_share: float = 0.2, threads: int | None = None) -> SeqSet:
     """Independent DNA pairs: a uniform root of length U{len_lo..len_hi} and a
-    partner mutated from it at divergence delta ~ U(div_lo, div_hi), with
-    substitution rate delta and indel rate ``indel_share`` x delta.  Sequence
-    2p is the root of pair p, sequence 2p+1 its partner."""
-    rng = np.random.default_rng(seed)
-    seqs = []
-    for _ in range(n_pairs):
-        L = int(rng.integers(len_lo, len_hi + 1))
-        root = random_seq(rng, L, UNIFORM4)
-        d = float(rng.uniform(div_lo, div_hi))
-        partner = mutate(rng, root, d, indel_share * d, UNIFORM4)
-        if partner.tobytes() == root.tobytes():
-            partner = mutate(rng, root, max(d, 0.05), indel_share * d, UNIFORM4)
-        seqs += [root, partner]
-    return _to_seqset(seqs, DNA, "divergent_pairs")
+    partner mutated from it at divergence delta ~ U(div_lo, div_hi): per root
+    site an indel event with probability indel_share * delta (insertion or
+    deletion, Geometric(1/2) length), else a substitution with probability
+    delta.  Sequence 2p is the root of pair p, sequence 2p+1 its partner.
+    Generated by ``synth_c/synth_pairs.c`` (one SplitMix64 stream per pair)."""
+    import os
+    L = _c_lib()
+    slab = 3 * len_hi + 64
+    buf = np.empty(n_pairs * slab, np.uint8)
+    lens = np.zeros(2 * n_pairs, np.int32)
+    nt = threads or min(32, os.cpu_count() or 1)
+    rc = L.synth_divergent_pairs(seed, n_pairs, len_lo, len_hi, div_lo, div_hi, indel_share,
+                                 buf.ctypes.data, slab, lens.ctypes.data, nt)
+    if rc != 0:
+        raise RuntimeError("divergent_pairs: a partner overflowed its slab")
+    lens64 = lens.astype(np.int64)
+    offs = np.zeros(2 * n_pairs + 1, np.int64)
+    np.cumsum(lens64, out=offs[1:])
+    codes = np.empty(int(offs[-1]), np.uint8)
+    L.synth_compact_pairs(buf.ctypes.data, slab, lens.ctypes.data, n_pairs, offs.ctypes.data, codes.ctypes.data)
+    return SeqSet(codes, offs, "dna")
 
 
 # ---------------------------------------------------------------------------

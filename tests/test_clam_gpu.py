@@ -1,0 +1,98 @@
+"""Guide tree (Alg. 1, A11) and bottom-up merge (section "Merging", A12)
+on the GPU against the oracle: identical trees, identical MSAs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15458_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_15458_gb300 import build
+    build.build()
+    c = api.Context(0, workspace_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _gpu_nodes(tree):
+    order = tree.order.cpu().numpy()
+    out = []
+    for k in range(tree.n_nodes):
+        out.append(dict(members=sorted(int(x) for x in order[tree.lo[k]:tree.hi[k]]), center=int(tree.center[k]),
+                        left=int(tree.left[k]), right=int(tree.right[k]), parent=int(tree.parent[k])))
+    return out
+
+
+def _check_same_tree(gpu, ref):
+    assert len(gpu) == len(ref)
+    for g, r in zip(gpu, ref):
+        assert g == r
+
+
+def _full(ctx, ds):
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
+    ctx.check()
+    return sq, tree, width, score, rows.cpu().numpy()
+
+
+def test_line_metric_tree(ctx):
+    ds = synth.SeqSet.from_list([b"A" * k for k in range(1, 8)])
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    ctx.check()
+    _check_same_tree(_gpu_nodes(tree), oracle.partition(ds.seqs()))
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.small_dna(seed=1),
+                                   lambda: synth.protein_families(seed=3, n_fam=3, per_fam=30)[0]])
+def test_tree_and_msa_match_oracle(ctx, maker):
+    ds = maker()
+    seqs = ds.seqs()
+    sq, tree, width, score, rows = _full(ctx, ds)
+    ref_nodes = oracle.partition(seqs)
+    _check_same_tree(_gpu_nodes(tree), ref_nodes)
+    ref_rows, ref_order, merges = oracle.merge_tree(seqs, ref_nodes)
+    assert list(tree.order.cpu().numpy()) == ref_order
+    assert [r.tobytes() for r in rows] == ref_rows
+    for k, (sc, _) in merges.items():
+        assert score[k] == sc
+    assert width[0] == len(ref_rows[0])
+
+
+def test_larger_tree_sampled_nodes(ctx):
+    """A 1,500-sequence 16S-like set: invariants everywhere, and Alg. 1 redone
+    by the oracle on sampled clusters (including sampled-medoid ones)."""
+    ds = synth.gg16s_dna(seed=5, n=1500)
+    seqs = ds.seqs()
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    ctx.check()
+    nodes = _gpu_nodes(tree)
+    assert tree.n_nodes == 2 * ds.n - 1
+    leaves = [nd for nd in nodes if nd["left"] < 0]
+    assert sorted(nd["members"][0] for nd in leaves) == list(range(ds.n))
+    dist = oracle._default_dist(seqs)
+    rng = np.random.default_rng(0)
+    internal = [k for k, nd in enumerate(nodes) if nd["left"] >= 0]
+    big = [k for k in internal if len(nodes[k]["members"]) > 256][:2]
+    small = list(rng.choice([k for k in internal if 2 <= len(nodes[k]["members"]) <= 40], 6, replace=False))
+    for k in big + small:
+        nd = nodes[k]
+        c, l, r, L, R = oracle.partition_step(nd["members"], dist)
+        assert nd["center"] == c
+        assert nodes[nd["left"]]["members"] == L and nodes[nd["right"]]["members"] == R
+    # merge: rows de-gap to their sequences, equal widths
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0])).cpu().numpy()
+    ctx.check()
+    order = tree.order.cpu().numpy()
+    for r in rng.choice(ds.n, 50, replace=False):
+        assert rows[r].tobytes().replace(b"-", b"") == seqs[order[r]]
+    assert not np.any(np.all(rows == ord("-"), axis=0))

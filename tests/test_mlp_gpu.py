@@ -1,0 +1,168 @@
+"""Learned band proposer (A8-A10): features bit-exact, network forward and
+gradients against the float64 oracle, Adam against its closed form, and the
+trained proposer's gain over the plain full DP with every distance exact."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_15458_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_15458_gb300 import build
+    build.build()
+    c = api.Context(0, workspace_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _bf16_of(t):
+    return t.view(torch.int16).cpu().numpy().view(np.uint16)
+
+
+def test_kmer_profiles_exact(ctx):
+    rng = np.random.default_rng(1)
+    seqs = [rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes() for L in (0, 1, 3, 4, 5, 33, 1000, 4097)]
+    ds = synth.SeqSet.from_list(seqs + synth.small_dna(seed=1, n=20).seqs())
+    sq = api.upload_and_pack(ctx, ds)
+    prof = api.kmer_profile(ctx, sq)
+    ctx.check()
+    got = prof.cpu().numpy().view(np.uint16)
+    for i in range(ds.n):
+        np.testing.assert_array_equal(got[i], oracle.kmer_counts(ds.seq(i)))
+
+
+def test_pair_features_exact(ctx):
+    ds = synth.tree_dna(seed=11, n=30, root_len=900)
+    sq = api.upload_and_pack(ctx, ds)
+    prof = api.kmer_profile(ctx, sq)
+    pairs = synth.random_pairs(2, ds.n, 50)
+    X = api.pair_features(ctx, sq, prof, pairs)
+    ctx.check()
+    got = _bf16_of(X)
+    lens = np.diff(ds.offs)
+    for p, (a, b) in enumerate(pairs):
+        ref = oracle.pair_feature(oracle.kmer_counts(ds.seq(a)), oracle.kmer_counts(ds.seq(b)), lens[a], lens[b])
+        np.testing.assert_array_equal(got[p], oracle.bf16_bits(ref))
+
+
+def _features(ctx, n=60, seed=12):
+    ds = synth.tree_dna(seed=seed, n=n, root_len=1200)
+    sq = api.upload_and_pack(ctx, ds)
+    prof = api.kmer_profile(ctx, sq)
+    pairs = synth.all_pairs(ds.n)
+    X = api.pair_features(ctx, sq, prof, pairs)
+    d = api.lev_batch(ctx, sq, pairs)
+    ctx.check()
+    lens = np.diff(ds.offs)
+    y = d.cpu().numpy() / np.maximum(lens[pairs[:, 0]], lens[pairs[:, 1]])
+    return X, y.astype(np.float32)
+
+
+def _oracle_params(p):
+    return dict(W1=p["W1"].T.astype(np.float64), b1=p["b1"], W2=p["W2"].T.astype(np.float64), b2=p["b2"],
+                W3=p["W3"].reshape(64, 1).astype(np.float64), b3=p["b3"])
+
+
+def test_forward_matches_oracle(ctx):
+    X, _ = _features(ctx)
+    model = api.BandModel(ctx, seed=3)
+    yh = model.forward(X)
+    ctx.check()
+    Xf = X.float().cpu().numpy()
+    ref, _ = oracle.mlp_forward(_oracle_params(model.params()), Xf)
+    got = yh.cpu().numpy()
+    # fp32 accumulation vs float64: a hidden value near a bf16 rounding tie may
+    # land one bf16 step apart, so compare with a tolerance scaled to the outputs
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(got - ref)) <= 2e-2 * scale
+    assert np.median(np.abs(got - ref)) <= 1e-3 * scale
+
+
+def test_gradients_match_oracle(ctx):
+    X, y = _features(ctx)
+    B = 512
+    idx = torch.arange(B, dtype=torch.int32, device="cuda")
+    model = api.BandModel(ctx, seed=4)
+    yt = torch.from_numpy(y).cuda()
+    loss = model.train_step(X, yt, idx, lr=0.0, tau=0.9)
+    G = model.read_grad()
+    ctx.check()
+    Xf = X[:B].float().cpu().numpy()
+    op = _oracle_params(model.params())
+    yh, cache = oracle.mlp_forward(op, Xf)
+    ref_loss, dy = oracle.pinball_loss(yh, y[:B].astype(np.float64), 0.9)
+    R = oracle.mlp_backward(cache, dy)
+    assert abs(loss.item() - ref_loss) <= 1e-3 * max(1e-6, abs(ref_loss)) + 1e-6
+    ref = dict(W1=R["W1"].T, b1=R["b1"], W2=R["W2"].T, b2=R["b2"], W3=R["W3"][:, 0], b3=R["b3"])
+    for k in ref:
+        num = np.linalg.norm(G[k].astype(np.float64) - ref[k])
+        den = np.linalg.norm(ref[k]) + 1e-12
+        assert num / den <= 1e-2, (k, num / den)
+
+
+def test_adam_step_matches_closed_form(ctx):
+    X, y = _features(ctx)
+    idx = torch.arange(256, dtype=torch.int32, device="cuda")
+    model = api.BandModel(ctx, seed=5)
+    p0 = model.params()
+    yt = torch.from_numpy(y).cuda()
+    model.train_step(X, yt, idx, lr=0.0)
+    g = model.read_grad()
+    model.train_step(X, yt, idx, lr=1e-3)
+    p1 = model.params()
+    ctx.check()
+    zero = {k: np.zeros_like(v, dtype=np.float64) for k, v in p0.items()}
+    exp, _, _ = oracle.adam_step({k: v.astype(np.float64) for k, v in p0.items()},
+                                 {k: v.astype(np.float64) for k, v in g.items()}, dict(zero), dict(zero), t=1, lr=1e-3)
+    for k in p0:
+        np.testing.assert_allclose(p1[k], exp[k], rtol=1e-5, atol=1e-6)
+
+
+def test_band_policy_and_learned_gain(ctx):
+    # train on exact distances of tree-simulated DNA, evaluate on fresh pairs
+    from paper_2601_15458_gb300 import learned_band
+    X, y, _ = learned_band.training_set(ctx, seed=21, n_per_tree=150)
+    model, info = learned_band.train(ctx, X, y, epochs=12, batch=1024, lr=2e-3)
+    assert info["val_loss"] < 0.05
+    ev = synth.divergent_pairs(seed=40, n_pairs=20000, len_lo=1000, len_hi=3000, div_lo=0.01, div_hi=0.15)
+    sq = api.upload_and_pack(ctx, ev)
+    prof = api.kmer_profile(ctx, sq)
+    pairs = np.stack([np.arange(0, ev.n, 2), np.arange(1, ev.n, 2)], 1).astype(np.int32)
+    yhat, k = model.predict_band(sq, prof, pairs, gamma=0.1, margin=8)
+    ctx.check()
+    lens = np.diff(ev.offs)
+    mx = np.maximum(lens[pairs[:, 0]], lens[pairs[:, 1]]).astype(np.float32)
+    yh = yhat.cpu().numpy()
+    kf = np.ceil(np.float32(1.1) * np.maximum(yh, np.float32(0)) * mx).astype(np.int64) + 8
+    kref = np.maximum(np.abs(lens[pairs[:, 0]] - lens[pairs[:, 1]]), kf)
+    np.testing.assert_array_equal(k.cpu().numpy(), kref)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    pt = torch.from_numpy(pairs).cuda()
+    d_full = api.lev_batch(ctx, sq, pt)
+    d_band, k_used = api.lev_banded_batch(ctx, sq, pt, k)
+    ctx.check()
+    np.testing.assert_array_equal(d_band.cpu().numpy(), d_full.cpu().numpy())
+    sample = pairs[:60]
+    np.testing.assert_array_equal(d_full.cpu().numpy()[:60], oracle.lev_pairs(ev.arena, ev.offs, sample))
+    t_full = timed(lambda: api.lev_batch(ctx, sq, pt))
+    t_band = timed(lambda: api.lev_banded_batch(ctx, sq, pt, k))
+    # what the network gains over the method without it (the plain full DP)
+    assert t_band * 1.5 < t_full, (t_band, t_full)
