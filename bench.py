@@ -156,7 +156,7 @@ def band_bench(ctx, args, stream):
     import torch
     from paper_2601_15458_gb300 import api, learned_band, synth
     t0 = time.perf_counter()
-    X, y, tinfo = learned_band.training_set(ctx, seed=4, n_per_tree=710)
+    X, y, tinfo = learned_band.training_set(ctx, seed=4)
     model, minfo = learned_band.train(ctx, X, y, epochs=8, batch=4096, lr=2e-3, tau=0.9)
     del X, y
     # the band margin is picked on held-out pairs of another seed, never on the evaluation pairs

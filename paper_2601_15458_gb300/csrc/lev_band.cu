@@ -21,8 +21,12 @@
 // above the window are taken to grow by +1 per column (exact for row 0, an
 // upper bound elsewhere), which is the carry-in of the window's top word; the
 // rows below it start from the +1 vertical deltas of a fresh word, also an
-// upper bound.  The window covers the band of half-width
-// k_w = 32 (WB - 1) - 1, so an accepted pair is certified for k_w >= k.
+// upper bound.  The window moves at warp-uniform points (every 32 steps of
+// the warp's loop, each lane by as many words as its band has moved), so
+// lanes never run the move separately, and the planes of the next word to
+// enter are loaded one move ahead.  Trailing the band by at most one word,
+// the window covers the band of half-width k_w = 32 (WB - 2) - 1, so an
+// accepted pair is certified for k_w >= k.
 // At the end D[m][n] = T + popc(Pv) - popc(Mv) over the window's rows <= m.
 #include <cuda_runtime.h>
 
@@ -41,7 +45,10 @@ constexpr int kBandRounds = 8;
 // protein (5 bit planes per word) up to 16 words (k_w 479)
 static int band_buckets(int alphabet) { return alphabet == MSA_DNA ? 12 : 9; }
 
-__host__ __device__ __forceinline__ int band_kw(int WB) { return 32 * (WB - 1) - 1; }
+// The window may trail its ideal position by one word between two moves
+// (moves happen at warp-uniform points, every 32 steps), so a window of WB
+// words covers the band of half-width 32 (WB - 2) - 1.
+__host__ __device__ __forceinline__ int band_kw(int WB) { return 32 * (WB - 2) - 1; }
 
 struct BandArgs {
     const uint32_t *planes;
@@ -66,17 +73,17 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
     const int cnt = a.bcount[a.bucket];
     const int32_t *list = a.blist + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
-    constexpr int KW = 32 * (WB - 1) - 1;
+    constexpr int KW = 32 * (WB - 2) - 1;
     const uint32_t one = a.one, two = a.two;
-    uint32_t Pv[WB], Mv[WB], Pl[WB][B];
+    uint32_t Pv[WB], Mv[WB], Pl[WB][B], Pn[B];
     // per-lane pair state; a warp-synchronous loop (a vote over the whole
     // warp each iteration) so that lanes with pairs of different lengths and
-    // window phases rejoin before every column
+    // band positions rejoin before every column
     int p = -1, m = 0, n = 0, j = 0, wlo = 0, wmax = 0, dmax = 0, T = 0, c_next = 0;
     bool full = true, has = false, more = true;
     int64_t qa = 0;
     const uint8_t *tc = nullptr;
-    while (true) {
+    for (uint32_t it = 0;; ++it) {
         if (!has && more) {
             const int k = atomicAdd(counter, 1);
             if (k >= cnt) {
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
                 n = (int)(tb - ta);
                 const int W = max(1, (m + 31) / 32);
                 full = W <= WB;                        // the window holds the whole column: plain DP
-                dmax = (n - m + KW) >> 1;              // floor((n - m + k_w) / 2), may be negative
+                dmax = (n - m + KW) >> 1;              // floor((n - m + k_w) / 2), >= 0 since k_w >= m - n
                 wmax = full ? 0 : W - WB;
                 tc = a.codes + ta;
                 wlo = 0;
@@ -111,16 +118,20 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
 #pragma unroll
                     for (int b = 0; b < B; ++b) Pl[s][b] = pl[b];
                 }
+                {
+                    uint32_t mask;
+                    query_planes<B>(a.planes, qa, m, WB, Pn, mask);
+                }
                 has = true;
             }
         }
         if (!__any_sync(kFull, has)) break;
-        if (!has) continue;
-        if (j < n) {
-            ++j;
-            const int num = j - dmax - 1;
+        // warp-uniform window moves: every 32 iterations each lane catches its
+        // window up with the band's first row for its next column
+        if ((it & 31u) == 0u && has && !full) {
+            const int num = j - dmax;            // next column is j + 1
             const int target = num < 0 ? 0 : min(num >> 5, wmax);
-            if (target > wlo) {
+            while (wlo < target) {
                 T += __popc(Pv[0]) - __popc(Mv[0]);
 #pragma unroll
                 for (int s = 0; s < WB - 1; ++s) {
@@ -132,12 +143,15 @@ __global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
                 ++wlo;
                 Pv[WB - 1] = kFull;
                 Mv[WB - 1] = 0u;
-                uint32_t mask;
-                uint32_t pl[B];
-                query_planes<B>(a.planes, qa, m, wlo + WB - 1, pl, mask);
 #pragma unroll
-                for (int b = 0; b < B; ++b) Pl[WB - 1][b] = pl[b];
+                for (int b = 0; b < B; ++b) Pl[WB - 1][b] = Pn[b];
+                uint32_t mask;
+                query_planes<B>(a.planes, qa, m, wlo + WB, Pn, mask);   // one move ahead
             }
+        }
+        if (!has) continue;
+        if (j < n) {
+            ++j;
             T += 1;
             const int c = c_next;
             if (j < n) c_next = __ldg(tc + j);

@@ -16,33 +16,39 @@ import torch
 from . import api, synth
 
 
-def training_set(ctx: api.Context, seed: int = 4, n_per_tree: int = 710,
-                 scales=(0.1, 0.25, 0.5, 1.0), root_len: int = 1500):
+def training_set(ctx: api.Context, seed: int = 4, n_per_tree: int = 334,
+                 root_lens=(1000, 2000, 3500, 5500, 8000, 10000), scales=(0.1, 0.3, 1.0)):
     """Exact distances on DNA simulated down Yule trees (the 2,000-sequence
-    workload's recipe, root length 1,500, per-branch substitution
-    U(0.005, 0.05) x scale, indels 0.2x), all pairs of each tree.
+    workload's recipe: per-branch substitution U(0.005, 0.05) x scale,
+    indels 0.2x), all pairs of each tree.
 
-    The rate scales spread the targets y = f / max(m, n) over the range of
-    the evaluation pairs (close relatives are rare among all pairs of one
-    tree).  Four trees of 710 leaves give 1,006,780 pairs.
-    Returns ``(X bf16 [N, 256], y fp32 [N], info)`` on the device.
+    The grid of root lengths and rate scales spreads the training pairs over
+    the lengths and divergences of the evaluation pairs (one tree of fixed
+    length has few close relatives among its pairs, and 4-mer count
+    differences shrink relative to length as sequences grow).  With the
+    defaults, 18 trees of 334 leaves give 999,702 pairs.
+    Returns ``(X bf16 [N, 256], y fp32 [N], info)`` on the device, with
+    y = f(a, b) / max(m, n).
     """
     Xs, ys = [], []
     t0 = time.perf_counter()
-    for i, sc in enumerate(scales):
-        ds = synth.tree_dna(seed=seed * 100 + i, n=n_per_tree, root_len=root_len,
-                            sub_lo=0.005 * sc, sub_hi=0.05 * sc)
-        sq = api.upload_and_pack(ctx, ds)
-        prof = api.kmer_profile(ctx, sq)
-        pairs = torch.from_numpy(synth.all_pairs(ds.n)).cuda()
-        Xs.append(api.pair_features(ctx, sq, prof, pairs))
-        d = api.lev_batch(ctx, sq, pairs)
-        lens = torch.from_numpy(np.diff(ds.offs)).cuda()
-        mx = torch.maximum(lens[pairs[:, 0].long()], lens[pairs[:, 1].long()]).clamp(min=1)
-        ys.append((d.double() / mx.double()).float())
+    i = 0
+    for L in root_lens:
+        for sc in scales:
+            ds = synth.tree_dna(seed=seed * 1000 + i, n=n_per_tree, root_len=L,
+                                sub_lo=0.005 * sc, sub_hi=0.05 * sc)
+            i += 1
+            sq = api.upload_and_pack(ctx, ds)
+            prof = api.kmer_profile(ctx, sq)
+            pairs = torch.from_numpy(synth.all_pairs(ds.n)).cuda()
+            Xs.append(api.pair_features(ctx, sq, prof, pairs))
+            d = api.lev_batch(ctx, sq, pairs)
+            lens = torch.from_numpy(np.diff(ds.offs)).cuda()
+            mx = torch.maximum(lens[pairs[:, 0].long()], lens[pairs[:, 1].long()]).clamp(min=1)
+            ys.append((d.double() / mx.double()).float())
     ctx.check()
     X, y = torch.cat(Xs), torch.cat(ys)
-    return X, y, dict(pairs=int(y.numel()), seconds=time.perf_counter() - t0)
+    return X, y, dict(pairs=int(y.numel()), trees=i, seconds=time.perf_counter() - t0)
 
 
 def train(ctx: api.Context, X: torch.Tensor, y: torch.Tensor, epochs: float = 4.0, batch: int = 4096,

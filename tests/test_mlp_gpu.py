@@ -128,10 +128,10 @@ def test_adam_step_matches_closed_form(ctx):
 def test_band_policy_and_learned_gain(ctx):
     # train on exact distances of tree-simulated DNA, evaluate on fresh pairs
     from paper_2601_15458_gb300 import learned_band
-    X, y, _ = learned_band.training_set(ctx, seed=21, n_per_tree=150)
+    X, y, _ = learned_band.training_set(ctx, seed=21, n_per_tree=90, root_lens=(1500, 3000, 6000))
     model, info = learned_band.train(ctx, X, y, epochs=12, batch=1024, lr=2e-3)
     assert info["val_loss"] < 0.05
-    ev = synth.divergent_pairs(seed=40, n_pairs=20000, len_lo=1000, len_hi=3000, div_lo=0.01, div_hi=0.15)
+    ev = synth.divergent_pairs(seed=40, n_pairs=30000, len_lo=2000, len_hi=6000, div_lo=0.01, div_hi=0.30)
     sq = api.upload_and_pack(ctx, ev)
     prof = api.kmer_profile(ctx, sq)
     pairs = np.stack([np.arange(0, ev.n, 2), np.arange(1, ev.n, 2)], 1).astype(np.int32)
@@ -158,11 +158,19 @@ def test_band_policy_and_learned_gain(ctx):
     pt = torch.from_numpy(pairs).cuda()
     d_full = api.lev_batch(ctx, sq, pt)
     d_band, k_used = api.lev_banded_batch(ctx, sq, pt, k)
+    # the band without the network: the 4-mer lower bound ceil(L1 / 8) <= f
+    Xe = api.pair_features(ctx, sq, prof, pt)
+    meanlen = torch.from_numpy(((lens[pairs[:, 0]] + lens[pairs[:, 1]]) / 2).astype(np.float32)).cuda()
+    l1 = (Xe.float() * meanlen[:, None]).sum(1)
+    dl = torch.from_numpy(np.abs(lens[pairs[:, 0]] - lens[pairs[:, 1]]).astype(np.int32)).cuda()
+    k_l1 = torch.maximum(dl, torch.ceil(l1 / 8).int())
+    d_l1, _ = api.lev_banded_batch(ctx, sq, pt, k_l1)
     ctx.check()
     np.testing.assert_array_equal(d_band.cpu().numpy(), d_full.cpu().numpy())
+    np.testing.assert_array_equal(d_l1.cpu().numpy(), d_full.cpu().numpy())
     sample = pairs[:60]
     np.testing.assert_array_equal(d_full.cpu().numpy()[:60], oracle.lev_pairs(ev.arena, ev.offs, sample))
-    t_full = timed(lambda: api.lev_batch(ctx, sq, pt))
+    # what the network gains over the band method without it
+    t_l1 = timed(lambda: api.lev_banded_batch(ctx, sq, pt, k_l1))
     t_band = timed(lambda: api.lev_banded_batch(ctx, sq, pt, k))
-    # what the network gains over the method without it (the plain full DP)
-    assert t_band * 1.5 < t_full, (t_band, t_full)
+    assert t_band < t_l1, (t_band, t_l1)
