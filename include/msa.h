@@ -131,6 +131,29 @@ msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs
 msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
                             int64_t P, int32_t *d_out, void *stream);
 
+/*
+ * Allocation-free variant of msa_lev_batch (the paper has no counterpart;
+ * this is a deployment convenience).  For callers that cannot allocate
+ * device memory or create a context: code running under another
+ * framework's memory budget (a caching allocator that holds the free device
+ * memory), plug-ins that may not allocate after start-up, loops that cannot
+ * take an allocation's implicit synchronisation.  It computes the same
+ * d_out[p] = f(seq[pairs[2p]], seq[pairs[2p+1]]) as msa_lev_batch, with no
+ * context and no cudaMalloc / cudaFree / allocating library call: its scratch
+ * is one fixed device array inside the library (about 5.8 MB, held on every
+ * GPU that loads the library until the process exits).
+ *  - Limits: P <= 262144 pairs and n_seqs <= 65536 per call; larger calls
+ *    return MSA_EINVAL before anything is enqueued.
+ *  - The first call on a device looks the array up with that device
+ *    current (cudaGetSymbolAddress); make it before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other
+ *    streams or threads) race; issue them on one stream.
+ *  - No error word: a pair with an index outside the set, or whose first
+ *    sequence is longer than the kernels hold (16384), gets d_out[p] = -1.
+ */
+msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                                 void *stream);
+
 /* ---- A4: banded Levenshtein with an exactness certificate --------------- */
 /*
  * Same result as msa_lev_batch: d_out[p] = f(a, b) exactly.  Each pair

@@ -42,6 +42,7 @@ SIGNATURES = {
     "msa_pack": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p]),
     "msa_lev_batch": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_int64, c_void_p, c_void_p]),
     "msa_lev_autotune": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_int64, c_void_p, c_void_p]),
+    "msa_lev_batch_noalloc": (c_int32, [ctypes.POINTER(SeqSetC), c_void_p, c_int64, c_void_p, c_void_p]),
     "msa_nw_align_batch": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p, c_int64,
                                      c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "msa_nw_workspace_bytes": (c_int64, [c_int32, c_int32]),

@@ -1,0 +1,268 @@
+// msa_lev_batch_noalloc: the batched Levenshtein distance for callers that
+// cannot allocate device memory.
+//
+// Some callers of this library cannot call cudaMalloc or create a context
+// workspace: code that runs inside another framework's memory budget (a
+// caching allocator that owns all free device memory), plug-ins loaded into
+// a host that forbids allocations after start-up, or latency-critical loops
+// where an allocation's implicit synchronisation is not acceptable.  This
+// entry point gives them the same distances as msa_lev_batch without any
+// allocation: its scratch lives in one file-scope __device__ array of a fixed
+// maximum size, which every GPU that loads the library holds until the
+// process exits.
+//
+// Properties (also stated in include/msa.h):
+//  * At most kMaxPairs pairs over at most kMaxSeqs sequences per call;
+//    larger calls are rejected with MSA_EINVAL before anything runs.
+//  * All calls share the one scratch array per device: calls whose work
+//    overlaps on the GPU (other streams, other host threads) race.  Serialise
+//    them on one stream.
+//  * The first call on a device looks the array's address up
+//    (cudaGetSymbolAddress) with that device current; make that first call
+//    before any stream capture.
+//  * No context, so no error word: pairs with an index outside the set, or a
+//    query longer than the kernels hold, get d_out = -1.
+//  * It calls no cudaMalloc, cudaFree or allocating library routine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "lev_kernels.cuh"
+
+namespace msa {
+namespace noalloc {
+
+constexpr int64_t kMaxPairs = int64_t(1) << 18;   // 262,144 pairs per call
+constexpr int32_t kMaxSeqs = int32_t(1) << 16;    // 65,536 sequences in the set
+constexpr int kNB = 64;                           // kernel buckets (>= lane + warp configurations)
+constexpr int kMaxDevices = 64;
+
+struct Scratch {
+    int32_t qcount[kMaxSeqs];
+    int32_t qfill[kMaxSeqs];
+    int32_t qcursor[kMaxSeqs];
+    int32_t qstart[kMaxSeqs + 1];
+    int32_t sorted_t[kMaxPairs];
+    int32_t sorted_p[kMaxPairs];
+    int2 tasks[kMaxPairs + kMaxSeqs + 1];
+    int32_t bcount[kNB];
+    int32_t bfill[kNB];
+    int32_t boff[kNB];
+    int32_t bcounter[kNB];
+    int32_t err[4];
+};
+
+// The scratch of every call (about 5.8 MB per device).
+static __device__ __align__(256) Scratch g_scratch;
+
+struct Plan {
+    int nlane, nwarp;
+    int lane_words[32];
+    int warp_words[32];
+    int lane_per_task;
+};
+
+__device__ __forceinline__ bool ok_seq(const int64_t *offs, int32_t n, int64_t total, int s) {
+    if (s < 0 || s >= n) return false;
+    const int64_t a = offs[s], b = offs[s + 1];
+    return a >= 0 && a <= b && b <= total;
+}
+
+__global__ void na_count(Scratch *S, const int32_t *__restrict__ pairs, int64_t P, int32_t n,
+                         const int64_t *__restrict__ offs, int64_t total) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+        if (ok_seq(offs, n, total, q) && ok_seq(offs, n, total, t)) atomicAdd(&S->qcount[q], 1);
+    }
+}
+
+__global__ void __launch_bounds__(1024) na_scan(Scratch *S, int32_t n) {
+    __shared__ int32_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t lo = tid * chunk, hi = min((int64_t)n, lo + chunk);
+    int32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += S->qcount[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = tid ? part[tid - 1] : 0;
+    for (int64_t i = lo; i < hi; ++i) {
+        S->qstart[i] = run;
+        run += S->qcount[i];
+    }
+    if (tid == 1023) S->qstart[n] = part[1023];
+}
+
+__global__ void na_scatter(Scratch *S, const int32_t *__restrict__ pairs, int64_t P, int32_t n,
+                           const int64_t *__restrict__ offs, int64_t total) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int q = pairs[2 * p], t = pairs[2 * p + 1];
+        if (!ok_seq(offs, n, total, q) || !ok_seq(offs, n, total, t)) continue;
+        const int pos = S->qstart[q] + atomicAdd(&S->qfill[q], 1);
+        S->sorted_t[pos] = t;
+        S->sorted_p[pos] = (int32_t)p;
+    }
+}
+
+__device__ __forceinline__ int na_bucket(const Plan &pl, int W, int c) {
+    if (W <= pl.lane_words[pl.nlane - 1] && c >= 12)
+        for (int b = 0; b < pl.nlane; ++b)
+            if (pl.lane_words[b] >= W) return b;
+    for (int b = 0; b < pl.nwarp; ++b)
+        if (32 * pl.warp_words[b] >= W) return pl.nlane + b;
+    return -1;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) na_tasks(Scratch *S, const int64_t *__restrict__ offs, int32_t n, Plan pl) {
+    __shared__ int32_t sboff[kNB];
+    const int NB = pl.nlane + pl.nwarp;
+    if (PASS == 1) {
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int b = 0; b < NB; ++b) {
+                sboff[b] = run;
+                run += S->bcount[b];
+            }
+        }
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x < NB) S->boff[threadIdx.x] = sboff[threadIdx.x];
+    }
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = S->qstart[q + 1] - S->qstart[q];
+        if (c == 0) continue;
+        const int m = (int)(offs[q + 1] - offs[q]);
+        const int b = na_bucket(pl, max(1, (m + 31) / 32), c);
+        if (b < 0) continue;   // too long for the kernels: its pairs keep d_out = -1
+        const int per = b < pl.nlane ? pl.lane_per_task : 4;
+        const int parts = (c + per - 1) / per;
+        if (PASS == 0) {
+            atomicAdd(&S->bcount[b], parts);
+        } else {
+            const int base = sboff[b] + atomicAdd(&S->bfill[b], parts);
+            for (int i = 0; i < parts; ++i) S->tasks[base + i] = make_int2((int)q, i);
+        }
+    }
+}
+
+// Per-device set-up: the scratch address, SM count and kernel occupancies.
+struct DeviceInfo {
+    bool ready = false;
+    Scratch *scratch = nullptr;
+    int sm_count = 0;
+    int occ[2][kNB] = {};
+};
+
+static DeviceInfo g_dev[kMaxDevices];
+static std::mutex g_mu;
+
+static msa_status setup(int dev, int alphabet, DeviceInfo **out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceInfo &d = g_dev[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return MSA_ECUDA;
+        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MSA_ECUDA;
+        d.scratch = static_cast<Scratch *>(ptr);
+        d.ready = true;
+    }
+    const LevKernelInfo *lane = alphabet == MSA_DNA ? kLevLaneDna : kLevLaneProt;
+    const LevKernelInfo *warp = alphabet == MSA_DNA ? kLevWarpDna : kLevWarpProt;
+    const int nl = alphabet == MSA_DNA ? kLevLaneDnaCount : kLevLaneProtCount;
+    const int nw = alphabet == MSA_DNA ? kLevWarpDnaCount : kLevWarpProtCount;
+    for (int b = 0; b < nl + nw; ++b) {
+        if (d.occ[alphabet][b] > 0) continue;
+        const LevKernelInfo &K = b < nl ? lane[b] : warp[b - nl];
+        const size_t smem = K.smem_per_warp * 4;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return MSA_ECUDA;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, K.fn, 128, smem) != cudaSuccess) return MSA_ECUDA;
+        d.occ[alphabet][b] = std::max(blocks, 1);
+    }
+    *out = &d;
+    return MSA_OK;
+}
+
+}  // namespace noalloc
+}  // namespace msa
+
+using namespace msa;
+using namespace msa::noalloc;
+
+extern "C" msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
+                                            void *stream) {
+    if (!s || P < 0) return MSA_EINVAL;
+    if (P == 0) return MSA_OK;
+    if (P > kMaxPairs || s->n_seqs > kMaxSeqs || s->n_seqs <= 0) return MSA_EINVAL;
+    if (!pairs || !d_out || !s->offs || !s->codes || !s->planes) return MSA_EINVAL;
+    if (s->alphabet != MSA_DNA && s->alphabet != MSA_PROTEIN) return MSA_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSA_ECUDA;
+    DeviceInfo *D = nullptr;
+    msa_status rc = setup(dev, s->alphabet, &D);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch *S = D->scratch;
+    const int32_t n = s->n_seqs;
+    // the scratch keeps the last call's contents: clear what must start at zero
+    if (cudaMemsetAsync(S->qcount, 0, sizeof(int32_t) * 3 * kMaxSeqs, st) != cudaSuccess ||
+        cudaMemsetAsync(S->bcount, 0, sizeof(int32_t) * 4 * kNB, st) != cudaSuccess ||
+        cudaMemsetAsync(d_out, 0xff, sizeof(int32_t) * P, st) != cudaSuccess)
+        return MSA_ECUDA;
+    const int gP = (int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, D->sm_count * 8));
+    const int gN = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, D->sm_count * 8));
+    na_count<<<gP, 256, 0, st>>>(S, pairs, P, n, s->offs, s->total);
+    na_scan<<<1, 1024, 0, st>>>(S, n);
+    na_scatter<<<gP, 256, 0, st>>>(S, pairs, P, n, s->offs, s->total);
+    const LevKernelInfo *lane = s->alphabet == MSA_DNA ? kLevLaneDna : kLevLaneProt;
+    const LevKernelInfo *warp = s->alphabet == MSA_DNA ? kLevWarpDna : kLevWarpProt;
+    Plan pl{};
+    pl.nlane = s->alphabet == MSA_DNA ? kLevLaneDnaCount : kLevLaneProtCount;
+    pl.nwarp = s->alphabet == MSA_DNA ? kLevWarpDnaCount : kLevWarpProtCount;
+    for (int b = 0; b < pl.nlane; ++b) pl.lane_words[b] = lane[b].words;
+    for (int b = 0; b < pl.nwarp; ++b) pl.warp_words[b] = warp[b].words;
+    int64_t per = P / ((int64_t)D->sm_count * 16 * 4);
+    per = std::max<int64_t>(32, std::min<int64_t>(512, per));
+    pl.lane_per_task = (int)(per / 32 * 32);
+    na_tasks<0><<<gN, 256, 0, st>>>(S, s->offs, n, pl);
+    na_tasks<1><<<gN, 256, 0, st>>>(S, s->offs, n, pl);
+    LevArgs a{};
+    a.planes = s->planes;
+    a.codes = s->codes;
+    a.offs = s->offs;
+    a.sorted_t = S->sorted_t;
+    a.sorted_p = S->sorted_p;
+    a.qstart = S->qstart;
+    a.qcursor = S->qcursor;
+    a.tasks = S->tasks;
+    a.boff = S->boff;
+    a.bcount = S->bcount;
+    a.bcounter = S->bcounter;
+    a.d_out = d_out;
+    a.err = S->err;
+    a.one = 1u;
+    a.two = 2u;
+    const int Wmax = std::max(1, (s->max_len + 31) / 32);
+    for (int b = 0; b < pl.nlane + pl.nwarp; ++b) {
+        const bool is_lane = b < pl.nlane;
+        const LevKernelInfo &K = is_lane ? lane[b] : warp[b - pl.nlane];
+        // a bucket whose smaller neighbour already holds the longest sequence is never used
+        if (b > 0 && b != pl.nlane) {
+            const LevKernelInfo &prev = is_lane ? lane[b - 1] : warp[b - pl.nlane - 1];
+            const int cap_prev = is_lane ? prev.words : 32 * prev.words;
+            if (cap_prev >= Wmax) continue;
+        }
+        a.bucket = b;
+        K.launch(a, D->sm_count * D->occ[s->alphabet][b], st);
+    }
+    return cudaGetLastError() == cudaSuccess ? MSA_OK : MSA_ECUDA;
+}
