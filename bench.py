@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (for profiling)")
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band measurement")
     ap.add_argument("--band-pairs", type=int, default=100000)
+    ap.add_argument("--clam", type=int, default=0, metavar="N",
+                    help="also build the guide tree and merge N 16S-like sequences (the 50,000 workload: --clam 50000)")
     return ap.parse_args()
 
 
@@ -51,6 +53,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(values, world):
+    """Element-wise maximum over all ranks (gloo / nccl all_reduce); identity at N=1."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_gcups(cells_per_rank, steps, max_ms, world):
+    """Cells of every rank over the slowest rank's time (weak scaling: each
+    rank runs its own copy of the batch)."""
+    return world * cells_per_rank * steps / (max_ms / 1e3) / 1e9
 
 
 def make_workload(n):
@@ -221,6 +240,61 @@ def band_bench(ctx, args, stream):
                 val_pinball=minfo["val_loss"], setup_s=setup_s)
 
 
+def clam_bench(ctx, args):
+    """Guide tree (Alg. 1) and bottom-up merges on N 16S-like sequences
+    (lengths 1,400-1,600), with Alg. 1 redone by the oracle on sampled
+    clusters and the MSA rows checked against their sequences."""
+    import torch
+    from paper_2601_15458_gb300 import api, synth
+    t0 = time.perf_counter()
+    ds = synth.gg16s_dna(seed=5, n=args.clam)
+    gen_s = time.perf_counter() - t0
+    sq = api.upload_and_pack(ctx, ds)
+    ctx.check()
+    ctx.prof_read(reset=True)
+    ctx.prof_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = api.clam_partition(ctx, sq)
+    torch.cuda.synchronize()
+    t_part = time.perf_counter() - t0
+    part_dp_ms, part_launches = ctx.prof_read(reset=True)
+    t0 = time.perf_counter()
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    torch.cuda.synchronize()
+    t_merge = time.perf_counter() - t0
+    merge_dp_ms, merge_launches = ctx.prof_read(reset=True)
+    ctx.prof_enable(False)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
+    ctx.check()
+    import oracle
+    order = tree.order.cpu().numpy()
+    rng = np.random.default_rng(0)
+    seqs = ds.seqs()
+    bad = 0
+    for r in rng.choice(ds.n, 64, replace=False):
+        bad += rows[r].cpu().numpy().tobytes().replace(b"-", b"") != seqs[order[r]]
+    dist = oracle._default_dist(seqs)
+    internal = [k for k in range(tree.n_nodes) if tree.left[k] >= 0 and 2 <= tree.hi[k] - tree.lo[k] <= 24]
+    for k in rng.choice(internal, min(4, len(internal)), replace=False):
+        mem = sorted(int(x) for x in order[tree.lo[k]:tree.hi[k]])
+        c, l, r, L, R = oracle.partition_step(mem, dist)
+        Lg = sorted(int(x) for x in order[tree.lo[tree.left[k]]:tree.hi[tree.left[k]]])
+        bad += int(tree.center[k] != c or Lg != L)
+    depth = np.zeros(tree.n_nodes, np.int64)
+    for k in range(1, tree.n_nodes):
+        depth[k] = depth[tree.parent[k]] + 1
+    nw_cells = 0
+    for k in range(tree.n_nodes):
+        if tree.left[k] >= 0:
+            nw_cells += int(width[tree.left[k]]) * int(width[tree.right[k]])
+    return dict(workload=f"gg16s_dna_{ds.n}_len1400-1600", n_seqs=ds.n, partition_s=t_part, merge_s=t_merge,
+                partition_dp_ms=part_dp_ms, merge_dp_ms=merge_dp_ms, launches=part_launches + merge_launches,
+                tree_depth=int(depth.max()), msa_width=int(width[0]), nw_cells=nw_cells,
+                nw_gcups=nw_cells / (merge_dp_ms / 1e3) / 1e9 if merge_dp_ms else None,
+                checks_failed=int(bad), generate_s=gen_s)
+
+
 def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores: each step a bounded sample."""
     if rank != 0:
@@ -309,12 +383,8 @@ def main():
     ctx.check()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, dp_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, dp_ms = float(t[0]), float(t[1])
-    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
+    total_ms, dp_ms = max_over_ranks([total_ms, dp_ms], world)
+    value = whole_job_gcups(cells, args.steps, total_ms, world)
 
     # end to end through the public API: host buffers, copies inside the timed region
     h_arena = torch.from_numpy(np.ascontiguousarray(np.concatenate(
@@ -349,12 +419,8 @@ def main():
     torch.cuda.synchronize()
     ctx.check()
     e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t[0])
-    e2e_value = world * cells * args.steps / (e2e_ms / 1e3) / 1e9
+    (e2e_ms,) = max_over_ranks([e2e_ms], world)
+    e2e_value = whole_job_gcups(cells, args.steps, e2e_ms, world)
     h2d = h_arena.numel() + h_offs.numel() * 8 + h_pairs.numel() * 4
     d2h = h_out.numel() * 4
     ok = np.array_equal(h_out.numpy(), out.cpu().numpy())
@@ -377,6 +443,7 @@ def main():
     band = None
     if not args.no_band:
         band = band_bench(ctx, args, stream)
+    clam = clam_bench(ctx, args) if args.clam else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(ds, pairs, args.cpu_seconds)
@@ -390,7 +457,7 @@ def main():
                     roofline=roof, cpu_baseline=cpu,
                     e2e=dict(value=e2e_value, unit="GCUPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                              output_matches_device=bool(ok)),
-                    gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps, band=band,
+                    gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps, band=band, clam=clam,
                     wall_s_timed=t_wall, clocks=clocks)
         print(json.dumps(line), flush=True)
     ctx.close()

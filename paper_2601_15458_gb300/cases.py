@@ -1,0 +1,101 @@
+"""Small fixed workloads that run one kernel family each, for profiling.
+
+    python -m paper_2601_15458_gb300.cases lev     # lane kernel, 400 x 1,500 DNA all pairs
+    python -m paper_2601_15458_gb300.cases nw      # NW fill + traceback, 2,000 pairs of ~1,500
+    python -m paper_2601_15458_gb300.cases band    # certified bands, 100,000 pairs 1,000-10,000
+    python -m paper_2601_15458_gb300.cases band_small  # the same on 20,000 pairs (for ncu captures)
+    python -m paper_2601_15458_gb300.cases pack    # packed loader, 1.1 GB arena
+    python -m paper_2601_15458_gb300.cases mlp     # band network forward + one training step
+
+Each case runs its call a few times (the first warms up) and prints one
+line with the call's device time.
+"""
+from __future__ import annotations
+
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import api, build, learned_band, synth
+
+
+def _time(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def case_lev(ctx):
+    ds = synth.tree_dna(seed=2, n=400)
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = torch.from_numpy(synth.all_pairs_balanced(ds.n)).cuda()
+    out = torch.empty(pairs.shape[0], dtype=torch.int32, device="cuda")
+    return _time(lambda: api.lev_batch(ctx, sq, pairs, out))
+
+
+def case_nw(ctx):
+    ds = synth.tree_dna(seed=2, n=2000)
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = torch.from_numpy(np.stack([np.arange(0, 2000, 2), np.arange(1, 2000, 2)], 1).astype(np.int32)).cuda()
+    pairs = torch.cat([pairs, pairs.flip(1)])
+    return _time(lambda: api.nw_align_batch(ctx, sq, pairs))
+
+
+def case_band(ctx):
+    ev = synth.divergent_pairs(seed=40, n_pairs=100000)
+    sq = api.upload_and_pack(ctx, ev)
+    pairs = torch.from_numpy(np.stack([np.arange(0, ev.n, 2), np.arange(1, ev.n, 2)], 1).astype(np.int32)).cuda()
+    d = api.lev_batch(ctx, sq, pairs)
+    k0 = (d.float() * 1.2).int() + 8          # a band 20% above the distance
+    full = _time(lambda: api.lev_batch(ctx, sq, pairs, d))
+    print(f"full DP: {full:.3f} ms per call")
+    return _time(lambda: api.lev_banded_batch(ctx, sq, pairs, k0))
+
+
+def case_band_small(ctx):
+    ev = synth.divergent_pairs(seed=40, n_pairs=20000)
+    sq = api.upload_and_pack(ctx, ev)
+    pairs = torch.from_numpy(np.stack([np.arange(0, ev.n, 2), np.arange(1, ev.n, 2)], 1).astype(np.int32)).cuda()
+    d = api.lev_batch(ctx, sq, pairs)
+    k0 = (d.float() * 1.2).int() + 8
+    return _time(lambda: api.lev_banded_batch(ctx, sq, pairs, k0))
+
+
+def case_pack(ctx):
+    ev = synth.divergent_pairs(seed=40, n_pairs=100000)
+    sq = api.DeviceSeqs.from_host(ev.arena, ev.offs, "dna")
+    return _time(lambda: api.pack(ctx, sq))
+
+
+def case_mlp(ctx):
+    X, y, _ = learned_band.training_set(ctx, seed=4, n_per_tree=120)
+    model = api.BandModel(ctx, seed=0)
+    idx = torch.arange(4096, dtype=torch.int32, device="cuda") % X.shape[0]
+    model.forward(X)
+    return _time(lambda: model.train_step(X, y, idx, lr=1e-3))
+
+
+CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp)
+
+
+def main(argv):
+    build.build()
+    ctx = api.Context(0, workspace_bytes=2 << 30)
+    t0 = time.perf_counter()
+    ms = CASES[argv[1]](ctx)
+    ctx.check()
+    print(f"case {argv[1]}: {ms:.3f} ms per call ({time.perf_counter() - t0:.1f} s total)")
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -1,0 +1,149 @@
+// Multi-word additions on the hardware carry chain: one add per 32-bit word
+// (word 0 lowest).  add(s, a, b): s = a + b, returns the carry out of the
+// top word.  inc(s, c): s += c for c in {0, 1} (the carry out is dropped).
+#pragma once
+
+#include <stdint.h>
+
+namespace msa {
+
+template <int N>
+struct CarryChain;
+
+template <>
+struct CarryChain<1> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[1], const uint32_t (&a)[1],
+                                                   const uint32_t (&b)[1]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, 0, 0;"
+            : "=r"(s[0]), "=r"(c)
+            : "r"(a[0]), "r"(b[0]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[1], uint32_t ci) {
+        asm("add.u32 %0, %0, %1;"
+            : "+r"(s[0])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<2> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[2], const uint32_t (&a)[2],
+                                                   const uint32_t (&b)[2]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %3, %5;\n\taddc.cc.u32 %1, %4, %6;\n\taddc.u32 %2, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[2], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;"
+            : "+r"(s[0]), "+r"(s[1])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<3> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[3], const uint32_t (&a)[3],
+                                                   const uint32_t (&b)[3]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %4, %7;\n\taddc.cc.u32 %1, %5, %8;\n\taddc.cc.u32 %2, %6, %9;\n\taddc.u32 %3, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[3], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.u32 %2, %2, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<4> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[4], const uint32_t (&a)[4],
+                                                   const uint32_t (&b)[4]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %5, %9;\n\taddc.cc.u32 %1, %6, %10;\n\taddc.cc.u32 %2, %7, %11;\n\taddc.cc.u32 %3, %8, %12;\n\taddc.u32 %4, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[4], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.u32 %3, %3, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<5> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[5], const uint32_t (&a)[5],
+                                                   const uint32_t (&b)[5]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %6, %11;\n\taddc.cc.u32 %1, %7, %12;\n\taddc.cc.u32 %2, %8, %13;\n\taddc.cc.u32 %3, %9, %14;\n\taddc.cc.u32 %4, %10, %15;\n\taddc.u32 %5, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[5], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %5;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.cc.u32 %3, %3, 0;\n\taddc.u32 %4, %4, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<6> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[6], const uint32_t (&a)[6],
+                                                   const uint32_t (&b)[6]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %7, %13;\n\taddc.cc.u32 %1, %8, %14;\n\taddc.cc.u32 %2, %9, %15;\n\taddc.cc.u32 %3, %10, %16;\n\taddc.cc.u32 %4, %11, %17;\n\taddc.cc.u32 %5, %12, %18;\n\taddc.u32 %6, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[6], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %6;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.cc.u32 %3, %3, 0;\n\taddc.cc.u32 %4, %4, 0;\n\taddc.u32 %5, %5, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<8> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[8], const uint32_t (&a)[8],
+                                                   const uint32_t (&b)[8]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %9, %17;\n\taddc.cc.u32 %1, %10, %18;\n\taddc.cc.u32 %2, %11, %19;\n\taddc.cc.u32 %3, %12, %20;\n\taddc.cc.u32 %4, %13, %21;\n\taddc.cc.u32 %5, %14, %22;\n\taddc.cc.u32 %6, %15, %23;\n\taddc.cc.u32 %7, %16, %24;\n\taddc.u32 %8, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[8], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %8;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.cc.u32 %3, %3, 0;\n\taddc.cc.u32 %4, %4, 0;\n\taddc.cc.u32 %5, %5, 0;\n\taddc.cc.u32 %6, %6, 0;\n\taddc.u32 %7, %7, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]), "+r"(s[7])
+            : "r"(ci));
+    }
+};
+
+template <>
+struct CarryChain<10> {
+    static __device__ __forceinline__ uint32_t add(uint32_t (&s)[10], const uint32_t (&a)[10],
+                                                   const uint32_t (&b)[10]) {
+        uint32_t c;
+        asm("add.cc.u32 %0, %11, %21;\n\taddc.cc.u32 %1, %12, %22;\n\taddc.cc.u32 %2, %13, %23;\n\taddc.cc.u32 %3, %14, %24;\n\taddc.cc.u32 %4, %15, %25;\n\taddc.cc.u32 %5, %16, %26;\n\taddc.cc.u32 %6, %17, %27;\n\taddc.cc.u32 %7, %18, %28;\n\taddc.cc.u32 %8, %19, %29;\n\taddc.cc.u32 %9, %20, %30;\n\taddc.u32 %10, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(s[8]), "=r"(s[9]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]));
+        return c;
+    }
+    static __device__ __forceinline__ void inc(uint32_t (&s)[10], uint32_t ci) {
+        asm("add.cc.u32 %0, %0, %10;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.cc.u32 %3, %3, 0;\n\taddc.cc.u32 %4, %4, 0;\n\taddc.cc.u32 %5, %5, 0;\n\taddc.cc.u32 %6, %6, 0;\n\taddc.cc.u32 %7, %7, 0;\n\taddc.cc.u32 %8, %8, 0;\n\taddc.u32 %9, %9, 0;"
+            : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]), "+r"(s[7]), "+r"(s[8]), "+r"(s[9])
+            : "r"(ci));
+    }
+};
+
+}  // namespace msa

@@ -236,7 +236,7 @@ namespace msa {
 // With idx != nullptr the batch is pairs[idx[0 .. *count_dev)), at most P of
 // them; the workspace is taken from `ar` (the whole context workspace if null).
 msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
-                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer) {
+                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer, int side_base) {
     const Registry R = registry(s->alphabet);
     msa_status rc = ensure_occupancy(ctx, R, s->alphabet);
     if (rc) return rc;
@@ -319,7 +319,7 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
         ai.bucket = launch_list[i];
         const int grid = grid_for(ctx->sm_count * T.occupancy[s->alphabet][ai.bucket]);
         R.at(ai.bucket).launch(ai, grid, s2);
-    });
+    }, side_base, 8);
     ctx->launches += (int64_t)launch_list.size();
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_batch launch");
     return cuda_check(ctx, cudaGetLastError(), "msa_lev_batch launch");

@@ -42,7 +42,7 @@ struct msa_ctx {
     double prof_ms = 0.0;
     // side streams for running independent bucket kernels concurrently
     // (fork / join through events, so stream capture still works)
-    static constexpr int kSide = 8;
+    static constexpr int kSide = 16;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kSide] = {};
@@ -96,7 +96,7 @@ struct ProfScope {
 };
 
 msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
-                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer);
+                   cudaStream_t st, const int32_t *idx, const int32_t *count_dev, Arena *outer, int side_base = 0);
 msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const void *out,
                         const char *who);
 int64_t lev_workspace(int64_t P, int32_t n);
@@ -105,25 +105,40 @@ msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *
                   int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
                   cudaStream_t st);
 
-// Runs launch(i, stream) for i < count, spread over the context's side
-// streams after a fork from `st`, and makes `st` wait for all of them.
+// Runs launch(i, stream) for i < count, spread over side streams
+// [base, base + width) of the context after a fork from `st`.  With join
+// (the default) `st` then waits for all of them; otherwise the caller joins
+// later with join_side().
 template <class F>
-cudaError_t run_concurrent(msa_ctx *ctx, cudaStream_t st, int count, F launch) {
+cudaError_t run_concurrent(msa_ctx *ctx, cudaStream_t st, int count, F launch, int base = 0, int width = 8,
+                           bool join = true) {
     if (count <= 1 || !ctx->fork_ev) {
         for (int i = 0; i < count; ++i) launch(i, st);
         return cudaGetLastError();
     }
     cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
-    const int used = count < msa_ctx::kSide ? count : msa_ctx::kSide;
-    for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0);
+    const int used = count < width ? count : width;
+    for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ctx->side[base + k], ctx->fork_ev, 0);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < count; ++i) launch(i, ctx->side[i % used]);
-    for (int k = 0; k < used && e == cudaSuccess; ++k) {
-        e = cudaEventRecord(ctx->join_ev[k], ctx->side[k]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[k], 0);
+    for (int i = 0; i < count; ++i) launch(i, ctx->side[base + i % used]);
+    if (join) {
+        for (int k = 0; k < used && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(ctx->join_ev[base + k], ctx->side[base + k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[base + k], 0);
+        }
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// Makes `st` wait for side streams [base, base + width).
+inline cudaError_t join_side(msa_ctx *ctx, cudaStream_t st, int base, int width) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < width && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(ctx->join_ev[base + k], ctx->side[base + k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[base + k], 0);
+    }
+    return e;
 }
 
 inline int bits_of(int alphabet) { return alphabet == MSA_DNA ? 2 : 5; }
