@@ -28,6 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALU_OPS_PER_WORD = 11    # integer ops of one 32-row word step (bv_word)
+# DRAM bytes per launch of the dominant kernel (lev_lane_kernel<48>) on this
+# workload, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# (profiles/launches_tree_dna_allpairs_2000x1500.md); valid only while the
+# kernel source is the one that was measured.
+TRAFFIC = dict(kernel_sha256_16="3e19c17b1871b96e", bytes_per_launch=20.0e6)
 WORKLOAD = "tree_dna_allpairs_2000x1500"
 
 
@@ -432,10 +437,16 @@ def main():
     alu_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e12   # T int32 lane-ops/s
     alg_ops = words * ALU_OPS_PER_WORD
     achieved = alg_ops * args.steps / (dp_ms / 1e3) / 1e12 if dp_ms > 0 else None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2601_15458_gb300", "csrc", "lev_kernels.cuh")
+    same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC["kernel_sha256_16"]
+    alu_pipe_peak = alu_peak / 2        # LOP3/SHF/IADD3 pipe: one warp instruction per 2 clk per scheduler
     roof = dict(bound="alu", kernel="lev_lane_kernel (all length buckets)", achieved=achieved, peak=alu_peak,
-                unit="Tops/s (int32 lane-ops)", frac=(achieved / alu_peak) if achieved else None, traffic=None,
+                unit="Tops/s (int32 lane-ops)", frac=(achieved / alu_peak) if achieved else None,
+                traffic=TRAFFIC["bytes_per_launch"] if same_kernel else None,
+                alu_pipe_peak=alu_pipe_peak, frac_of_alu_pipe=(achieved / alu_pipe_peak) if achieved else None,
                 peak_source=f"{props.multi_processor_count} SMs x 4 issue/clk x 32 lanes x {sm_max:.0f} MHz "
-                            f"({pk_kind} max clock)",
+                            f"({pk_kind} max clock); the ALU pipe takes half that rate (ncu)",
                 algorithmic=f"{ALU_OPS_PER_WORD} ops per 32-row word per column; "
                             f"{words:.4e} word-columns per launch set")
 

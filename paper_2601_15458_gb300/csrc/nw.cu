@@ -29,6 +29,12 @@ constexpr int kNwR = 16;                 // rows per lane
 constexpr int kNwTile = 32 * kNwR;       // rows per tile
 constexpr int kNwWarps = 4;              // warps per block
 
+// 0: plain min / compare / select; 1: the two-way min-with-flag instruction
+// (__vibmin_s32), which yields the move preference with the minimum
+#ifndef MSA_NW_VARIANT
+#define MSA_NW_VARIANT 1
+#endif
+
 struct NwArgs {
     const uint8_t *codes;
     const int64_t *offs;
@@ -127,10 +133,19 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
 #pragma unroll
                     for (int r = 0; r < kNwR; ++r) {
                         const int dg = diag + (ac[r] == bj ? match : mismatch);
+#if MSA_NW_VARIANT == 0
                         const int u = up + gap;
                         const int lf = H[r] + gap;
                         const int d = min(dg, min(u, lf));
                         const uint32_t c = d == dg ? 0u : (d == u ? 1u : 2u);
+#else
+                        // two-way minima with their "first argument won" flag:
+                        // up <= left keeps up, then diagonal <= that keeps diagonal
+                        bool up_wins, diag_wins;
+                        const int m1 = __vibmin_s32(up + gap, H[r] + gap, &up_wins);
+                        const int d = __vibmin_s32(dg, m1, &diag_wins);
+                        const uint32_t c = diag_wins ? 0u : (up_wins ? 1u : 2u);
+#endif
                         code |= c << (2 * r);
                         diag = H[r];
                         H[r] = d;
