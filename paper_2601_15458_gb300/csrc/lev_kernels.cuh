@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "carry_chain.cuh"
 #include "msa_internal.cuh"
 
 namespace msa {
@@ -148,6 +149,77 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
     mv = phs & (eq | mv);
 }
 
+#ifndef MSA_LANE_CHAIN
+#define MSA_LANE_CHAIN 1
+#endif
+
+// One column over WC words, in chunks of up to 8 words: the chunk's
+// (Eq & Pv) + Pv additions run on the hardware carry chain (add.cc/addc), and
+// the shifts by one take the lower word's top bit by funnel shift, so no
+// carry or top bit is extracted by separate instructions.
+template <int WC, int SIGMA>
+__device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t (&Pv)[WC], uint32_t (&Mv)[WC],
+                                                  uint32_t one) {
+    uint32_t cy = 0u, ph_prev = 0u, mh_prev = 0u;
+#pragma unroll
+    for (int k0 = 0; k0 < WC; k0 += 8) {
+        constexpr int kMax = 8;
+        const int len = WC - k0 < kMax ? WC - k0 : kMax;
+        if (len == 8) {
+            uint32_t eq[8], u[8], pv[8], s[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                eq[w] = row[(k0 + w) * SIGMA];
+                pv[w] = Pv[k0 + w];
+                u[w] = eq[w] & pv[w];
+            }
+#if MSA_LANE_CHAIN == 2
+            cy = CarryChainMadIn<8>::add(s, u, pv, cy, one);
+#else
+            cy = CarryChainIn<8>::add(s, u, pv, cy);
+            (void)one;
+#endif
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const int k = k0 + w;
+                const uint32_t xh = (s[w] ^ pv[w]) | eq[w];
+                const uint32_t ph = Mv[k] | ~(xh | pv[w]);
+                const uint32_t mh = pv[w] & xh;
+                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
+                const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
+                ph_prev = ph;
+                mh_prev = mh;
+                const uint32_t xv = eq[w] | Mv[k];
+                Pv[k] = mhs | ~(xv | phs);
+                Mv[k] = phs & xv;
+            }
+        } else {
+            // the tail of fewer than 8 words (WC % 8), same steps
+#pragma unroll
+            for (int w = 0; w < kMax; ++w) {
+                if (w >= len) break;
+                const int k = k0 + w;
+                const uint32_t eq = row[k * SIGMA];
+                const uint32_t pv = Pv[k];
+                const uint32_t u = eq & pv;
+                const uint64_t t = (uint64_t)u + pv + cy;
+                const uint32_t sum = (uint32_t)t;
+                cy = (uint32_t)(t >> 32);
+                const uint32_t xh = (sum ^ pv) | eq;
+                const uint32_t ph = Mv[k] | ~(xh | pv);
+                const uint32_t mh = pv & xh;
+                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
+                const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
+                ph_prev = ph;
+                mh_prev = mh;
+                const uint32_t xv = eq | Mv[k];
+                Pv[k] = mhs | ~(xv | phs);
+                Mv[k] = phs & xv;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);
@@ -223,9 +295,13 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
                     const int c = c_next;
                     if (j + 1 < n) c_next = __ldg(tc + j + 1);
                     const uint32_t *row = sPeq + c;
+#if MSA_LANE_CHAIN
+                    lane_column_chain<WC, SIGMA>(row, Pv, Mv, one);
+#else
                     uint32_t ph_in = 1u, mh_in = 0u;
 #pragma unroll
                     for (int k = 0; k < WC; ++k) bv_word(row[k * SIGMA], Pv[k], Mv[k], ph_in, mh_in, one, two);
+#endif
                     ++j;
                 }
                 if (j == n) {
