@@ -147,8 +147,8 @@ struct CarryChain<10> {
 };
 
 // add_in(s, a, b, cin): s = a + b + cin over N words on the carry chain,
-// cin in {0, 1} entered by one add that sets the carry flag; returns the
-// carry out of the top word.
+// cin in {0, 1} entered by one add that sets the carry flag (cin + 0xffffffff
+// carries exactly when cin = 1); returns the carry out of the top word.
 template <int N>
 struct CarryChainIn;
 
@@ -156,10 +156,10 @@ template <>
 struct CarryChainIn<1> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[1], const uint32_t (&a)[1],
                                                    const uint32_t (&b)[1], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %2, %5, -1;\n\taddc.cc.u32 %0, %3, %4;\n\taddc.u32 %1, 0, 0;"
-            : "=r"(s[0]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(b[0]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %2, %2, -1;\n\taddc.cc.u32 %0, %3, %4;\n\taddc.u32 %1, 0, 0;"
+            : "=r"(s[0]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(b[0]));
         return c;
     }
 };
@@ -168,10 +168,10 @@ template <>
 struct CarryChainIn<2> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[2], const uint32_t (&a)[2],
                                                    const uint32_t (&b)[2], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %3, %8, -1;\n\taddc.cc.u32 %0, %4, %6;\n\taddc.cc.u32 %1, %5, %7;\n\taddc.u32 %2, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %3, %3, -1;\n\taddc.cc.u32 %0, %4, %6;\n\taddc.cc.u32 %1, %5, %7;\n\taddc.u32 %2, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
         return c;
     }
 };
@@ -180,10 +180,10 @@ template <>
 struct CarryChainIn<3> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[3], const uint32_t (&a)[3],
                                                    const uint32_t (&b)[3], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %4, %11, -1;\n\taddc.cc.u32 %0, %5, %8;\n\taddc.cc.u32 %1, %6, %9;\n\taddc.cc.u32 %2, %7, %10;\n\taddc.u32 %3, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %4, %4, -1;\n\taddc.cc.u32 %0, %5, %8;\n\taddc.cc.u32 %1, %6, %9;\n\taddc.cc.u32 %2, %7, %10;\n\taddc.u32 %3, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
         return c;
     }
 };
@@ -192,10 +192,10 @@ template <>
 struct CarryChainIn<4> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[4], const uint32_t (&a)[4],
                                                    const uint32_t (&b)[4], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %5, %14, -1;\n\taddc.cc.u32 %0, %6, %10;\n\taddc.cc.u32 %1, %7, %11;\n\taddc.cc.u32 %2, %8, %12;\n\taddc.cc.u32 %3, %9, %13;\n\taddc.u32 %4, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %5, %5, -1;\n\taddc.cc.u32 %0, %6, %10;\n\taddc.cc.u32 %1, %7, %11;\n\taddc.cc.u32 %2, %8, %12;\n\taddc.cc.u32 %3, %9, %13;\n\taddc.u32 %4, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
         return c;
     }
 };
@@ -204,10 +204,10 @@ template <>
 struct CarryChainIn<5> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[5], const uint32_t (&a)[5],
                                                    const uint32_t (&b)[5], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %6, %17, -1;\n\taddc.cc.u32 %0, %7, %12;\n\taddc.cc.u32 %1, %8, %13;\n\taddc.cc.u32 %2, %9, %14;\n\taddc.cc.u32 %3, %10, %15;\n\taddc.cc.u32 %4, %11, %16;\n\taddc.u32 %5, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %6, %6, -1;\n\taddc.cc.u32 %0, %7, %12;\n\taddc.cc.u32 %1, %8, %13;\n\taddc.cc.u32 %2, %9, %14;\n\taddc.cc.u32 %3, %10, %15;\n\taddc.cc.u32 %4, %11, %16;\n\taddc.u32 %5, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]));
         return c;
     }
 };
@@ -216,10 +216,10 @@ template <>
 struct CarryChainIn<6> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[6], const uint32_t (&a)[6],
                                                    const uint32_t (&b)[6], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %7, %20, -1;\n\taddc.cc.u32 %0, %8, %14;\n\taddc.cc.u32 %1, %9, %15;\n\taddc.cc.u32 %2, %10, %16;\n\taddc.cc.u32 %3, %11, %17;\n\taddc.cc.u32 %4, %12, %18;\n\taddc.cc.u32 %5, %13, %19;\n\taddc.u32 %6, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %7, %7, -1;\n\taddc.cc.u32 %0, %8, %14;\n\taddc.cc.u32 %1, %9, %15;\n\taddc.cc.u32 %2, %10, %16;\n\taddc.cc.u32 %3, %11, %17;\n\taddc.cc.u32 %4, %12, %18;\n\taddc.cc.u32 %5, %13, %19;\n\taddc.u32 %6, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]));
         return c;
     }
 };
@@ -228,10 +228,10 @@ template <>
 struct CarryChainIn<7> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[7], const uint32_t (&a)[7],
                                                    const uint32_t (&b)[7], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %8, %23, -1;\n\taddc.cc.u32 %0, %9, %16;\n\taddc.cc.u32 %1, %10, %17;\n\taddc.cc.u32 %2, %11, %18;\n\taddc.cc.u32 %3, %12, %19;\n\taddc.cc.u32 %4, %13, %20;\n\taddc.cc.u32 %5, %14, %21;\n\taddc.cc.u32 %6, %15, %22;\n\taddc.u32 %7, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %8, %8, -1;\n\taddc.cc.u32 %0, %9, %16;\n\taddc.cc.u32 %1, %10, %17;\n\taddc.cc.u32 %2, %11, %18;\n\taddc.cc.u32 %3, %12, %19;\n\taddc.cc.u32 %4, %13, %20;\n\taddc.cc.u32 %5, %14, %21;\n\taddc.cc.u32 %6, %15, %22;\n\taddc.u32 %7, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]));
         return c;
     }
 };
@@ -240,10 +240,10 @@ template <>
 struct CarryChainIn<8> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[8], const uint32_t (&a)[8],
                                                    const uint32_t (&b)[8], uint32_t cin) {
-        uint32_t c, t;
-        asm("add.cc.u32 %9, %26, -1;\n\taddc.cc.u32 %0, %10, %18;\n\taddc.cc.u32 %1, %11, %19;\n\taddc.cc.u32 %2, %12, %20;\n\taddc.cc.u32 %3, %13, %21;\n\taddc.cc.u32 %4, %14, %22;\n\taddc.cc.u32 %5, %15, %23;\n\taddc.cc.u32 %6, %16, %24;\n\taddc.cc.u32 %7, %17, %25;\n\taddc.u32 %8, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(cin));
+        uint32_t c;
+        asm("add.cc.u32 %9, %9, -1;\n\taddc.cc.u32 %0, %10, %18;\n\taddc.cc.u32 %1, %11, %19;\n\taddc.cc.u32 %2, %12, %20;\n\taddc.cc.u32 %3, %13, %21;\n\taddc.cc.u32 %4, %14, %22;\n\taddc.cc.u32 %5, %15, %23;\n\taddc.cc.u32 %6, %16, %24;\n\taddc.cc.u32 %7, %17, %25;\n\taddc.u32 %8, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
         return c;
     }
 };
@@ -259,10 +259,10 @@ template <>
 struct CarryChainMadIn<1> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[1], const uint32_t (&a)[1],
                                                    const uint32_t (&b)[1], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %2, %5, -1;\n\tmadc.lo.cc.u32 %0, %3, %6, %4;\n\taddc.u32 %1, 0, 0;"
-            : "=r"(s[0]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(b[0]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %2, %2, -1;\n\tmadc.lo.cc.u32 %0, %3, %5, %4;\n\taddc.u32 %1, 0, 0;"
+            : "=r"(s[0]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(b[0]), "r"(one));
         return c;
     }
 };
@@ -271,10 +271,10 @@ template <>
 struct CarryChainMadIn<2> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[2], const uint32_t (&a)[2],
                                                    const uint32_t (&b)[2], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %3, %8, -1;\n\tmadc.lo.cc.u32 %0, %4, %9, %6;\n\tmadc.lo.cc.u32 %1, %5, %9, %7;\n\taddc.u32 %2, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %3, %3, -1;\n\tmadc.lo.cc.u32 %0, %4, %8, %6;\n\tmadc.lo.cc.u32 %1, %5, %8, %7;\n\taddc.u32 %2, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]), "r"(one));
         return c;
     }
 };
@@ -283,10 +283,10 @@ template <>
 struct CarryChainMadIn<3> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[3], const uint32_t (&a)[3],
                                                    const uint32_t (&b)[3], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %4, %11, -1;\n\tmadc.lo.cc.u32 %0, %5, %12, %8;\n\tmadc.lo.cc.u32 %1, %6, %12, %9;\n\tmadc.lo.cc.u32 %2, %7, %12, %10;\n\taddc.u32 %3, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %4, %4, -1;\n\tmadc.lo.cc.u32 %0, %5, %11, %8;\n\tmadc.lo.cc.u32 %1, %6, %11, %9;\n\tmadc.lo.cc.u32 %2, %7, %11, %10;\n\taddc.u32 %3, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(one));
         return c;
     }
 };
@@ -295,10 +295,10 @@ template <>
 struct CarryChainMadIn<4> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[4], const uint32_t (&a)[4],
                                                    const uint32_t (&b)[4], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %5, %14, -1;\n\tmadc.lo.cc.u32 %0, %6, %15, %10;\n\tmadc.lo.cc.u32 %1, %7, %15, %11;\n\tmadc.lo.cc.u32 %2, %8, %15, %12;\n\tmadc.lo.cc.u32 %3, %9, %15, %13;\n\taddc.u32 %4, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %5, %5, -1;\n\tmadc.lo.cc.u32 %0, %6, %14, %10;\n\tmadc.lo.cc.u32 %1, %7, %14, %11;\n\tmadc.lo.cc.u32 %2, %8, %14, %12;\n\tmadc.lo.cc.u32 %3, %9, %14, %13;\n\taddc.u32 %4, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(one));
         return c;
     }
 };
@@ -307,10 +307,10 @@ template <>
 struct CarryChainMadIn<5> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[5], const uint32_t (&a)[5],
                                                    const uint32_t (&b)[5], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %6, %17, -1;\n\tmadc.lo.cc.u32 %0, %7, %18, %12;\n\tmadc.lo.cc.u32 %1, %8, %18, %13;\n\tmadc.lo.cc.u32 %2, %9, %18, %14;\n\tmadc.lo.cc.u32 %3, %10, %18, %15;\n\tmadc.lo.cc.u32 %4, %11, %18, %16;\n\taddc.u32 %5, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %6, %6, -1;\n\tmadc.lo.cc.u32 %0, %7, %17, %12;\n\tmadc.lo.cc.u32 %1, %8, %17, %13;\n\tmadc.lo.cc.u32 %2, %9, %17, %14;\n\tmadc.lo.cc.u32 %3, %10, %17, %15;\n\tmadc.lo.cc.u32 %4, %11, %17, %16;\n\taddc.u32 %5, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(one));
         return c;
     }
 };
@@ -319,10 +319,10 @@ template <>
 struct CarryChainMadIn<6> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[6], const uint32_t (&a)[6],
                                                    const uint32_t (&b)[6], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %7, %20, -1;\n\tmadc.lo.cc.u32 %0, %8, %21, %14;\n\tmadc.lo.cc.u32 %1, %9, %21, %15;\n\tmadc.lo.cc.u32 %2, %10, %21, %16;\n\tmadc.lo.cc.u32 %3, %11, %21, %17;\n\tmadc.lo.cc.u32 %4, %12, %21, %18;\n\tmadc.lo.cc.u32 %5, %13, %21, %19;\n\taddc.u32 %6, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %7, %7, -1;\n\tmadc.lo.cc.u32 %0, %8, %20, %14;\n\tmadc.lo.cc.u32 %1, %9, %20, %15;\n\tmadc.lo.cc.u32 %2, %10, %20, %16;\n\tmadc.lo.cc.u32 %3, %11, %20, %17;\n\tmadc.lo.cc.u32 %4, %12, %20, %18;\n\tmadc.lo.cc.u32 %5, %13, %20, %19;\n\taddc.u32 %6, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(one));
         return c;
     }
 };
@@ -331,10 +331,10 @@ template <>
 struct CarryChainMadIn<7> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[7], const uint32_t (&a)[7],
                                                    const uint32_t (&b)[7], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %8, %23, -1;\n\tmadc.lo.cc.u32 %0, %9, %24, %16;\n\tmadc.lo.cc.u32 %1, %10, %24, %17;\n\tmadc.lo.cc.u32 %2, %11, %24, %18;\n\tmadc.lo.cc.u32 %3, %12, %24, %19;\n\tmadc.lo.cc.u32 %4, %13, %24, %20;\n\tmadc.lo.cc.u32 %5, %14, %24, %21;\n\tmadc.lo.cc.u32 %6, %15, %24, %22;\n\taddc.u32 %7, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %8, %8, -1;\n\tmadc.lo.cc.u32 %0, %9, %23, %16;\n\tmadc.lo.cc.u32 %1, %10, %23, %17;\n\tmadc.lo.cc.u32 %2, %11, %23, %18;\n\tmadc.lo.cc.u32 %3, %12, %23, %19;\n\tmadc.lo.cc.u32 %4, %13, %23, %20;\n\tmadc.lo.cc.u32 %5, %14, %23, %21;\n\tmadc.lo.cc.u32 %6, %15, %23, %22;\n\taddc.u32 %7, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(one));
         return c;
     }
 };
@@ -343,10 +343,10 @@ template <>
 struct CarryChainMadIn<8> {
     static __device__ __forceinline__ uint32_t add(uint32_t (&s)[8], const uint32_t (&a)[8],
                                                    const uint32_t (&b)[8], uint32_t cin, uint32_t one) {
-        uint32_t c, t;
-        asm("add.cc.u32 %9, %26, -1;\n\tmadc.lo.cc.u32 %0, %10, %27, %18;\n\tmadc.lo.cc.u32 %1, %11, %27, %19;\n\tmadc.lo.cc.u32 %2, %12, %27, %20;\n\tmadc.lo.cc.u32 %3, %13, %27, %21;\n\tmadc.lo.cc.u32 %4, %14, %27, %22;\n\tmadc.lo.cc.u32 %5, %15, %27, %23;\n\tmadc.lo.cc.u32 %6, %16, %27, %24;\n\tmadc.lo.cc.u32 %7, %17, %27, %25;\n\taddc.u32 %8, 0, 0;"
-            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(c), "=r"(t)
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(cin), "r"(one));
+        uint32_t c;
+        asm("add.cc.u32 %9, %9, -1;\n\tmadc.lo.cc.u32 %0, %10, %26, %18;\n\tmadc.lo.cc.u32 %1, %11, %26, %19;\n\tmadc.lo.cc.u32 %2, %12, %26, %20;\n\tmadc.lo.cc.u32 %3, %13, %26, %21;\n\tmadc.lo.cc.u32 %4, %14, %26, %22;\n\tmadc.lo.cc.u32 %5, %15, %26, %23;\n\tmadc.lo.cc.u32 %6, %16, %26, %24;\n\tmadc.lo.cc.u32 %7, %17, %26, %25;\n\taddc.u32 %8, 0, 0;"
+            : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(c), "+r"(cin)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(one));
         return c;
     }
 };

@@ -10,24 +10,26 @@
 // true value, returns some d_k with d <= d_k; and d_k <= k implies d_k = d.
 // So the result is accepted exactly when d_k <= k, else k doubles.
 //
-// Kernel: one lane per pair; the longer sequence sits on the rows.  The lane
-// keeps a window of WB consecutive 32-row words of the bit-vector column in
-// registers (Pv, Mv and the query's bit planes, from which each column's
-// match mask is formed with a few logic ops).  The window starts at the top
-// and moves down one word whenever the band's first row passes a word
-// boundary (at most once per 32 columns): the word leaving at the top adds
-// its vertical deltas to T, the value of D on the row just above the window,
-// and a fresh word (all vertical deltas +1) enters at the bottom.  The rows
-// above the window are taken to grow by +1 per column (exact for row 0, an
-// upper bound elsewhere), which is the carry-in of the window's top word; the
-// rows below it start from the +1 vertical deltas of a fresh word, also an
-// upper bound.  The window moves at warp-uniform points (every 32 steps of
-// the warp's loop, each lane by as many words as its band has moved), so
-// lanes never run the move separately, and the planes of the next word to
-// enter are loaded one move ahead.  Trailing the band by at most one word,
-// the window covers the band of half-width k_w = 32 (WB - 2) - 1, so an
-// accepted pair is certified for k_w >= k.
-// At the end D[m][n] = T + popc(Pv) - popc(Mv) over the window's rows <= m.
+// Kernel: a group of G lanes per pair (32 / G pairs per warp).  The rows
+// are cut into blocks of H = 32 WPL rows; lane l of a group holds blocks
+// l, l + G, l + 2G, ... one at a time, each as WPL words of Pv, Mv and the
+// query's bit planes in registers.  Block b computes column j at the group's
+// step j + b, one step behind the block above it (a skewed pipeline), so the
+// carry into its top row and the shifted-in Ph/Mh bits of column j arrive
+// from the lane above by one shuffle per step; the carry of the addition out
+// of a row equals that row's Mh bit, so the two Ph/Mh bits are all that
+// crosses.  Block b is live on the columns where its rows meet the band,
+// [max(1, bH + 1 + dlo), min(n, bH + H + dhi)] for the band diagonals
+// [dlo, dhi]; before its first column it holds the upper bound "+1 on every
+// row" (D[i][j] <= D[i-1][j] + 1), and once the block above it has passed its
+// last column it takes that row to grow by +1 per column (D[i][j] <=
+// D[i][j-1] + 1), the top-of-matrix boundary.  The value of D on the row just
+// above a block (T) is handed down with the carries when the block above
+// leaves.  A lane whose block leaves takes its next block, so the group
+// covers any band with dhi - dlo <= (G - 1) H: the computed rows per column
+// follow the requested band, not the group's capacity.
+// At column n each live block adds its vertical deltas over rows <= m (the
+// top one also its T), and the group's sum is D[m][n].
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,23 +40,21 @@
 
 namespace msa {
 
-constexpr int kBandBuckets = 18;
-// buckets 0..6: one lane per pair, window of WB words in registers;
-// buckets 7..17: G lanes per pair, window of G x WPL words, (G, WPL) =
-// (4,4) (8,3) (8,4) (8,5) (8,6) (16,4) (16,5) (16,6) (16,8) (32,5) (32,6)
-// half-widths: lane buckets 32 (WB - 2) - 1, group buckets 32 (G WPL - 1) - 1
-#define BAND_KW_LIST {-1, 31, 63, 95, 127, 191, 255, 479, 735, 991, 1247, 1503, 2015, 2527, 3039, 4063, 5087, 6111}
-__constant__ int kBandKW[kBandBuckets] = BAND_KW_LIST;
-static const int kBandKWHost[kBandBuckets] = BAND_KW_LIST;
-__constant__ int kBandCap[kBandBuckets] = {2, 3, 4, 5, 6, 8, 10, 16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192};
-static const int kBandCapHost[kBandBuckets] = {2, 3, 4, 5, 6, 8, 10, 16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192};
-// a window taller than this share of the column costs more than the full DP
-// (the multi-lane window pays carry-lookahead and ballots per column), so
-// such pairs go straight to the full bit-vector DP
-constexpr float kBandMaxShare = 0.6f;
+// (G, WPL) of the pipelined kernel, in increasing cost per step (G lanes x
+// about 10 WPL + 26 instructions) and increasing capacity (G - 1) x 32 WPL;
+// a pair goes to the first one that holds its band.
+constexpr int kBandBuckets = 24;
+#define BAND_G_LIST {2, 2, 2, 2, 2, 4, 4, 4, 4, 4, 8, 8, 8, 8, 8, 16, 16, 16, 16, 16, 32, 32, 32, 32}
+#define BAND_WPL_LIST {2, 3, 4, 6, 8, 3, 4, 5, 6, 8, 4, 5, 6, 7, 8, 4, 5, 6, 7, 8, 4, 5, 6, 8}
+__constant__ int kBandG[kBandBuckets] = BAND_G_LIST;
+__constant__ int kBandWPL[kBandBuckets] = BAND_WPL_LIST;
+static const int kBandGHost[kBandBuckets] = BAND_G_LIST;
+static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
+// a band whose rows per column (k + H) exceed this share of the column goes
+// to the full bit-vector DP, whose kernels need no band bookkeeping
+constexpr float kBandMaxShare = 0.75f;
 constexpr int kBandRounds = 8;
-static int band_buckets(int) { return kBandBuckets; }
-
+constexpr int kBandThreads = 128;
 
 struct BandArgs {
     const uint32_t *planes;
@@ -71,330 +71,231 @@ struct BandArgs {
     int32_t *next_list;       // failures
     int32_t *next_count;
     int32_t bucket;
-    uint32_t one, two;        // 1 and 2, as runtime values (see bv_word)
 };
 
-template <int WB, int B>
-__global__ void __launch_bounds__(128) band_kernel(BandArgs a) {
-    const int cnt = a.bcount[a.bucket];
-    const int32_t *list = a.blist + a.boff[a.bucket];
-    int32_t *counter = a.bcounter + a.bucket;
-    constexpr int KW = 32 * (WB - 2) - 1;
-    const uint32_t one = a.one, two = a.two;
-    uint32_t Pv[WB], Mv[WB], Pl[WB][B], Pn[B];
-    // per-lane pair state; a warp-synchronous loop (a vote over the whole
-    // warp each iteration) so that lanes with pairs of different lengths and
-    // band positions rejoin before every column
-    int p = -1, m = 0, n = 0, j = 0, wlo = 0, wmax = 0, dmax = 0, T = 0, c_next = 0;
-    bool full = true, has = false, more = true;
-    int64_t qa = 0;
-    const uint8_t *tc = nullptr;
-    for (uint32_t it = 0;; ++it) {
-        if (!has && more) {
-            const int k = atomicAdd(counter, 1);
-            if (k >= cnt) {
-                more = false;
-            } else {
-                p = list[k];
-                const int q = a.pairs[2 * p], t = a.pairs[2 * p + 1];
-                int64_t qb = a.offs[q + 1], ta = a.offs[t], tb = a.offs[t + 1];
-                qa = a.offs[q];
-                if (qb - qa < tb - ta) {     // longer sequence on the rows
-                    int64_t y = qa; qa = ta; ta = y;
-                    y = qb; qb = tb; tb = y;
-                }
-                m = (int)(qb - qa);
-                n = (int)(tb - ta);
-                const int W = max(1, (m + 31) / 32);
-                full = W <= WB;                        // the window holds the whole column: plain DP
-                dmax = (n - m + KW) >> 1;              // floor((n - m + k_w) / 2), >= 0 since k_w >= m - n
-                wmax = full ? 0 : W - WB;
-                tc = a.codes + ta;
-                wlo = 0;
-                T = 0;
-                j = 0;
-                c_next = n > 0 ? __ldg(tc) : 0;
-#pragma unroll
-                for (int s = 0; s < WB; ++s) {
-                    Pv[s] = kFull;
-                    Mv[s] = 0u;
-                    uint32_t mask;
-                    uint32_t pl[B];
-                    query_planes<B>(a.planes, qa, m, s, pl, mask);
-#pragma unroll
-                    for (int b = 0; b < B; ++b) Pl[s][b] = pl[b];
-                }
-                {
-                    uint32_t mask;
-                    query_planes<B>(a.planes, qa, m, WB, Pn, mask);
-                }
-                has = true;
-            }
-        }
-        if (!__any_sync(kFull, has)) break;
-        // warp-uniform window moves: every 32 iterations each lane catches its
-        // window up with the band's first row for its next column
-        if ((it & 31u) == 0u && has && !full) {
-            const int num = j - dmax;            // next column is j + 1
-            const int target = num < 0 ? 0 : min(num >> 5, wmax);
-            while (wlo < target) {
-                T += __popc(Pv[0]) - __popc(Mv[0]);
-#pragma unroll
-                for (int s = 0; s < WB - 1; ++s) {
-                    Pv[s] = Pv[s + 1];
-                    Mv[s] = Mv[s + 1];
-#pragma unroll
-                    for (int b = 0; b < B; ++b) Pl[s][b] = Pl[s + 1][b];
-                }
-                ++wlo;
-                Pv[WB - 1] = kFull;
-                Mv[WB - 1] = 0u;
-#pragma unroll
-                for (int b = 0; b < B; ++b) Pl[WB - 1][b] = Pn[b];
-                uint32_t mask;
-                query_planes<B>(a.planes, qa, m, wlo + WB, Pn, mask);   // one move ahead
-            }
-        }
-        if (!has) continue;
-        if (j < n) {
-            ++j;
-            T += 1;
-            const int c = c_next;
-            if (j < n) c_next = __ldg(tc + j);
-            uint32_t x[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) x[b] = ((c >> b) & 1) ? 0u : kFull;
-            uint32_t ph_in = 1u, mh_in = 0u;
-#pragma unroll
-            for (int s = 0; s < WB; ++s) {
-                uint32_t eq = Pl[s][0] ^ x[0];
-#pragma unroll
-                for (int b = 1; b < B; ++b) eq &= Pl[s][b] ^ x[b];
-                bv_word(eq, Pv[s], Mv[s], ph_in, mh_in, one, two);
-            }
-        }
-        if (j == n) {
-            // T = D[32 wlo][n] (exactly n while the window still starts at row 0)
-            int d = T;
-#pragma unroll
-            for (int s = 0; s < WB; ++s) {
-                const int rem = m - 32 * (wlo + s);
-                const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-                d += __popc(Pv[s] & mk) - __popc(Mv[s] & mk);
-            }
-            if (full || d <= KW) {
-                a.d_out[p] = d;
-                a.k_used[p] = full ? max(m, n) : KW;
-            } else {
-                a.k_cur[p] = 2 * KW + 1;
-                a.next_list[atomicAdd(a.next_count, 1)] = p;
-            }
-            has = false;
-        }
-    }
-}
+// Per-lane match masks of DNA blocks in shared memory, [symbol][word][thread]
+// (thread-minor, so a warp's loads hit 32 distinct banks whatever symbols
+// its lanes read); other alphabets form each column's mask from the bit
+// planes held in registers.
+template <int WPL, int B>
+struct BandEq {
+    static constexpr bool kShared = B == 2;
+    static constexpr int kSigma = 4;
+    uint32_t pl[kShared ? 1 : WPL][kShared ? 1 : B];
+};
 
-// Group banded kernel: G lanes per pair (32 / G pairs per warp), the band
-// window of G x WPL words spread over the group's lanes (lane l of a group
-// holds window words l*WPL .. l*WPL+WPL-1); all lanes of the warp step in
-// lockstep, each group on its own pair and column.  The carry of a column's
-// addition crosses the group's lanes by carry-lookahead on two ballots
-// (generate / propagate of each lane's WPL-word sum), the Ph/Mh top bits by
-// two more; a group's window moves down one word (shuffled up from the next
-// lane of the group) when its band's first row passes a word boundary, so
-// the window covers the band of half-width 32 (G WPL - 1) - 1.
-template <int G, int WPL, int B>
-__global__ void __launch_bounds__(128) band_group_kernel(BandArgs a) {
-    constexpr int NW = G * WPL;
-    constexpr int KW = 32 * (NW - 1) - 1;
-    constexpr uint32_t GM = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;
-    const int gbase = lane - gl;
-    const int cnt = a.bcount[a.bucket];
-    const int32_t *list = a.blist + a.boff[a.bucket];
-    int32_t *counter = a.bcounter + a.bucket;
-    uint32_t Pv[WPL], Mv[WPL], Pl[WPL][B], Pn[B];
+// Takes block bk of the current pair: its live columns, the last column of
+// the block above (0 for the top block), fresh +1 vertical deltas, the
+// query's match masks of its rows and the symbol of its first column.
+template <int WPL, int B>
+__device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m, int n, const uint32_t *planes,
+                                                 int64_t qa, const uint8_t *tc, int &js, int &je, int &jep,
+                                                 uint32_t (&Pv)[WPL], uint32_t (&Mv)[WPL], BandEq<WPL, B> &E,
+                                                 uint32_t *sPeq, int &c_next) {
+    constexpr int H = 32 * WPL;
+    js = max(1, bk * H + 1 + dlo);
+    je = min(n, bk * H + H + dhi);
+    jep = bk == 0 ? 0 : min(n, bk * H + dhi);
 #pragma unroll
     for (int w = 0; w < WPL; ++w) {
         Pv[w] = kFull;
         Mv[w] = 0u;
+        uint32_t pl[B], mask;
+        query_planes<B>(planes, qa, m, bk * WPL + w, pl, mask);
+        if constexpr (BandEq<WPL, B>::kShared) {
 #pragma unroll
-        for (int b = 0; b < B; ++b) Pl[w][b] = 0u;
+            for (int c = 0; c < 4; ++c) sPeq[(c * WPL + w) * kBandThreads] = match_mask<B, 4>(pl, mask, c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < B; ++q) E.pl[w][q] = pl[q];
+        }
     }
+    c_next = __ldg(tc + js - 1);
+}
+
+template <int G, int WPL, int B>
+__global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "group size");
+    constexpr int H = 32 * WPL;
+    constexpr bool kShared = BandEq<WPL, B>::kShared;
+    __shared__ uint32_t sPeqAll[kShared ? 4 * WPL * kBandThreads : 1];
+    uint32_t *sPeq = sPeqAll + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gbase = lane - gl;
+    const int src = gbase + ((gl + G - 1) & (G - 1));    // the lane holding the block above
+    const int cnt = a.bcount[a.bucket];
+    const int32_t *list = a.blist + a.boff[a.bucket];
+    int32_t *counter = a.bcounter + a.bucket;
+    uint32_t Pv[WPL], Mv[WPL];
+    BandEq<WPL, B> E;
 #pragma unroll
-    for (int b = 0; b < B; ++b) Pn[b] = 0u;
-    int p = -1, m = 0, n = 0, j = 0, wlo = 0, wmax = 0, dmax = 0, T = 0, c_next = 0;
-    bool full = true, has = false, more = true;
+    for (int w = 0; w < WPL; ++w) {
+        Pv[w] = kFull;
+        Mv[w] = 0u;
+    }
+    if constexpr (!kShared) {
+#pragma unroll
+        for (int w = 0; w < WPL; ++w)
+#pragma unroll
+            for (int q = 0; q < B; ++q) E.pl[w][q] = 0u;
+    }
+    // per group (the same in each of its lanes)
+    int p = -1, m = 0, n = 0, k = 0, dlo = 0, dhi = 0, bm = -1, t = 0, tend = 0;
+    bool has = false, more = true;
     int64_t qa = 0;
     const uint8_t *tc = nullptr;
+    // per lane: its block, that block's live columns, the last column of the
+    // block above, T, the lane's share of D[m][n] and the word sent down
+    int bk = 0, js = 1, je = 0, jep = 0, Tb = 0, acc = 0, c_next = 0;
+    uint32_t out = 0u;
+    bool fin = false;
     while (true) {
-        // 1. groups without a pair take the next one
-        const bool need = !has && more;
-        if (__any_sync(kFull, need)) {
-            int k = 0;
-            if (need && gl == 0) k = atomicAdd(counter, 1);
-            k = __shfl_sync(kFull, k, gbase);
-            if (need) {
-                if (k >= cnt) {
-                    more = false;
-                } else {
-                    p = list[k];
-                    const int q = a.pairs[2 * p], t = a.pairs[2 * p + 1];
-                    int64_t qb = a.offs[q + 1], ta = a.offs[t], tb = a.offs[t + 1];
-                    qa = a.offs[q];
-                    if (qb - qa < tb - ta) {     // longer sequence on the rows
-                        int64_t y = qa; qa = ta; ta = y;
-                        y = qb; qb = tb; tb = y;
+        // 1. groups whose pair is done report it; groups without a pair take
+        //    the next one (one vote per step: this runs only when some group
+        //    of the warp finished, and once at the start)
+        if (__any_sync(kFull, fin || (!has && more))) {
+            if (__any_sync(kFull, fin)) {
+                int d = fin ? acc : 0;
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o, G);
+                if (fin) {
+                    if (gl == 0) {
+                        if (d <= k) {
+                            a.d_out[p] = d;
+                            a.k_used[p] = k;
+                        } else {
+                            // d_k > k is an upper bound of the distance, so a
+                            // band of d_k certifies; the band at most doubles
+                            a.k_cur[p] = min(d, 2 * k + 1);
+                            a.next_list[atomicAdd(a.next_count, 1)] = p;
+                        }
                     }
-                    m = (int)(qb - qa);
-                    n = (int)(tb - ta);
-                    const int W = max(1, (m + 31) / 32);
-                    full = W <= NW;
-                    dmax = (n - m + KW) >> 1;
-                    wmax = full ? 0 : W - NW;
-                    tc = a.codes + ta;
-                    wlo = 0;
-                    T = 0;
-                    j = 0;
-                    c_next = n > 0 ? __ldg(tc) : 0;
+                    has = false;
+                    fin = false;
+                }
+            }
+            const bool need = !has && more;
+            if (__any_sync(kFull, need)) {
+                int i = 0;
+                if (need && gl == 0) i = atomicAdd(counter, 1);
+                i = __shfl_sync(kFull, i, gbase);
+                if (need) {
+                    if (i >= cnt) {
+                        more = false;
+                    } else {
+                        p = list[i];
+                        const int q = a.pairs[2 * p], r = a.pairs[2 * p + 1];
+                        int64_t qb = a.offs[q + 1], ta = a.offs[r], tb = a.offs[r + 1];
+                        qa = a.offs[q];
+                        if (qb - qa < tb - ta) {     // longer sequence on the rows
+                            int64_t y = qa; qa = ta; ta = y;
+                            y = qb; qb = tb; tb = y;
+                        }
+                        m = (int)(qb - qa);
+                        n = (int)(tb - ta);
+                        k = min(max(a.k_cur[p], m - n), m);
+                        dlo = -((k + m - n) >> 1);   // ceil((n - m - k) / 2)
+                        dhi = (n - m + k) >> 1;      // floor((n - m + k) / 2)
+                        tc = a.codes + ta;
+                        t = 0;
+                        Tb = 0;
+                        acc = 0;
+                        out = 0u;
+                        if (n == 0) {                // no columns: D[m][0] = m
+                            if (gl == 0) {
+                                a.d_out[p] = m;
+                                a.k_used[p] = k;
+                            }
+                        } else {
+                            bm = (m - 1) / H;
+                            tend = n + bm;
+                            bk = gl;
+                            if (bk <= bm)
+                                band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, js, je, jep, Pv, Mv,
+                                                         E, sPeq, c_next);
+                            has = true;
+                        }
+                    }
+                }
+            }
+            if (!__any_sync(kFull, has)) break;
+        }
+        // 2. one pipeline step: block bk computes column t - bk
+        const uint32_t in = __shfl_sync(kFull, out, src);
+        if (has) {
+            ++t;
+            fin = t == tend;
+            const int j = t - bk;
+            if (bk <= bm) {
+                if (j == jep) Tb = (int)(in >> 2);          // the block above leaves after this column
+                if (j >= js && j <= je) {
+                    const bool top = j > jep;
+                    uint32_t ph_in = in & 1u, mh_in = (in >> 1) & 1u;
+                    if (top) {
+                        ++Tb;
+                        ph_in = 1u;
+                        mh_in = 0u;
+                    }
+                    const int c = c_next;
+                    if (j < je) c_next = __ldg(tc + j);
+                    uint32_t eq[WPL], u[WPL], sum[WPL], pv[WPL];
+                    if constexpr (kShared) {
+                        const uint32_t *row = sPeq + (c & 3) * WPL * kBandThreads;
+#pragma unroll
+                        for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
+                    } else {
+                        uint32_t x[B];
+#pragma unroll
+                        for (int q = 0; q < B; ++q) x[q] = ((c >> q) & 1) ? 0u : kFull;
+#pragma unroll
+                        for (int w = 0; w < WPL; ++w) {
+                            uint32_t e = E.pl[w][0] ^ x[0];
+#pragma unroll
+                            for (int q = 1; q < B; ++q) e &= E.pl[w][q] ^ x[q];
+                            eq[w] = e;
+                        }
+                    }
 #pragma unroll
                     for (int w = 0; w < WPL; ++w) {
-                        Pv[w] = kFull;
-                        Mv[w] = 0u;
-                        uint32_t mask;
-                        uint32_t pl[B];
-                        query_planes<B>(a.planes, qa, m, gl * WPL + w, pl, mask);
-#pragma unroll
-                        for (int b = 0; b < B; ++b) Pl[w][b] = pl[b];
+                        pv[w] = Pv[w];
+                        u[w] = eq[w] & pv[w];
                     }
-                    if (gl == G - 1) {
-                        uint32_t mask;
-                        query_planes<B>(a.planes, qa, m, NW, Pn, mask);
+                    CarryChainIn<WPL>::add(sum, u, pv, mh_in);
+                    uint32_t php = ph_in << 31, mhp = mh_in << 31;
+#pragma unroll
+                    for (int w = 0; w < WPL; ++w) {
+                        const uint32_t xh = (sum[w] ^ pv[w]) | eq[w];
+                        const uint32_t ph = Mv[w] | ~(xh | pv[w]);
+                        const uint32_t mh = pv[w] & xh;
+                        const uint32_t phs = __funnelshift_l(php, ph, 1);
+                        const uint32_t mhs = __funnelshift_l(mhp, mh, 1);
+                        php = ph;
+                        mhp = mh;
+                        const uint32_t xv = eq[w] | Mv[w];
+                        Pv[w] = mhs | ~(xv | phs);
+                        Mv[w] = phs & xv;
                     }
-                    has = true;
-                }
-            }
-        }
-        if (!__any_sync(kFull, has)) break;
-        // 2. window moves before the next column (j + 1)
-        bool move = false;
-        if (has && !full && j < n) {
-            const int num = j - dmax;
-            const int target = num < 0 ? 0 : min(num >> 5, wmax);
-            move = target > wlo;
-        }
-        if (__any_sync(kFull, move)) {
-            const int dT = __shfl_sync(kFull, __popc(Pv[0]) - __popc(Mv[0]), gbase);
-            const uint32_t pv0 = __shfl_down_sync(kFull, Pv[0], 1, G);
-            const uint32_t mv0 = __shfl_down_sync(kFull, Mv[0], 1, G);
-            uint32_t pl0[B];
+                    out = (php >> 31) | ((mhp >> 31) << 1);
+                    if (j == je) {
+                        // the block's last column: hand D on its bottom row to
+                        // the block below, add its share at column n, move on
+                        int delta = 0, part = 0;
 #pragma unroll
-            for (int b = 0; b < B; ++b) pl0[b] = __shfl_down_sync(kFull, Pl[0][b], 1, G);
-            if (move) {
-                T += dT;
-#pragma unroll
-                for (int w = 0; w < WPL - 1; ++w) {
-                    Pv[w] = Pv[w + 1];
-                    Mv[w] = Mv[w + 1];
-#pragma unroll
-                    for (int b = 0; b < B; ++b) Pl[w][b] = Pl[w + 1][b];
-                }
-                ++wlo;
-                if (gl == G - 1) {
-                    Pv[WPL - 1] = kFull;
-                    Mv[WPL - 1] = 0u;
-#pragma unroll
-                    for (int b = 0; b < B; ++b) Pl[WPL - 1][b] = Pn[b];
-                    uint32_t mask;
-                    query_planes<B>(a.planes, qa, m, wlo + NW, Pn, mask);   // one move ahead
-                } else {
-                    Pv[WPL - 1] = pv0;
-                    Mv[WPL - 1] = mv0;
-#pragma unroll
-                    for (int b = 0; b < B; ++b) Pl[WPL - 1][b] = pl0[b];
-                }
-            }
-        }
-        // 3. one column for every group that has one
-        const bool act = has && j < n;
-        const int c = c_next;
-        uint32_t x[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) x[b] = ((c >> b) & 1) ? 0u : kFull;
-        uint32_t eq[WPL], u[WPL], s0[WPL];
-#pragma unroll
-        for (int w = 0; w < WPL; ++w) {
-            uint32_t e = Pl[w][0] ^ x[0];
-#pragma unroll
-            for (int b = 1; b < B; ++b) e &= Pl[w][b] ^ x[b];
-            eq[w] = e;
-            u[w] = e & Pv[w];
-        }
-        // the lane's words added on the carry chain with carry-in 0
-        const uint32_t cy = CarryChain<WPL>::add(s0, u, Pv);
-        uint32_t all = kFull;
-#pragma unroll
-        for (int w = 0; w < WPL; ++w) all &= s0[w];
-        // carry into each lane of the group: c_{l+1} = g_l | (p_l & c_l), c_0 = 0
-        const uint32_t Gb = (__ballot_sync(kFull, act && cy != 0u) >> gbase) & GM;
-        const uint32_t Pb = (__ballot_sync(kFull, act && all == kFull) >> gbase) & GM;
-        const uint32_t GP = Gb | Pb;
-        const uint32_t carries = (Gb + GP) ^ GP ^ Gb;
-        const uint32_t ci = gl == 0 ? 0u : (carries >> gl) & 1u;
-        CarryChain<WPL>::inc(s0, ci);
-        uint32_t ph[WPL], mh[WPL];
-#pragma unroll
-        for (int w = 0; w < WPL; ++w) {
-            const uint32_t xh = (s0[w] ^ Pv[w]) | eq[w];
-            ph[w] = Mv[w] | ~(xh | Pv[w]);
-            mh[w] = Pv[w] & xh;
-        }
-        const uint32_t PT = (__ballot_sync(kFull, (ph[WPL - 1] >> 31) != 0u) >> gbase) & GM;
-        const uint32_t MT = (__ballot_sync(kFull, (mh[WPL - 1] >> 31) != 0u) >> gbase) & GM;
-        if (act) {
-            uint32_t ph_in = gl == 0 ? 1u : (PT >> (gl - 1)) & 1u;
-            uint32_t mh_in = gl == 0 ? 0u : (MT >> (gl - 1)) & 1u;
-#pragma unroll
-            for (int w = 0; w < WPL; ++w) {
-                const uint32_t phs = (ph[w] << 1) | ph_in;
-                const uint32_t mhs = (mh[w] << 1) | mh_in;
-                ph_in = ph[w] >> 31;
-                mh_in = mh[w] >> 31;
-                const uint32_t xv = eq[w] | Mv[w];
-                Pv[w] = mhs | ~(xv | phs);
-                Mv[w] = phs & xv;
-            }
-            ++j;
-            T += 1;
-            if (j < n) c_next = __ldg(tc + j);
-        }
-        // 4. groups whose pair is done report it
-        const bool fin = has && j == n;
-        if (__any_sync(kFull, fin)) {
-            int part = 0;
-            if (fin) {
-#pragma unroll
-                for (int w = 0; w < WPL; ++w) {
-                    const int rem = m - 32 * (wlo + gl * WPL + w);
-                    const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-                    part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
-                }
-            }
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, G);
-            if (fin) {
-                if (gl == 0) {
-                    const int d = T + part;
-                    if (full || d <= KW) {
-                        a.d_out[p] = d;
-                        a.k_used[p] = full ? max(m, n) : KW;
-                    } else {
-                        a.k_cur[p] = 2 * KW + 1;
-                        a.next_list[atomicAdd(a.next_count, 1)] = p;
+                        for (int w = 0; w < WPL; ++w) {
+                            const int rem = m - 32 * (bk * WPL + w);
+                            const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                            delta += __popc(Pv[w]) - __popc(Mv[w]);
+                            part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
+                        }
+                        out |= (uint32_t)(Tb + delta) << 2;
+                        if (j == n) acc += (top ? Tb : 0) + part;
+                        bk += G;
+                        if (bk <= bm)
+                            band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, js, je, jep, Pv, Mv, E,
+                                                     sPeq, c_next);
                     }
                 }
-                has = false;
             }
         }
     }
@@ -402,31 +303,26 @@ __global__ void __launch_bounds__(128) band_group_kernel(BandArgs a) {
 
 using BandLauncher = void (*)(const BandArgs &, int, cudaStream_t);
 
-template <int WB, int B>
-void launch_band(const BandArgs &a, int grid, cudaStream_t st) {
-    band_kernel<WB, B><<<grid, 128, 0, st>>>(a);
-}
-
 template <int G, int WPL, int B>
-void launch_band_group(const BandArgs &a, int grid, cudaStream_t st) {
-    band_group_kernel<G, WPL, B><<<grid, 128, 0, st>>>(a);
+void launch_band_pipe(const BandArgs &a, int grid, cudaStream_t st) {
+    band_pipe_kernel<G, WPL, B><<<grid, kBandThreads, 0, st>>>(a);
 }
 
-#define BAND_TABLE(B)                                                                                        \
-    {launch_band<2, B>, launch_band<3, B>, launch_band<4, B>, launch_band<5, B>, launch_band<6, B>,          \
-     launch_band<8, B>, launch_band<10, B>, launch_band_group<4, 4, B>, launch_band_group<8, 3, B>,           \
-     launch_band_group<8, 4, B>, launch_band_group<8, 5, B>, launch_band_group<8, 6, B>,                      \
-     launch_band_group<16, 4, B>, launch_band_group<16, 5, B>, launch_band_group<16, 6, B>,                  \
-     launch_band_group<16, 8, B>, launch_band_group<32, 5, B>, launch_band_group<32, 6, B>}
-#define BAND_FNS(B)                                                                                          \
-    {(const void *)band_kernel<2, B>, (const void *)band_kernel<3, B>, (const void *)band_kernel<4, B>,      \
-     (const void *)band_kernel<5, B>, (const void *)band_kernel<6, B>, (const void *)band_kernel<8, B>,      \
-     (const void *)band_kernel<10, B>, (const void *)band_group_kernel<4, 4, B>,                             \
-     (const void *)band_group_kernel<8, 3, B>, (const void *)band_group_kernel<8, 4, B>,                     \
-     (const void *)band_group_kernel<8, 5, B>, (const void *)band_group_kernel<8, 6, B>,                     \
-     (const void *)band_group_kernel<16, 4, B>, (const void *)band_group_kernel<16, 5, B>,                   \
-     (const void *)band_group_kernel<16, 6, B>, (const void *)band_group_kernel<16, 8, B>,                   \
-     (const void *)band_group_kernel<32, 5, B>, (const void *)band_group_kernel<32, 6, B>}
+#define BAND_TABLE(B) \
+    {launch_band_pipe<2, 2, B>, launch_band_pipe<2, 3, B>, launch_band_pipe<2, 4, B>, launch_band_pipe<2, 6, B>, launch_band_pipe<2, 8, B>,            \
+         launch_band_pipe<4, 3, B>, launch_band_pipe<4, 4, B>, launch_band_pipe<4, 5, B>, launch_band_pipe<4, 6, B>, launch_band_pipe<4, 8, B>,        \
+         launch_band_pipe<8, 4, B>, launch_band_pipe<8, 5, B>, launch_band_pipe<8, 6, B>, launch_band_pipe<8, 7, B>, launch_band_pipe<8, 8, B>,        \
+         launch_band_pipe<16, 4, B>, launch_band_pipe<16, 5, B>, launch_band_pipe<16, 6, B>, launch_band_pipe<16, 7, B>, launch_band_pipe<16, 8, B>,   \
+         launch_band_pipe<32, 4, B>, launch_band_pipe<32, 5, B>, launch_band_pipe<32, 6, B>, launch_band_pipe<32, 8, B>}
+#define BAND_FNS(B) \
+    {(const void *)band_pipe_kernel<2, 2, B>, (const void *)band_pipe_kernel<2, 3, B>, (const void *)band_pipe_kernel<2, 4, B>,          \
+         (const void *)band_pipe_kernel<2, 6, B>, (const void *)band_pipe_kernel<2, 8, B>, (const void *)band_pipe_kernel<4, 3, B>,      \
+         (const void *)band_pipe_kernel<4, 4, B>, (const void *)band_pipe_kernel<4, 5, B>, (const void *)band_pipe_kernel<4, 6, B>,      \
+         (const void *)band_pipe_kernel<4, 8, B>, (const void *)band_pipe_kernel<8, 4, B>, (const void *)band_pipe_kernel<8, 5, B>,      \
+         (const void *)band_pipe_kernel<8, 6, B>, (const void *)band_pipe_kernel<8, 7, B>, (const void *)band_pipe_kernel<8, 8, B>,      \
+         (const void *)band_pipe_kernel<16, 4, B>, (const void *)band_pipe_kernel<16, 5, B>, (const void *)band_pipe_kernel<16, 6, B>,   \
+         (const void *)band_pipe_kernel<16, 7, B>, (const void *)band_pipe_kernel<16, 8, B>, (const void *)band_pipe_kernel<32, 4, B>,   \
+         (const void *)band_pipe_kernel<32, 5, B>, (const void *)band_pipe_kernel<32, 6, B>, (const void *)band_pipe_kernel<32, 8, B>}
 static const BandLauncher kBandDna[kBandBuckets] = BAND_TABLE(2);
 static const BandLauncher kBandProt[kBandBuckets] = BAND_TABLE(5);
 static const void *kBandFnDna[kBandBuckets] = BAND_FNS(2);
@@ -473,23 +369,15 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
         }
         const int lx = (int)(offs[x + 1] - offs[x]), ly = (int)(offs[y + 1] - offs[y]);
         const int m = max(lx, ly), dl = abs(lx - ly);
-        const int W = max(1, (m + 31) / 32);
-        const int k = max(k_cur[p], dl);
+        const int k = min(max(k_cur[p], dl), m);
         int b = -1;
-        if (k < m) {
+        if (ly > 0 && lx > 0) {
             for (int c = 0; c < nb; ++c)
-                if (kBandCap[c] >= W || kBandKW[c] >= k) {
+                if ((kBandG[c] - 1) * 32 * kBandWPL[c] >= k) {
                     b = c;
                     break;
                 }
-            if (b >= 0 && kBandCap[b] < W && (float)kBandCap[b] > kBandMaxShare * (float)W) b = -1;
-        } else {
-            // the band is the whole matrix: a window as tall as the column is a plain DP
-            for (int c = 0; c < nb; ++c)
-                if (kBandCap[c] >= W) {
-                    b = c;
-                    break;
-                }
+            if (b >= 0 && (float)(k + 32 * kBandWPL[b]) > kBandMaxShare * (float)m) b = -1;
         }
         if (PASS == 0) {
             if (b < 0)
@@ -559,28 +447,25 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_banded_batch setup");
     const void *const *fns = s->alphabet == MSA_DNA ? kBandFnDna : kBandFnProt;
     const BandLauncher *launch = s->alphabet == MSA_DNA ? kBandDna : kBandProt;
-    const int nb = band_buckets(s->alphabet);
-    {
-        static const int wb[7] = {2, 3, 4, 5, 6, 8, 10};
-        for (int b = 0; b < kBandBuckets; ++b) {
-            const int expect = b < 7 ? 32 * (wb[b] - 2) - 1 : 32 * (kBandCapHost[b] - 1) - 1;
-            if (kBandKWHost[b] != expect || (b < 7 && kBandCapHost[b] != wb[b]))
-                return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table inconsistent at %d", b);
-        }
+    const int nb = kBandBuckets;
+    for (int b = 1; b < nb; ++b) {
+        const int c0 = (kBandGHost[b - 1] - 1) * 32 * kBandWPLHost[b - 1];
+        const int c1 = (kBandGHost[b] - 1) * 32 * kBandWPLHost[b];
+        if (c1 <= c0) return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table not increasing at %d", b);
     }
     static int occ[2][kBandBuckets] = {};
     for (int b = 0; b < nb; ++b)
         if (occ[s->alphabet][b] == 0) {
             int o = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[b], 128, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[b], kBandThreads, 0);
             if (e != cudaSuccess) return cuda_check(ctx, e, "band occupancy");
             occ[s->alphabet][b] = std::max(o, 1);
         }
-    // windows taller than any sequence of this set are never needed beyond the first that holds it
-    const int Wmax = std::max(1, (s->max_len + 31) / 32);
+    // buckets beyond the first that holds a band as wide as the longest
+    // sequence of this set are never used
     int last = nb - 1;
     for (int b = 0; b < nb; ++b)
-        if (kBandCapHost[b] >= Wmax) {
+        if ((kBandGHost[b] - 1) * 32 * kBandWPLHost[b] >= s->max_len) {
             last = b;
             break;
         }
@@ -604,7 +489,7 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
                                                             nb, ctx->dev_err);
         ctx->launches += 2;
         BandArgs a{s->planes, s->codes, s->offs, pairs, blist, boff, bcount, bcounter, k_cur, d_out, k_used_out,
-                   nxt, nxt_count, 0, 1u, 2u};
+                   nxt, nxt_count, 0};
         {
             ProfScope prof(ctx, st);
             e = run_concurrent(ctx, st, last + 1, [&](int b, cudaStream_t s2) {
