@@ -328,30 +328,31 @@ static const BandLauncher kBandProt[kBandBuckets] = BAND_TABLE(5);
 static const void *kBandFnDna[kBandBuckets] = BAND_FNS(2);
 static const void *kBandFnProt[kBandBuckets] = BAND_FNS(5);
 
-// Sorts the pending pairs of one round into window buckets (pass 0 counts,
-// pass 1 writes); pairs whose band needs more than the largest window go to
-// the exact full-DP list.  Round 0 reads all pairs (cur == nullptr) and
-// checks every index.
+// Pairs of a bucket are ordered longest first (by half-octave classes of
+// the column count), so that the long pairs start early and the short ones
+// fill the end of the persistent launch.
+constexpr int kLenClasses = 64;
+// per round: bcount, boff, bcounter [buckets]; ccount, coff, cfill [buckets x classes]
+constexpr int kBandMeta = 3 * kBandBuckets + 3 * kBandBuckets * kLenClasses;
+__device__ __forceinline__ int band_len_class(int n) {
+    if (n <= 1) return kLenClasses - 1;
+    const int lg = 31 - __clz(n);
+    return kLenClasses - 1 - min(kLenClasses - 1, 2 * lg + ((n >> (lg - 1)) & 1));
+}
+
+// Sorts the pending pairs of one round into band buckets (pass 0 counts,
+// pass 1 writes); pairs whose band is too wide for a bucket go to the exact
+// full-DP list.  Round 0 reads all pairs (cur == nullptr) and checks every
+// index.
 template <int PASS>
 __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restrict__ pairs, int64_t P,
                                                         const int32_t *__restrict__ cur, const int32_t *cur_count,
                                                         const int64_t *__restrict__ offs, int32_t n, int64_t total,
                                                         int32_t *__restrict__ k_cur, int32_t *__restrict__ bcount,
-                                                        int32_t *__restrict__ bfill, int32_t *__restrict__ boff,
-                                                        int32_t *__restrict__ blist, int32_t *__restrict__ full_list,
-                                                        int32_t *full_count, int32_t nb, int32_t *err) {
-    __shared__ int32_t sboff[kBandBuckets];
-    if (PASS == 1) {
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int b = 0; b < nb; ++b) {
-                sboff[b] = run;
-                run += bcount[b];
-            }
-        }
-        __syncthreads();
-        if (blockIdx.x == 0 && threadIdx.x < nb) boff[threadIdx.x] = sboff[threadIdx.x];
-    }
+                                                        int32_t *__restrict__ ccount, int32_t *__restrict__ cfill,
+                                                        const int32_t *__restrict__ coff, int32_t *__restrict__ blist,
+                                                        int32_t *__restrict__ full_list, int32_t *full_count, int32_t nb,
+                                                        int32_t *err) {
     const int64_t N = cur ? (int64_t)*cur_count : P;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int p = cur ? cur[i] : (int)i;
@@ -379,13 +380,30 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
                 }
             if (b >= 0 && (float)(k + 32 * kBandWPL[b]) > kBandMaxShare * (float)m) b = -1;
         }
+        if (b < 0) {
+            if (PASS == 0) full_list[atomicAdd(full_count, 1)] = p;
+            continue;
+        }
+        const int slot = b * kLenClasses + band_len_class(min(lx, ly));
         if (PASS == 0) {
-            if (b < 0)
-                full_list[atomicAdd(full_count, 1)] = p;
-            else
-                atomicAdd(bcount + b, 1);
-        } else if (b >= 0) {
-            blist[sboff[b] + atomicAdd(bfill + b, 1)] = p;
+            atomicAdd(bcount + b, 1);
+            atomicAdd(ccount + slot, 1);
+        } else {
+            blist[coff[slot] + atomicAdd(cfill + slot, 1)] = p;
+        }
+    }
+}
+
+// Offsets of the buckets and of their length classes in the pair list.
+__global__ void band_scan_kernel(const int32_t *__restrict__ ccount, int32_t *__restrict__ coff,
+                                 int32_t *__restrict__ boff, int32_t nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int b = 0; b < nb; ++b) {
+        boff[b] = run;
+        for (int c = 0; c < kLenClasses; ++c) {
+            coff[b * kLenClasses + c] = run;
+            run += ccount[b * kLenClasses + c];
         }
     }
 }
@@ -416,7 +434,7 @@ extern "C" {
 
 int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs) {
     auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
-    return r(4 * P) * 6 + r(4 * 4 * kBandBuckets) + r(16) + lev_workspace(P, n_seqs);
+    return r(4 * P) * 6 + r(4 * kBandMeta) + r(16) + lev_workspace(P, n_seqs);
 }
 
 msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
@@ -431,7 +449,7 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     int32_t *list_a = ar.take<int32_t>(P);
     int32_t *list_b = ar.take<int32_t>(P);
     int32_t *blist = ar.take<int32_t>(P);
-    int32_t *meta = ar.take<int32_t>(4 * kBandBuckets);     // bcount, bfill, boff, bcounter
+    int32_t *meta = ar.take<int32_t>(kBandMeta);
     int32_t *counts = ar.take<int32_t>(4);                  // count_a, count_b, full (round 0), full (later)
     // the full-DP fallback list reuses list storage: pairs that reach it are
     // never pending again, so it gets its own array
@@ -440,8 +458,9 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     if (!full_list2 || ar.cap - ar.used < lev_workspace(P, s->n_seqs))
         return set_error(ctx, MSA_ENOMEM, "msa_lev_banded_batch: needs %lld workspace bytes, context has %lld",
                          (long long)msa_lev_banded_workspace_bytes(P, s->n_seqs), (long long)ctx->ws_bytes);
-    int32_t *bcount = meta, *bfill = meta + kBandBuckets, *boff = meta + 2 * kBandBuckets,
-            *bcounter = meta + 3 * kBandBuckets;
+    int32_t *bcount = meta, *boff = meta + kBandBuckets, *bcounter = meta + 2 * kBandBuckets;
+    int32_t *ccount = meta + 3 * kBandBuckets, *coff = ccount + kBandBuckets * kLenClasses,
+            *cfill = coff + kBandBuckets * kLenClasses;
     cudaError_t e = cudaMemcpyAsync(k_cur, k0, P * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 4 * sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_banded_batch setup");
@@ -474,7 +493,7 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     for (int r = 0; r < kBandRounds; ++r) {
         int32_t *nxt = (r & 1) ? list_b : list_a;
         int32_t *nxt_count = counts + (r & 1);
-        if ((e = cudaMemsetAsync(meta, 0, 4 * kBandBuckets * sizeof(int32_t), st)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(meta, 0, kBandMeta * sizeof(int32_t), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(nxt_count, 0, sizeof(int32_t), st)) != cudaSuccess)
             return cuda_check(ctx, e, "band round memset");
         // round 0 sends wide bands straight to the full DP, which then runs
@@ -482,12 +501,13 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
         int32_t *flist = r == 0 ? full_list : full_list2;
         int32_t *fcount = counts + (r == 0 ? 2 : 3);
         band_plan_kernel<0><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
-                                                            k_cur, bcount, bfill, boff, blist, flist, fcount,
+                                                            k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
                                                             nb, ctx->dev_err);
+        band_scan_kernel<<<1, 32, 0, st>>>(ccount, coff, boff, nb);
         band_plan_kernel<1><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
-                                                            k_cur, bcount, bfill, boff, blist, flist, fcount,
+                                                            k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
                                                             nb, ctx->dev_err);
-        ctx->launches += 2;
+        ctx->launches += 3;
         BandArgs a{s->planes, s->codes, s->offs, pairs, blist, boff, bcount, bcounter, k_cur, d_out, k_used_out,
                    nxt, nxt_count, 0};
         {
