@@ -201,11 +201,11 @@ def band_bench(ctx, args, stream):
     yhat, k = model.predict_band(es, prof, pairs, gamma=gamma, margin=8)
     d_band, k_used = api.lev_banded_batch(ctx, es, pairs, k)
     # non-learned start: the 4-mer L1 lower bound, ceil(L1 / 8) <= f
-    Xe = api.pair_features(ctx, es, prof, pairs)
-    meanlen = torch.from_numpy(((lens[0::2] + lens[1::2]) / 2).astype(np.float32)).cuda()
-    l1 = (Xe.float() * meanlen[:, None]).sum(1)
+    cnt = prof.int() & 0xFFFF
+    l1 = (cnt[pairs[:, 0].long()] - cnt[pairs[:, 1].long()]).abs().sum(1)
+    del cnt
     dl = torch.from_numpy(np.abs(lens[0::2] - lens[1::2]).astype(np.int32)).cuda()
-    k_l1 = torch.maximum(dl, torch.ceil(l1 / 8).int())
+    k_l1 = torch.maximum(dl, ((l1 + 7) // 8).int())
     d_l1, _ = api.lev_banded_batch(ctx, es, pairs, k_l1)
     ctx.check()
     mism = int((d_band != d_full).sum().item()) + int((d_l1 != d_full).sum().item())

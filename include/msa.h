@@ -179,7 +179,8 @@ int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs);
  * distance exact.  Features: 4-mer count profiles of DNA (256 bins, k-mer
  * s0 s1 s2 s3 of codes A=0 C=1 G=2 T=3 in bin 64 s0 + 16 s1 + 4 s2 + s3,
  * counted over the len - 3 windows), and for a pair (a, b) the 256 values
- * |c_a - c_b| / ((len_a + len_b) / 2), divided in fp32 and rounded to bf16.
+ * (c_a - c_b)^2 / ((len_a + len_b) / 2), squared and divided in fp32 and
+ * rounded to bf16.
  * Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with W1 128x256,
  * W2 64x128, W3 1x64; bf16 weights and activations, fp32 accumulation on the
  * tensor cores; target y = f(a, b) / max(m, n).

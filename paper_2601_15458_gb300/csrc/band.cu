@@ -1,8 +1,13 @@
 // Learned band proposer: 4-mer count profiles (A8), the MLP 256->128->64->1
 // forward (A9) and its training step (A10), and msa_band_predict.
 //
-// The network maps the pair feature x = |c_a - c_b| / ((len_a + len_b) / 2)
-// over the 256 DNA 4-mer counts to y ~ f(a, b) / max(m, n).  Weights and
+// The network maps the pair feature x = (c_a - c_b)^2 / ((len_a + len_b) / 2)
+// over the 256 DNA 4-mer counts to y ~ f(a, b) / max(m, n).  Squared
+// differences: if the k-mers that edits remove and add fall into the bins
+// like independent Poisson draws, E (c_a - c_b)_i^2 is the number of changed
+// windows in bin i, so the feature sum estimates the changed windows per
+// residue whatever the length, where absolute differences cancel more in
+// longer sequences (more changes share a bin).  Weights and
 // activations are bf16, products accumulate in fp32 on the tensor cores
 // (mma.sync m16n8k16 bf16); biases and the last layer are fp32.  The
 // proposer only picks the starting band of msa_lev_banded_batch, whose
@@ -120,7 +125,7 @@ __device__ __forceinline__ void features_tile(__nv_bfloat16 *X, const uint16_t *
 #pragma unroll
             for (int k = lane * 8; k < lane * 8 + 8; ++k) {
                 const float d = fabsf((float)ca[k] - (float)cb[k]);
-                X[r * kS1 + k] = __float2bfloat16_rn(d / den);
+                X[r * kS1 + k] = __float2bfloat16_rn(d * d / den);
             }
         } else {
 #pragma unroll
@@ -144,8 +149,10 @@ __global__ void __launch_bounds__(256) features_kernel(const uint16_t *__restric
         const float den = den0 > 0.f ? den0 : 1.f;
         const uint16_t *ca = prof + (int64_t)a * 256, *cb = prof + (int64_t)b * 256;
 #pragma unroll
-        for (int k = lane * 8; k < lane * 8 + 8; ++k)
-            X[p * 256 + k] = __float2bfloat16_rn(fabsf((float)ca[k] - (float)cb[k]) / den);
+        for (int k = lane * 8; k < lane * 8 + 8; ++k) {
+            const float d = fabsf((float)ca[k] - (float)cb[k]);
+            X[p * 256 + k] = __float2bfloat16_rn(d * d / den);
+        }
     }
 }
 

@@ -84,18 +84,42 @@ struct BandEq {
     uint32_t pl[kShared ? 1 : WPL][kShared ? 1 : B];
 };
 
-// Takes block bk of the current pair: its live columns, the last column of
-// the block above (0 for the top block), fresh +1 vertical deltas, the
-// query's match masks of its rows and the symbol of its first column.
+#ifndef MSA_BAND_CPS
+#define MSA_BAND_CPS 4
+#endif
+// Columns per pipeline step: each step a block computes a chunk of CPS
+// consecutive columns, so the per-step bookkeeping (the shuffle, the live
+// tests, the vote) is paid once per chunk.  A block's live columns are
+// widened to whole chunks (a superset of the band, so still exact), and the
+// lane above sends the Ph/Mh bits of all CPS columns in one word.
+constexpr int kBandCps = MSA_BAND_CPS;
+static_assert(kBandCps >= 1 && 2 * kBandCps <= 8, "columns per step");
+// capacity of a (G, WPL) group at CPS columns per step: the lane that holds
+// block b must have finished it before block b + G needs it
+__host__ __device__ constexpr int band_capacity(int G, int WPL) { return (G - 1) * 32 * WPL - 2 * kBandCps; }
+
+// Takes block bk of the current pair: its live chunks [qs, qe] (columns
+// widened to whole chunks), the last live column of the block above (0 for
+// the top block) and its chunk, fresh +1 vertical deltas, the query's match
+// masks of its rows and the symbols of its first chunk.
 template <int WPL, int B>
 __device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m, int n, const uint32_t *planes,
-                                                 int64_t qa, const uint8_t *tc, int &js, int &je, int &jep,
+                                                 int64_t qa, const uint8_t *tc, int &qs, int &qe, int &jep, int &qep,
                                                  uint32_t (&Pv)[WPL], uint32_t (&Mv)[WPL], BandEq<WPL, B> &E,
-                                                 uint32_t *sPeq, int &c_next) {
+                                                 uint32_t *sPeq, int (&c_next)[kBandCps]) {
     constexpr int H = 32 * WPL;
-    js = max(1, bk * H + 1 + dlo);
-    je = min(n, bk * H + H + dhi);
-    jep = bk == 0 ? 0 : min(n, bk * H + dhi);
+    const int js = max(1, bk * H + 1 + dlo);
+    const int je = min(n, bk * H + H + dhi);
+    qs = (js - 1) / kBandCps + 1;
+    qe = (je - 1) / kBandCps + 1;
+    if (bk == 0) {
+        jep = 0;
+        qep = 0;
+    } else {
+        const int jp = min(n, (bk - 1) * H + H + dhi);      // last live column of the block above, widened
+        qep = (jp - 1) / kBandCps + 1;
+        jep = min(n, qep * kBandCps);
+    }
 #pragma unroll
     for (int w = 0; w < WPL; ++w) {
         Pv[w] = kFull;
@@ -110,13 +134,16 @@ __device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m
             for (int q = 0; q < B; ++q) E.pl[w][q] = pl[q];
         }
     }
-    c_next = __ldg(tc + js - 1);
+    const int j0 = (qs - 1) * kBandCps;
+#pragma unroll
+    for (int c = 0; c < kBandCps; ++c) c_next[c] = j0 + c < n ? __ldg(tc + j0 + c) : 0;
 }
 
 template <int G, int WPL, int B>
 __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "group size");
     constexpr int H = 32 * WPL;
+    constexpr int CPS = kBandCps;
     constexpr bool kShared = BandEq<WPL, B>::kShared;
     __shared__ uint32_t sPeqAll[kShared ? 4 * WPL * kBandThreads : 1];
     uint32_t *sPeq = sPeqAll + threadIdx.x;
@@ -145,9 +172,13 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
     bool has = false, more = true;
     int64_t qa = 0;
     const uint8_t *tc = nullptr;
-    // per lane: its block, that block's live columns, the last column of the
-    // block above, T, the lane's share of D[m][n] and the word sent down
-    int bk = 0, js = 1, je = 0, jep = 0, Tb = 0, acc = 0, c_next = 0;
+    // per lane: its block, that block's live chunks, the last live column of
+    // the block above and its chunk, T, the lane's share of D[m][n] and the
+    // word sent down
+    int bk = 0, qs = 1, qe = 0, jep = 0, qep = 0, Tb = 0, acc = 0;
+    int c_next[CPS];
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) c_next[c] = 0;
     uint32_t out = 0u;
     bool fin = false;
     while (true) {
@@ -209,11 +240,11 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                             }
                         } else {
                             bm = (m - 1) / H;
-                            tend = n + bm;
+                            tend = (n - 1) / CPS + 1 + bm;
                             bk = gl;
                             if (bk <= bm)
-                                band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, js, je, jep, Pv, Mv,
-                                                         E, sPeq, c_next);
+                                band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv,
+                                                         Mv, E, sPeq, c_next);
                             has = true;
                         }
                     }
@@ -221,79 +252,79 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
             }
             if (!__any_sync(kFull, has)) break;
         }
-        // 2. one pipeline step: block bk computes column t - bk
+        // 2. one pipeline step: block bk computes chunk t - bk
         const uint32_t in = __shfl_sync(kFull, out, src);
         if (has) {
             ++t;
             fin = t == tend;
-            const int j = t - bk;
+            const int q = t - bk;
             if (bk <= bm) {
-                if (j == jep) Tb = (int)(in >> 2);          // the block above leaves after this column
-                if (j >= js && j <= je) {
-                    const bool top = j > jep;
-                    uint32_t ph_in = in & 1u, mh_in = (in >> 1) & 1u;
-                    if (top) {
-                        ++Tb;
-                        ph_in = 1u;
-                        mh_in = 0u;
+                if (q == qep) Tb = (int)(in >> (2 * CPS));    // the block above leaves after this chunk
+                if (q >= qs && q <= qe) {
+                    int cc[CPS];
+#pragma unroll
+                    for (int c = 0; c < CPS; ++c) cc[c] = c_next[c];
+                    const int j0 = (q - 1) * CPS;              // columns j0 + 1 .. j0 + CPS
+                    if (q < qe) {
+#pragma unroll
+                        for (int c = 0; c < CPS; ++c) c_next[c] = j0 + CPS + c < n ? __ldg(tc + j0 + CPS + c) : 0;
                     }
-                    const int c = c_next;
-                    if (j < je) c_next = __ldg(tc + j);
-                    uint32_t eq[WPL], u[WPL], sum[WPL], pv[WPL];
-                    if constexpr (kShared) {
-                        const uint32_t *row = sPeq + (c & 3) * WPL * kBandThreads;
+                    uint32_t o = 0u;
 #pragma unroll
-                        for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
-                    } else {
-                        uint32_t x[B];
+                    for (int c = 0; c < CPS; ++c) {
+                        const int j = j0 + 1 + c;
+                        if (CPS > 1 && j > n) break;
+                        const bool top = j > jep;
+                        uint32_t ph_in = (in >> (2 * c)) & 1u, mh_in = (in >> (2 * c + 1)) & 1u;
+                        if (top) {
+                            ++Tb;
+                            ph_in = 1u;
+                            mh_in = 0u;
+                        }
+                        uint32_t eq[WPL];
+                        if constexpr (kShared) {
+                            const uint32_t *row = sPeq + (cc[c] & 3) * WPL * kBandThreads;
 #pragma unroll
-                        for (int q = 0; q < B; ++q) x[q] = ((c >> q) & 1) ? 0u : kFull;
+                            for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
+                        } else {
+                            uint32_t x[B];
 #pragma unroll
-                        for (int w = 0; w < WPL; ++w) {
-                            uint32_t e = E.pl[w][0] ^ x[0];
+                            for (int b = 0; b < B; ++b) x[b] = ((cc[c] >> b) & 1) ? 0u : kFull;
 #pragma unroll
-                            for (int q = 1; q < B; ++q) e &= E.pl[w][q] ^ x[q];
-                            eq[w] = e;
+                            for (int w = 0; w < WPL; ++w) {
+                                uint32_t e = E.pl[w][0] ^ x[0];
+#pragma unroll
+                                for (int b = 1; b < B; ++b) e &= E.pl[w][b] ^ x[b];
+                                eq[w] = e;
+                            }
+                        }
+                        uint32_t ph_out, mh_out;
+                        bv_column<WPL>(eq, Pv, Mv, ph_in, mh_in, ph_out, mh_out);
+                        o |= (ph_out | (mh_out << 1)) << (2 * c);
+                        if (j == n) {
+                            // this block's share of D[m][n]: its rows <= m (and T if on top)
+                            int part = top ? Tb : 0;
+#pragma unroll
+                            for (int w = 0; w < WPL; ++w) {
+                                const int rem = m - 32 * (bk * WPL + w);
+                                const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                                part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
+                            }
+                            acc += part;
                         }
                     }
+                    out = o;
+                    if (q == qe) {
+                        // the block's last chunk: hand D on its bottom row to
+                        // the block below and move on to the next block
+                        int delta = 0;
 #pragma unroll
-                    for (int w = 0; w < WPL; ++w) {
-                        pv[w] = Pv[w];
-                        u[w] = eq[w] & pv[w];
-                    }
-                    CarryChainIn<WPL>::add(sum, u, pv, mh_in);
-                    uint32_t php = ph_in << 31, mhp = mh_in << 31;
-#pragma unroll
-                    for (int w = 0; w < WPL; ++w) {
-                        const uint32_t xh = (sum[w] ^ pv[w]) | eq[w];
-                        const uint32_t ph = Mv[w] | ~(xh | pv[w]);
-                        const uint32_t mh = pv[w] & xh;
-                        const uint32_t phs = __funnelshift_l(php, ph, 1);
-                        const uint32_t mhs = __funnelshift_l(mhp, mh, 1);
-                        php = ph;
-                        mhp = mh;
-                        const uint32_t xv = eq[w] | Mv[w];
-                        Pv[w] = mhs | ~(xv | phs);
-                        Mv[w] = phs & xv;
-                    }
-                    out = (php >> 31) | ((mhp >> 31) << 1);
-                    if (j == je) {
-                        // the block's last column: hand D on its bottom row to
-                        // the block below, add its share at column n, move on
-                        int delta = 0, part = 0;
-#pragma unroll
-                        for (int w = 0; w < WPL; ++w) {
-                            const int rem = m - 32 * (bk * WPL + w);
-                            const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-                            delta += __popc(Pv[w]) - __popc(Mv[w]);
-                            part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
-                        }
-                        out |= (uint32_t)(Tb + delta) << 2;
-                        if (j == n) acc += (top ? Tb : 0) + part;
+                        for (int w = 0; w < WPL; ++w) delta += __popc(Pv[w]) - __popc(Mv[w]);
+                        out |= (uint32_t)(Tb + delta) << (2 * CPS);
                         bk += G;
                         if (bk <= bm)
-                            band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, js, je, jep, Pv, Mv, E,
-                                                     sPeq, c_next);
+                            band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv, Mv,
+                                                     E, sPeq, c_next);
                     }
                 }
             }
@@ -374,7 +405,7 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
         int b = -1;
         if (ly > 0 && lx > 0) {
             for (int c = 0; c < nb; ++c)
-                if ((kBandG[c] - 1) * 32 * kBandWPL[c] >= k) {
+                if (band_capacity(kBandG[c], kBandWPL[c]) >= k) {
                     b = c;
                     break;
                 }
@@ -468,8 +499,8 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     const BandLauncher *launch = s->alphabet == MSA_DNA ? kBandDna : kBandProt;
     const int nb = kBandBuckets;
     for (int b = 1; b < nb; ++b) {
-        const int c0 = (kBandGHost[b - 1] - 1) * 32 * kBandWPLHost[b - 1];
-        const int c1 = (kBandGHost[b] - 1) * 32 * kBandWPLHost[b];
+        const int c0 = band_capacity(kBandGHost[b - 1], kBandWPLHost[b - 1]);
+        const int c1 = band_capacity(kBandGHost[b], kBandWPLHost[b]);
         if (c1 <= c0) return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table not increasing at %d", b);
     }
     static int occ[2][kBandBuckets] = {};
@@ -484,7 +515,7 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     // sequence of this set are never used
     int last = nb - 1;
     for (int b = 0; b < nb; ++b)
-        if ((kBandGHost[b] - 1) * 32 * kBandWPLHost[b] >= s->max_len) {
+        if (band_capacity(kBandGHost[b], kBandWPLHost[b]) >= s->max_len) {
             last = b;
             break;
         }

@@ -150,17 +150,25 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
 }
 
 #ifndef MSA_LANE_CHAIN
-#define MSA_LANE_CHAIN 1
+#define MSA_LANE_CHAIN 3
 #endif
 
 // One column over WC words, in chunks of up to 8 words: the chunk's
 // (Eq & Pv) + Pv additions run on the hardware carry chain (add.cc/addc), and
 // the shifts by one take the lower word's top bit by funnel shift, so no
 // carry or top bit is extracted by separate instructions.
+//
+// Variants 3 and 4 use that the carry into row i of the addition is Mh of
+// row i - 1 (and the word's carry-in for its first row): the shifted Mh
+// vector is the carry-in vector sum ^ u ^ Pv, one logic op, and with it
+// neither Mh nor Xh is formed (Ph = Mv | ~(Xh | Pv) = Mv | ~(sum | Pv | Eq)),
+// 9 ops per word instead of 10.  Variants 2 and 4 issue the addition as a
+// multiply-add by a runtime one (madc), on the FMA pipe.
 template <int WC, int SIGMA>
 __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t (&Pv)[WC], uint32_t (&Mv)[WC],
                                                   uint32_t one) {
     uint32_t cy = 0u, ph_prev = 0u, mh_prev = 0u;
+    (void)mh_prev;
 #pragma unroll
     for (int k0 = 0; k0 < WC; k0 += 8) {
         constexpr int kMax = 8;
@@ -173,7 +181,7 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 pv[w] = Pv[k0 + w];
                 u[w] = eq[w] & pv[w];
             }
-#if MSA_LANE_CHAIN == 2
+#if MSA_LANE_CHAIN == 2 || MSA_LANE_CHAIN == 4
             cy = CarryChainMadIn<8>::add(s, u, pv, cy, one);
 #else
             cy = CarryChainIn<8>::add(s, u, pv, cy);
@@ -182,6 +190,12 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
                 const int k = k0 + w;
+#if MSA_LANE_CHAIN >= 3
+                const uint32_t mhs = s[w] ^ u[w] ^ pv[w];
+                const uint32_t ph = Mv[k] | ~(s[w] | pv[w] | eq[w]);
+                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
+                ph_prev = ph;
+#else
                 const uint32_t xh = (s[w] ^ pv[w]) | eq[w];
                 const uint32_t ph = Mv[k] | ~(xh | pv[w]);
                 const uint32_t mh = pv[w] & xh;
@@ -189,6 +203,7 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
                 ph_prev = ph;
                 mh_prev = mh;
+#endif
                 const uint32_t xv = eq[w] | Mv[k];
                 Pv[k] = mhs | ~(xv | phs);
                 Mv[k] = phs & xv;
@@ -205,6 +220,12 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 const uint64_t t = (uint64_t)u + pv + cy;
                 const uint32_t sum = (uint32_t)t;
                 cy = (uint32_t)(t >> 32);
+#if MSA_LANE_CHAIN >= 3
+                const uint32_t mhs = sum ^ u ^ pv;
+                const uint32_t ph = Mv[k] | ~(sum | pv | eq);
+                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
+                ph_prev = ph;
+#else
                 const uint32_t xh = (sum ^ pv) | eq;
                 const uint32_t ph = Mv[k] | ~(xh | pv);
                 const uint32_t mh = pv & xh;
@@ -212,12 +233,63 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
                 ph_prev = ph;
                 mh_prev = mh;
+#endif
                 const uint32_t xv = eq | Mv[k];
                 Pv[k] = mhs | ~(xv | phs);
                 Mv[k] = phs & xv;
             }
         }
     }
+}
+
+// (Eq & Pv) + Pv + cin over N words on the carry chain, in chunks of at
+// most 8 words; returns the carry out of the last word.
+template <int N, int K0 = 0>
+__device__ __forceinline__ uint32_t chain_add_all(uint32_t (&s)[N], const uint32_t (&u)[N], const uint32_t (&pv)[N],
+                                                  uint32_t cy) {
+    if constexpr (K0 >= N) {
+        return cy;
+    } else {
+        constexpr int L = N - K0 < 8 ? N - K0 : 8;
+        uint32_t ss[L], uu[L], pp[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            uu[i] = u[K0 + i];
+            pp[i] = pv[K0 + i];
+        }
+        cy = CarryChainIn<L>::add(ss, uu, pp, cy);
+#pragma unroll
+        for (int i = 0; i < L; ++i) s[K0 + i] = ss[i];
+        return chain_add_all<N, K0 + L>(s, u, pv, cy);
+    }
+}
+
+// One column over N consecutive words, 9 ops a word (the carry-in vector
+// sum ^ u ^ Pv is Mh shifted down a row, see lane_column_chain).  ph_in and
+// cin are the Ph bit and the addition carry (= Mh bit) of the row above the
+// first word; ph_out and cout those of the last word's top row.
+template <int N>
+__device__ __forceinline__ void bv_column(const uint32_t (&eq)[N], uint32_t (&Pv)[N], uint32_t (&Mv)[N],
+                                          uint32_t ph_in, uint32_t cin, uint32_t &ph_out, uint32_t &cout) {
+    uint32_t u[N], sum[N], pv[N];
+#pragma unroll
+    for (int w = 0; w < N; ++w) {
+        pv[w] = Pv[w];
+        u[w] = eq[w] & pv[w];
+    }
+    cout = chain_add_all<N>(sum, u, pv, cin);
+    uint32_t php = ph_in << 31;
+#pragma unroll
+    for (int w = 0; w < N; ++w) {
+        const uint32_t mhs = sum[w] ^ u[w] ^ pv[w];
+        const uint32_t ph = Mv[w] | ~(sum[w] | pv[w] | eq[w]);
+        const uint32_t phs = __funnelshift_l(php, ph, 1);
+        php = ph;
+        const uint32_t xv = eq[w] | Mv[w];
+        Pv[w] = mhs | ~(xv | phs);
+        Mv[w] = phs & xv;
+    }
+    ph_out = php >> 31;
 }
 
 __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
@@ -330,6 +402,9 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
 // Match masks: layout [w][c][lane], conflict-free for any mix of symbols.
 // ---------------------------------------------------------------------------
 constexpr int kRing = 32;
+#ifndef MSA_WARP_CHAIN
+#define MSA_WARP_CHAIN 1
+#endif
 
 template <int WPL, int B, int SIGMA>
 __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
@@ -420,10 +495,18 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
                     uint32_t ph_in = lane == 0 ? 1u : (uint32_t)(msg_in & 1);
                     uint32_t mh_in = lane == 0 ? 0u : (uint32_t)((msg_in >> 1) & 1);
                     const uint32_t *col = sPeq + c * 32 + lane;
+#if MSA_WARP_CHAIN
+                    uint32_t eq[WPL], ph_out, mh_out;
+#pragma unroll
+                    for (int w = 0; w < WPL; ++w) eq[w] = col[w * SIGMA * 32];
+                    bv_column<WPL>(eq, Pv, Mv, ph_in, mh_in, ph_out, mh_out);
+                    msg = (int)(ph_out | (mh_out << 1));
+#else
 #pragma unroll
                     for (int w = 0; w < WPL; ++w)
                         bv_word(col[w * SIGMA * 32], Pv[w], Mv[w], ph_in, mh_in, one, two);
                     msg = (int)(ph_in | (mh_in << 1));
+#endif
                     ++j;
                     if (j == n) {
                         int part = lane == 0 ? 0 : (msg_in >> 2);

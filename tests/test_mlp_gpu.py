@@ -159,11 +159,10 @@ def test_band_policy_and_learned_gain(ctx):
     d_full = api.lev_batch(ctx, sq, pt)
     d_band, k_used = api.lev_banded_batch(ctx, sq, pt, k)
     # the band without the network: the 4-mer lower bound ceil(L1 / 8) <= f
-    Xe = api.pair_features(ctx, sq, prof, pt)
-    meanlen = torch.from_numpy(((lens[pairs[:, 0]] + lens[pairs[:, 1]]) / 2).astype(np.float32)).cuda()
-    l1 = (Xe.float() * meanlen[:, None]).sum(1)
+    cnt = prof.int() & 0xFFFF
+    l1 = (cnt[pt[:, 0].long()] - cnt[pt[:, 1].long()]).abs().sum(1)
     dl = torch.from_numpy(np.abs(lens[pairs[:, 0]] - lens[pairs[:, 1]]).astype(np.int32)).cuda()
-    k_l1 = torch.maximum(dl, torch.ceil(l1 / 8).int())
+    k_l1 = torch.maximum(dl, ((l1 + 7) // 8).int())
     d_l1, _ = api.lev_banded_batch(ctx, sq, pt, k_l1)
     ctx.check()
     np.testing.assert_array_equal(d_band.cpu().numpy(), d_full.cpu().numpy())

@@ -240,6 +240,29 @@ def test_kmer_l1_lower_bound():
         assert l1 <= 8 * oracle.lev(a, b)
 
 
+def test_pair_feature_closed_forms():
+    # AAAAAAA has 4 windows AAAA, AAAAA has 2: the only bin differs by 2, and
+    # its feature is 2^2 / ((7 + 5) / 2) = 2/3 (squared, not 2 / 6)
+    f = oracle.pair_feature(oracle.kmer_counts(b"AAAAAAA"), oracle.kmer_counts(b"AAAAA"), 7, 5)
+    assert f[0] == oracle.bf16_round(np.float32(4.0) / np.float32(6.0))
+    assert np.count_nonzero(f) == 1
+    # a sequence against itself: all zero; the feature is symmetric in (a, b)
+    rng = np.random.default_rng(19)
+    a, b = _rand_dna(rng, 200), _rand_dna(rng, 180)
+    ca, cb = oracle.kmer_counts(a), oracle.kmer_counts(b)
+    assert not oracle.pair_feature(ca, ca, 200, 200).any()
+    np.testing.assert_array_equal(oracle.pair_feature(ca, cb, 200, 180), oracle.pair_feature(cb, ca, 180, 200))
+    # one substitution inside a run of distinct windows moves 4 windows out and
+    # 4 in (8 bins off by one when all 8 are distinct): the sum is 8 / len
+    s = bytearray(b"ACGTTGCAAGCTTCGAATGC")
+    t = bytearray(s)
+    t[10] = ord("A") if s[10] != ord("A") else ord("C")
+    cs, ct = oracle.kmer_counts(bytes(s)), oracle.kmer_counts(bytes(t))
+    assert np.abs(cs - ct).max() == 1 and np.abs(cs - ct).sum() == 8
+    f = oracle.pair_feature(cs, ct, 20, 20)
+    assert f.sum() == pytest.approx(8 / 20, rel=1e-2)
+
+
 def test_bf16_round_against_torch():
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(18)
