@@ -55,6 +55,12 @@ static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
 constexpr float kBandMaxShare = 0.75f;
 constexpr int kBandRounds = 8;
 constexpr int kBandThreads = 128;
+#ifndef MSA_BAND_HEADROOM
+#define MSA_BAND_HEADROOM 0.0f
+#endif
+// a pair's first group holds a band this share wider than requested, so that
+// a near miss retries in place (its retry band is min(d_k, 2k + 1))
+constexpr float kBandHeadroom = MSA_BAND_HEADROOM;
 
 struct BandArgs {
     const uint32_t *planes;
@@ -94,6 +100,8 @@ struct BandEq {
 // lane above sends the Ph/Mh bits of all CPS columns in one word.
 constexpr int kBandCps = MSA_BAND_CPS;
 static_assert(kBandCps >= 1 && 2 * kBandCps <= 8, "columns per step");
+// the carry word of a top block: Ph = 1, Mh (carry) = 0 for each column
+constexpr uint32_t kBandTopBits = 0x55u & ((1u << (2 * kBandCps)) - 1u);
 // capacity of a (G, WPL) group at CPS columns per step: the lane that holds
 // block b must have finished it before block b + G needs it
 __host__ __device__ constexpr int band_capacity(int G, int WPL) { return (G - 1) * 32 * WPL - 2 * kBandCps; }
@@ -191,18 +199,35 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o, G);
                 if (fin) {
-                    if (gl == 0) {
-                        if (d <= k) {
+                    // d_k > k is an upper bound of the distance, so a band of
+                    // d_k certifies; the band at most doubles.  A retry that
+                    // still fits this group runs at once, in place.
+                    const int k2 = min(d, 2 * k + 1);
+                    if (d <= k) {
+                        if (gl == 0) {
                             a.d_out[p] = d;
                             a.k_used[p] = k;
-                        } else {
-                            // d_k > k is an upper bound of the distance, so a
-                            // band of d_k certifies; the band at most doubles
-                            a.k_cur[p] = min(d, 2 * k + 1);
+                        }
+                        has = false;
+                    } else if (k2 <= band_capacity(G, WPL) && k2 < m) {
+                        k = k2;
+                        dlo = -((k + m - n) >> 1);
+                        dhi = (n - m + k) >> 1;
+                        t = 0;
+                        Tb = 0;
+                        acc = 0;
+                        out = 0u;
+                        bk = gl;
+                        if (bk <= bm)
+                            band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv, Mv,
+                                                     E, sPeq, c_next);
+                    } else {
+                        if (gl == 0) {
+                            a.k_cur[p] = k2;
                             a.next_list[atomicAdd(a.next_count, 1)] = p;
                         }
+                        has = false;
                     }
-                    has = false;
                     fin = false;
                 }
             }
@@ -269,18 +294,18 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
 #pragma unroll
                         for (int c = 0; c < CPS; ++c) c_next[c] = j0 + CPS + c < n ? __ldg(tc + j0 + CPS + c) : 0;
                     }
+                    // the block above leaves at a chunk end, so a chunk is
+                    // either all below it or all on top (row above: +1 per
+                    // column, Ph = 1, carry 0 for every column)
+                    const bool top = q > qep;
+                    const uint32_t inb = top ? kBandTopBits : in;
+                    if (top) Tb += min(CPS, n - j0);
+                    const bool last = j0 + CPS >= n;          // the chunk holds column n
                     uint32_t o = 0u;
 #pragma unroll
                     for (int c = 0; c < CPS; ++c) {
-                        const int j = j0 + 1 + c;
-                        if (CPS > 1 && j > n) break;
-                        const bool top = j > jep;
-                        uint32_t ph_in = (in >> (2 * c)) & 1u, mh_in = (in >> (2 * c + 1)) & 1u;
-                        if (top) {
-                            ++Tb;
-                            ph_in = 1u;
-                            mh_in = 0u;
-                        }
+                        // columns past n (in the last chunk) run on symbol 0
+                        // and are never read
                         uint32_t eq[WPL];
                         if constexpr (kShared) {
                             const uint32_t *row = sPeq + (cc[c] & 3) * WPL * kBandThreads;
@@ -299,9 +324,9 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                             }
                         }
                         uint32_t ph_out, mh_out;
-                        bv_column<WPL>(eq, Pv, Mv, ph_in, mh_in, ph_out, mh_out);
+                        bv_column<WPL>(eq, Pv, Mv, (inb >> (2 * c)) & 1u, (inb >> (2 * c + 1)) & 1u, ph_out, mh_out);
                         o |= (ph_out | (mh_out << 1)) << (2 * c);
-                        if (j == n) {
+                        if (last && j0 + 1 + c == n) {
                             // this block's share of D[m][n]: its rows <= m (and T if on top)
                             int part = top ? Tb : 0;
 #pragma unroll
@@ -405,7 +430,7 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
         int b = -1;
         if (ly > 0 && lx > 0) {
             for (int c = 0; c < nb; ++c)
-                if (band_capacity(kBandG[c], kBandWPL[c]) >= k) {
+                if ((float)band_capacity(kBandG[c], kBandWPL[c]) >= (float)k * (1.f + kBandHeadroom)) {
                     b = c;
                     break;
                 }

@@ -93,7 +93,7 @@ def train(ctx: api.Context, X: torch.Tensor, y: torch.Tensor, epochs: float = 4.
 
 
 def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof: torch.Tensor,
-               pairs: torch.Tensor, candidates=(0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 2):
+               pairs: torch.Tensor, candidates=(-0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 2):
     """The band margin gamma with the fastest certified banded run on a
     validation batch (timed with CUDA events; all candidates are exact)."""
     best, best_t = candidates[0], float("inf")
