@@ -153,6 +153,14 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
 #define MSA_LANE_CHAIN 3
 #endif
 
+// Lane kernel match masks: [symbol][word], WC words padded to a stride of 4
+// mod 8 words, so a 16-byte load of 4 words starts aligned and the 4 symbols'
+// rows fall on disjoint bank groups (lanes of a warp reading different
+// symbols never conflict; lanes reading the same symbol share a broadcast).
+__host__ __device__ constexpr int lane_peq_stride(int WC) {
+    return ((WC + 3) / 4 * 4) % 8 == 0 ? (WC + 3) / 4 * 4 + 4 : (WC + 3) / 4 * 4;
+}
+
 // One column over WC words, in chunks of up to 8 words: the chunk's
 // (Eq & Pv) + Pv additions run on the hardware carry chain (add.cc/addc), and
 // the shifts by one take the lower word's top bit by funnel shift, so no
@@ -164,7 +172,7 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
 // neither Mh nor Xh is formed (Ph = Mv | ~(Xh | Pv) = Mv | ~(sum | Pv | Eq)),
 // 9 ops per word instead of 10.  Variants 2 and 4 issue the addition as a
 // multiply-add by a runtime one (madc), on the FMA pipe.
-template <int WC, int SIGMA>
+template <int WC>
 __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t (&Pv)[WC], uint32_t (&Mv)[WC],
                                                   uint32_t one) {
     uint32_t cy = 0u, ph_prev = 0u, mh_prev = 0u;
@@ -175,9 +183,12 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
         const int len = WC - k0 < kMax ? WC - k0 : kMax;
         if (len == 8) {
             uint32_t eq[8], u[8], pv[8], s[8];
+            const uint4 e0 = reinterpret_cast<const uint4 *>(row + k0)[0];
+            const uint4 e1 = reinterpret_cast<const uint4 *>(row + k0)[1];
+            eq[0] = e0.x; eq[1] = e0.y; eq[2] = e0.z; eq[3] = e0.w;
+            eq[4] = e1.x; eq[5] = e1.y; eq[6] = e1.z; eq[7] = e1.w;
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
-                eq[w] = row[(k0 + w) * SIGMA];
                 pv[w] = Pv[k0 + w];
                 u[w] = eq[w] & pv[w];
             }
@@ -214,7 +225,7 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
             for (int w = 0; w < kMax; ++w) {
                 if (w >= len) break;
                 const int k = k0 + w;
-                const uint32_t eq = row[k * SIGMA];
+                const uint32_t eq = row[k];
                 const uint32_t pv = Pv[k];
                 const uint32_t u = eq & pv;
                 const uint64_t t = (uint64_t)u + pv + cy;
@@ -300,14 +311,16 @@ __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
 
 // ---------------------------------------------------------------------------
 // Lane kernel: one warp per query, each lane streams its own targets.
-// Match masks of the query live in shared memory, layout [k][c] so lanes that
-// read different symbols hit different banks.  Pv/Mv: WC words in registers.
+// Match masks of the query live in shared memory, layout [c][k] with a padded
+// stride (lane_peq_stride), read 4 words per load.  Pv/Mv: WC words in
+// registers.
 // ---------------------------------------------------------------------------
 template <int WC, int B, int SIGMA>
 __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
-    uint32_t *sPeq = smem + (threadIdx.x >> 5) * (WC * SIGMA);
+    constexpr int S = lane_peq_stride(WC);
+    uint32_t *sPeq = smem + (threadIdx.x >> 5) * (S * SIGMA);
     const uint32_t one = a.one, two = a.two;
     const int ntasks = a.bcount[a.bucket];
     const int2 *tasks = a.tasks + a.boff[a.bucket];
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
             uint32_t pl[B], mask;
             query_planes<B>(a.planes, qpos, m, k, pl, mask);
 #pragma unroll
-            for (int c = 0; c < SIGMA; ++c) sPeq[k * SIGMA + c] = match_mask<B, SIGMA>(pl, mask, c);
+            for (int c = 0; c < SIGMA; ++c) sPeq[c * S + k] = match_mask<B, SIGMA>(pl, mask, c);
         }
         __syncwarp();
         const int cbeg = a.qstart[q];
@@ -366,13 +379,13 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
                 if (j < n) {
                     const int c = c_next;
                     if (j + 1 < n) c_next = __ldg(tc + j + 1);
-                    const uint32_t *row = sPeq + c;
+                    const uint32_t *row = sPeq + c * S;
 #if MSA_LANE_CHAIN
-                    lane_column_chain<WC, SIGMA>(row, Pv, Mv, one);
+                    lane_column_chain<WC>(row, Pv, Mv, one);
 #else
                     uint32_t ph_in = 1u, mh_in = 0u;
 #pragma unroll
-                    for (int k = 0; k < WC; ++k) bv_word(row[k * SIGMA], Pv[k], Mv[k], ph_in, mh_in, one, two);
+                    for (int k = 0; k < WC; ++k) bv_word(row[k], Pv[k], Mv[k], ph_in, mh_in, one, two);
 #endif
                     ++j;
                 }
@@ -534,7 +547,7 @@ struct LevKernelInfo {
 
 template <int WC, int B, int SIGMA>
 void launch_lane(const LevArgs &a, int grid, cudaStream_t st) {
-    lev_lane_kernel<WC, B, SIGMA><<<grid, 128, 4 * WC * SIGMA * sizeof(uint32_t), st>>>(a);
+    lev_lane_kernel<WC, B, SIGMA><<<grid, 128, 4 * lane_peq_stride(WC) * SIGMA * sizeof(uint32_t), st>>>(a);
 }
 
 template <int WPL, int B, int SIGMA>
