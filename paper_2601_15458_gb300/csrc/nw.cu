@@ -51,6 +51,8 @@ struct NwArgs {
     int64_t slab_bytes;
     int32_t max_len;        // slab capacity in rows / columns
     int32_t *counter;
+    const int32_t *plist;   // optional pair ids (count at *pcount); all pairs when null
+    const int32_t *pcount;
     int32_t *err;
 };
 
@@ -67,11 +69,13 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
     uint32_t *tb = reinterpret_cast<uint32_t *>(slab + (((int64_t)a.max_len + 1) * 4 + 255) / 256 * 256);
     const int gap = a.gap, match = a.match, mismatch = a.mismatch;
 
+    const int64_t count = a.plist ? (int64_t)*a.pcount : a.P;
     while (true) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(a.counter, 1);
-        p = __shfl_sync(FULL, p, 0);
-        if (p >= a.P) break;
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(a.counter, 1);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= count) break;
+        const int p = a.plist ? a.plist[idx] : idx;
         const int x = a.pairs[2 * p], y = a.pairs[2 * p + 1];
         bool ok = x >= 0 && x < a.n_seqs && y >= 0 && y < a.n_seqs;
         int64_t xa = 0, xb = 0, ya = 0, yb = 0;
@@ -221,12 +225,19 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
     }
 }
 
+// Per-warp scratch, large enough for either kernel (the bit-parallel one for
+// the unit cost model, the plain DP for the rest); the two run one after the
+// other on the same slabs.
 int64_t nw_slab_bytes(int max_len) {
     const int64_t brow = (((int64_t)max_len + 1) * 4 + 255) / 256 * 256;
     const int64_t tiles = (max_len + kNwTile - 1) / kNwTile;
     const int64_t tbw = tiles * 32 * (int64_t)std::max(max_len, 1) * 4;
-    return brow + (tbw + 255) / 256 * 256;
+    return std::max(brow + (tbw + 255) / 256 * 256, nw_bv_slab_bytes(max_len));
 }
+
+#ifndef MSA_NW_BV
+#define MSA_NW_BV 1
+#endif
 
 msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
                   int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
@@ -237,28 +248,44 @@ msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *
     if (P == 0) return MSA_OK;
     if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: null pointer");
-    static int occ = 0;
+    static int occ = 0, occ_bv = 0;
     if (occ == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_kernel, kNwWarps * 32, 0);
         if (e != cudaSuccess) return cuda_check(ctx, e, "nw occupancy");
         if (occ < 1) occ = 1;
+        occ_bv = nw_bv_occupancy();
     }
+    // unit costs (match 0, mismatch = gap > 0): the bit-parallel kernel, with
+    // the plain DP for the pairs it hands back
+    const bool unit = MSA_NW_BV && match == 0 && mismatch == gap && gap > 0;
     int32_t *counter = ar.take<int32_t>(64);
+    int32_t *fb_list = unit ? ar.take<int32_t>(P) : nullptr;
     const int64_t slab = nw_slab_bytes(max_len);
-    const int64_t avail = counter ? ar.cap - ar.used : 0;
-    int64_t warps = std::min<int64_t>((int64_t)ctx->sm_count * occ * kNwWarps, avail / slab);
+    const int64_t avail = counter && (!unit || fb_list) ? ar.cap - ar.used : 0;
+    const int64_t want = (int64_t)ctx->sm_count * std::max(occ, unit ? occ_bv : 0) * kNwWarps;
+    int64_t warps = std::min<int64_t>(want, avail / slab);
     warps = std::min<int64_t>(warps, ((P + kNwWarps - 1) / kNwWarps) * kNwWarps);
     warps = warps / kNwWarps * kNwWarps;
     if (warps < kNwWarps)
         return set_error(ctx, MSA_ENOMEM, "msa_nw_align_batch: max_len %d needs %lld workspace bytes per warp group",
-                         max_len, (long long)(slab * kNwWarps + 256));
+                         max_len, (long long)(slab * kNwWarps + 256 + (unit ? 4 * P : 0)));
     char *slabs = ar.take<char>(warps * slab);
-    cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4 * 64, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
-    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, gap, score_out, ops_out, ops_off,
-             ops_len_out, slabs, slab, max_len, counter, ctx->dev_err};
     ProfScope prof(ctx, st);
-    nw_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a);
+    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, gap, score_out, ops_out, ops_off,
+             ops_len_out, slabs, slab, max_len, counter, nullptr, nullptr, ctx->dev_err};
+    if (unit) {
+        const int64_t wbv = std::min<int64_t>(warps, (int64_t)ctx->sm_count * occ_bv * kNwWarps) / kNwWarps * kNwWarps;
+        e = nw_bv_launch(ctx, codes, offs, n_seqs, total, max_len, pairs, P, gap, score_out, ops_out, ops_off,
+                         ops_len_out, slabs, slab, std::max<int64_t>(wbv, kNwWarps), counter, fb_list, counter + 32, st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "nw launch");
+        a.counter = counter + 1;
+        a.plist = fb_list;
+        a.pcount = counter + 32;
+    }
+    const int64_t wdp = std::min<int64_t>(warps, (int64_t)ctx->sm_count * occ * kNwWarps) / kNwWarps * kNwWarps;
+    nw_kernel<<<(int)(std::max<int64_t>(wdp, kNwWarps) / kNwWarps), kNwWarps * 32, 0, st>>>(a);
     ++ctx->launches;
     return cuda_check(ctx, cudaGetLastError(), "nw launch");
 }

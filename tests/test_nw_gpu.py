@@ -49,7 +49,7 @@ def test_small_dna_pairs(ctx):
     _check(ctx, ds.seqs(), pairs)
 
 
-@pytest.mark.parametrize("costs", [(0, 1, 1), (0, 3, 2), (-1, 2, 3)])
+@pytest.mark.parametrize("costs", [(0, 1, 1), (0, 2, 2), (0, 3, 2), (-1, 2, 3)])
 def test_bruteforce_tiny(ctx, costs):
     rng = np.random.default_rng(sum(costs) + 40)
     rows = [rng.choice(list(b"ACG-"), size=int(rng.integers(0, 7))).astype(np.uint8).tobytes() for _ in range(40)]
@@ -95,6 +95,22 @@ def test_protein_center_rows(ctx):
     rows = members.seqs() + roots.seqs()
     pairs = [[members.n + f, f * 10 + k] for f in range(4) for k in range(10)]
     _check(ctx, rows, pairs)
+
+
+def test_unit_cost_many_symbols_and_absent_symbols(ctx):
+    """Unit costs run bit-parallel over the distinct bytes of the row
+    sequence; rows with more than 32 distinct bytes go to the plain DP in the
+    same call; column bytes absent from the row sequence never match."""
+    rng = np.random.default_rng(43)
+    rows = []
+    for L in (300, 2100, 40, 2049):
+        rows.append(rng.integers(0, 256, size=L).astype(np.uint8).tobytes())          # many distinct bytes
+        rows.append(rng.choice(list(b"ACGT-"), size=L).astype(np.uint8).tobytes())    # 5 symbols
+        rows.append(rng.choice(list(b"acgtXYZ"), size=L // 2 + 1).astype(np.uint8).tobytes())  # disjoint
+    n = len(rows)
+    pairs = [[i, j] for i in range(n) for j in range(n) if (i + j) % 3 != 2]
+    _check(ctx, rows, pairs)
+    _check(ctx, rows, pairs[:40], (0, 2, 2))
 
 
 def test_capacity_error(ctx):
