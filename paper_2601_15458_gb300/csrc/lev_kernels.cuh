@@ -152,6 +152,9 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
 #ifndef MSA_LANE_CHAIN
 #define MSA_LANE_CHAIN 3
 #endif
+#ifndef MSA_LANE_UNROLL
+#define MSA_LANE_UNROLL 2
+#endif
 
 // Lane kernel match masks: [symbol][word], WC words padded to a stride of 4
 // mod 8 words, so a 16-byte load of 4 words starts aligned and the 4 symbols'
@@ -315,8 +318,14 @@ __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
 // stride (lane_peq_stride), read 4 words per load.  Pv/Mv: WC words in
 // registers.
 // ---------------------------------------------------------------------------
+#ifndef MSA_LANE_MINB
+#define MSA_LANE_MINB 1
+#endif
+// MSA_LANE_MINB = 4 caps registers for 4 resident blocks (16 warps per SM)
+// where the bit vectors still fit (up to 52 words); measured slower than the
+// uncapped build (53.6-54.7 vs 55.9 TCUPS on 2,000 x 1,500 all pairs)
 template <int WC, int B, int SIGMA>
-__global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
+__global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_kernel(LevArgs a) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
     constexpr int S = lane_peq_stride(WC);
@@ -350,7 +359,7 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
             Pv[k] = kFull;
             Mv[k] = 0u;
         }
-        int n = 0, j = 0, pid = -1, c_next = 0;
+        int n = 0, j = 0, pid = -1, c_next = 0, c_next2 = 0;
         bool has = false, more = true;
         const uint8_t *tc = nullptr;
         while (true) {
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
                     tc = a.codes + tp;
                     j = 0;
                     c_next = n > 0 ? __ldg(tc) : 0;
+                    c_next2 = n > 1 ? __ldg(tc + 1) : 0;
 #pragma unroll
                     for (int k = 0; k < WC; ++k) {
                         Pv[k] = kFull;
@@ -375,10 +385,26 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
                 }
             }
             if (!__any_sync(kFull, has)) break;
+#if MSA_LANE_UNROLL == 2
+            // two columns per iteration while every busy lane has two left:
+            // the second column's first words overlap the first column's
+            // last ones, and the vote is paid once per two columns
+            const bool pair2 = __all_sync(kFull, !has || j + 1 < n);
+#else
+            const bool pair2 = false;
+#endif
             if (has) {
-                if (j < n) {
+                if (pair2) {
+                    const int c0 = c_next, c1 = c_next2;
+                    c_next = j + 2 < n ? __ldg(tc + j + 2) : 0;
+                    c_next2 = j + 3 < n ? __ldg(tc + j + 3) : 0;
+                    lane_column_chain<WC>(sPeq + c0 * S, Pv, Mv, one);
+                    lane_column_chain<WC>(sPeq + c1 * S, Pv, Mv, one);
+                    j += 2;
+                } else if (j < n) {
                     const int c = c_next;
-                    if (j + 1 < n) c_next = __ldg(tc + j + 1);
+                    c_next = c_next2;
+                    c_next2 = j + 2 < n ? __ldg(tc + j + 2) : 0;
                     const uint32_t *row = sPeq + c * S;
 #if MSA_LANE_CHAIN
                     lane_column_chain<WC>(row, Pv, Mv, one);
