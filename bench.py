@@ -238,6 +238,7 @@ def band_bench(ctx, args, stream):
                             api.lev_banded_batch(ctx, es, pairs, k, d_band, k_used)), reps)
     t_l1 = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_l1, d_l1), reps)
     ctx.check()
+    args.band_model = (model, gamma)
     return dict(workload=f"divergent_dna_pairs_{P}_len1000-10000_div1-30pct", pairs=P, cells=cells,
                 pairs_per_s_learned=P / (t_band / 1e3), pairs_per_s_full=P / (t_full / 1e3),
                 pairs_per_s_l1_bound=P / (t_l1 / 1e3), speedup_learned_vs_full=t_full / t_band,
@@ -254,11 +255,26 @@ def clam_bench(ctx, args):
     clusters and the MSA rows checked against their sequences."""
     import torch
     from paper_2601_15458_gb300 import api, synth
+    from paper_2601_15458_gb300 import learned_band
+    model, gamma = getattr(args, "band_model", (None, None))
+    if model is None:
+        X, y, _ = learned_band.training_set(ctx, seed=4)
+        model, _ = learned_band.train(ctx, X, y, epochs=8, batch=4096, lr=2e-3, tau=0.9)
+        del X, y
+        gamma = 0.2
     t0 = time.perf_counter()
     ds = synth.gg16s_dna(seed=5, n=args.clam)
     gen_s = time.perf_counter() - t0
     sq = api.upload_and_pack(ctx, ds)
+    prof = api.kmer_profile(ctx, sq)
     ctx.check()
+    # learned band on: the same tree from banded distance batches
+    api.clam_partition(ctx, api.upload_and_pack(ctx, synth.small_dna(seed=1)), band=model, gamma=gamma)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree_b = api.clam_partition(ctx, sq, band=model, prof=prof, gamma=gamma)
+    torch.cuda.synchronize()
+    t_part_b = time.perf_counter() - t0
     ctx.prof_read(reset=True)
     ctx.prof_enable(True)
     torch.cuda.synchronize()
@@ -267,6 +283,9 @@ def clam_bench(ctx, args):
     torch.cuda.synchronize()
     t_part = time.perf_counter() - t0
     part_dp_ms, part_launches = ctx.prof_read(reset=True)
+    same_tree = bool(np.array_equal(tree.order.cpu().numpy(), tree_b.order.cpu().numpy())
+                     and np.array_equal(tree.center, tree_b.center) and np.array_equal(tree.left, tree_b.left)
+                     and np.array_equal(tree.lo, tree_b.lo))
     t0 = time.perf_counter()
     pos, width, score = api.merge_tree(ctx, sq, tree)
     torch.cuda.synchronize()
@@ -297,6 +316,8 @@ def clam_bench(ctx, args):
         if tree.left[k] >= 0:
             nw_cells += int(width[tree.left[k]]) * int(width[tree.right[k]])
     return dict(workload=f"gg16s_dna_{ds.n}_len1400-1600", n_seqs=ds.n, partition_s=t_part, merge_s=t_merge,
+                partition_learned_band_s=t_part_b, learned_band_speedup=t_part / t_part_b,
+                learned_band_gamma=gamma, learned_band_same_tree=same_tree,
                 partition_dp_ms=part_dp_ms, merge_dp_ms=merge_dp_ms, launches=part_launches + merge_launches,
                 tree_depth=int(depth.max()), msa_width=int(width[0]), nw_cells=nw_cells,
                 nw_gcups=nw_cells / (merge_dp_ms / 1e3) / 1e9 if merge_dp_ms else None,

@@ -64,6 +64,9 @@ SIGNATURES = {
                                    c_float, c_int32, c_void_p, c_void_p, c_void_p]),
     "msa_clam_partition": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "msa_clam_partition_banded": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_float, c_int32,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p]),
     "msa_merge_tree": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                  c_void_p, c_void_p]),

@@ -359,13 +359,24 @@ def _np_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def clam_partition(ctx: Context, seqs: DeviceSeqs, stream=None) -> Tree:
-    """A11: build the guide tree (msa_clam_partition)."""
+def clam_partition(ctx: Context, seqs: DeviceSeqs, band: "BandModel | None" = None, prof: torch.Tensor | None = None,
+                   gamma: float = 0.2, margin: int = 8, stream=None) -> Tree:
+    """A11: build the guide tree (msa_clam_partition).
+
+    With ``band`` (a trained :class:`BandModel`) the distance batches start
+    from the network's bands (msa_clam_partition_banded); the tree is the same.
+    """
     t = Tree(seqs.n)
     nn = ctypes.c_int32(0)
-    ctx.raise_if(_lib.lib().msa_clam_partition(ctx.handle, ctypes.byref(seqs.c), _ptr(t.order), _np_ptr(t.lo),
-                                               _np_ptr(t.hi), _np_ptr(t.center), _np_ptr(t.left), _np_ptr(t.right),
-                                               _np_ptr(t.parent), ctypes.byref(nn), _stream(stream)))
+    outs = (_ptr(t.order), _np_ptr(t.lo), _np_ptr(t.hi), _np_ptr(t.center), _np_ptr(t.left), _np_ptr(t.right),
+            _np_ptr(t.parent), ctypes.byref(nn), _stream(stream))
+    if band is None:
+        ctx.raise_if(_lib.lib().msa_clam_partition(ctx.handle, ctypes.byref(seqs.c), *outs))
+    else:
+        if prof is None:
+            prof = kmer_profile(ctx, seqs, stream)
+        ctx.raise_if(_lib.lib().msa_clam_partition_banded(ctx.handle, ctypes.byref(seqs.c), _ptr(band.state),
+                                                          _ptr(prof), gamma, margin, *outs))
     t.n_nodes = nn.value
     return t
 

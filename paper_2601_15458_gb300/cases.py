@@ -6,6 +6,7 @@
     python -m paper_2601_15458_gb300.cases band_small  # the same on 20,000 pairs (for ncu captures)
     python -m paper_2601_15458_gb300.cases pack    # packed loader, 1.1 GB arena
     python -m paper_2601_15458_gb300.cases mlp     # band network forward + one training step
+    python -m paper_2601_15458_gb300.cases protein # 10,000 x 100 centre distances, 9,999 NW with traceback
 
 Each case runs its call a few times (the first warms up) and prints one
 line with the call's device time.
@@ -85,7 +86,33 @@ def case_mlp(ctx):
     return _time(lambda: model.train_step(X, y, idx, lr=1e-3))
 
 
-CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp)
+def case_protein(ctx):
+    members, roots = synth.protein_families(seed=3)
+    allseq = synth.SeqSet.from_list(members.seqs() + roots.seqs(), "protein")
+    nm = members.n
+    sq = api.upload_and_pack(ctx, allseq)
+    lens = np.diff(allseq.offs).astype(np.int64)
+    cen = np.array([[nm + c, x] for c in range(roots.n) for x in range(nm)], np.int32)
+    fam = members.extra["family"]
+    aln = np.array([[x, nm + int(fam[x])] for x in range(nm - 1)], np.int32)
+    cen_d = torch.from_numpy(cen).cuda()
+    aln_d = torch.from_numpy(aln).cuda()
+    out = torch.empty(len(cen), dtype=torch.int32, device="cuda")
+    t_lev = _time(lambda: api.lev_batch(ctx, sq, cen_d, out))
+    bs = api.ByteSeqs.from_device_seqs(sq)
+    cap = torch.from_numpy(lens[aln[:, 0]] + lens[aln[:, 1]]).cuda()
+    off = torch.zeros(len(aln) + 1, dtype=torch.int64, device="cuda")
+    torch.cumsum(cap, 0, out=off[1:])
+    t_nw = _time(lambda: api.nw_align_batch(ctx, bs, aln_d, ops_off=off))
+    c_lev = int((lens[cen[:, 0]] * lens[cen[:, 1]]).sum())
+    c_nw = int((lens[aln[:, 0]] * lens[aln[:, 1]]).sum())
+    print(f"centre distances: {len(cen)} pairs, {t_lev:.3f} ms, {c_lev / t_lev / 1e9:.1f} TCUPS")
+    print(f"NW with traceback: {len(aln)} pairs, {t_nw:.3f} ms, {c_nw / t_nw / 1e9:.2f} TCUPS")
+    return t_lev + t_nw
+
+
+CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
+             protein=case_protein)
 
 
 def main(argv):

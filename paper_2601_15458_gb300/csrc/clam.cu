@@ -320,15 +320,18 @@ static msa_status h2d(msa_ctx *ctx, T *dst, const std::vector<T> &src, cudaStrea
                       "host to device copy");
 }
 
-}  // namespace msa
+// Starting bands of the distance batches from the band network (nullptr:
+// every batch runs the full DP).
+struct PartitionBand {
+    const void *state;
+    const uint16_t *prof;
+    float gamma;
+    int32_t margin;
+};
 
-using namespace msa;
-
-extern "C" {
-
-msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order, int32_t *lo, int32_t *hi,
-                              int32_t *center, int32_t *left, int32_t *right, int32_t *parent, int32_t *n_nodes,
-                              void *stream) {
+static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const PartitionBand *band, int32_t *order,
+                                     int32_t *lo, int32_t *hi, int32_t *center, int32_t *left, int32_t *right,
+                                     int32_t *parent, int32_t *n_nodes, void *stream) {
     msa_status rc = lev_validate(ctx, s, order, 1, order, "msa_clam_partition");
     if (rc) return rc;
     if (!lo || !hi || !center || !left || !right || !parent || !n_nodes)
@@ -377,8 +380,24 @@ msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order,
         int32_t *pairs = ar.take<int32_t>(2 * std::max(PM, PC));
         int32_t *dm = ar.take<int32_t>(PM), *dc = ar.take<int32_t>(PC), *dl = ar.take<int32_t>(PC),
                 *dr = ar.take<int32_t>(PC);
-        if (!dr || ar.cap - ar.used < lev_workspace(std::max(PM, PC), N))
+        const int64_t PX = std::max(PM, PC);
+        const int64_t need = band ? msa_lev_banded_workspace_bytes(PX, N) + 3 * ((4 * PX + 255) / 256 * 256)
+                                  : lev_workspace(PX, N);
+        if (!dr || ar.cap - ar.used < need)
             return set_error(ctx, MSA_ENOMEM, "msa_clam_partition: workspace too small for a level of %d clusters", A);
+        // one distance batch: the full DP, or the network's band and the
+        // certified banded DP (exact either way)
+        auto dist = [&](const int32_t *pr, int64_t np, int32_t *out) -> msa_status {
+            Arena tmp = ar;
+            if (!band) return lev_run(ctx, s, pr, np, out, st, nullptr, nullptr, &tmp);
+            float *yhat = tmp.take<float>(np);
+            int32_t *k0 = tmp.take<int32_t>(np), *ku = tmp.take<int32_t>(np);
+            if (!ku) return set_error(ctx, MSA_ENOMEM, "msa_clam_partition_banded: workspace");
+            msa_status r2 = msa_band_predict(ctx, band->state, s, band->prof, pr, np, band->gamma, band->margin,
+                                             yhat, k0, st);
+            if (r2) return r2;
+            return lev_banded_run(ctx, s, pr, np, k0, out, ku, st, tmp);
+        };
         if ((rc = h2d(ctx, d_lo, hlo, st)) || (rc = h2d(ctx, d_sz, hsz, st)) || (rc = h2d(ctx, d_poff, poff, st)) ||
             (rc = h2d(ctx, d_soff, soff, st)) || (rc = h2d(ctx, d_moff, moff, st)))
             return rc;
@@ -386,29 +405,17 @@ msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order,
         if (e != cudaSuccess) return cuda_check(ctx, e, "partition memset");
         const int g = std::min(A, 65535);
         medoid_pairs_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_poff, A, pairs);
-        {
-            Arena tmp = ar;
-            if ((rc = lev_run(ctx, s, pairs, PM, dm, st, nullptr, nullptr, &tmp))) return rc;
-        }
+        if ((rc = dist(pairs, PM, dm))) return rc;
         medoid_sums_kernel<<<g, 256, 0, st>>>(d_sz, d_poff, d_soff, A, dm, sums);
         medoid_argmin_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_soff, A, sums, d_c);
         one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_c, pairs);
-        {
-            Arena tmp = ar;
-            if ((rc = lev_run(ctx, s, pairs, PC, dc, st, nullptr, nullptr, &tmp))) return rc;
-        }
+        if ((rc = dist(pairs, PC, dc))) return rc;
         argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dc, d_l);
         one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_l, pairs);
-        {
-            Arena tmp = ar;
-            if ((rc = lev_run(ctx, s, pairs, PC, dl, st, nullptr, nullptr, &tmp))) return rc;
-        }
+        if ((rc = dist(pairs, PC, dl))) return rc;
         argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dl, d_r);
         one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_r, pairs);
-        {
-            Arena tmp = ar;
-            if ((rc = lev_run(ctx, s, pairs, PC, dr, st, nullptr, nullptr, &tmp))) return rc;
-        }
+        if ((rc = dist(pairs, PC, dr))) return rc;
         split_kernel<<<g, 1024, 0, st>>>(order, order_tmp, d_lo, d_sz, d_moff, A, dl, dr, d_nl);
         ctx->launches += 9;
         // copy the partitioned ranges back (only the active ranges changed)
@@ -457,6 +464,31 @@ msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order,
     *n_nodes = nn;
     return MSA_OK;
 }
+
+}  // namespace msa
+
+using namespace msa;
+
+extern "C" {
+
+msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order, int32_t *lo, int32_t *hi,
+                              int32_t *center, int32_t *left, int32_t *right, int32_t *parent, int32_t *n_nodes,
+                              void *stream) {
+    return clam_partition_run(ctx, s, nullptr, order, lo, hi, center, left, right, parent, n_nodes, stream);
+}
+
+msa_status msa_clam_partition_banded(msa_ctx *ctx, const msa_seqset *s, const void *state, const uint16_t *prof,
+                                     float gamma, int32_t margin, int32_t *order, int32_t *lo, int32_t *hi,
+                                     int32_t *center, int32_t *left, int32_t *right, int32_t *parent,
+                                     int32_t *n_nodes, void *stream) {
+    if (!ctx) return MSA_EINVAL;
+    if (!state || !prof) return set_error(ctx, MSA_EINVAL, "msa_clam_partition_banded: null pointer");
+    if (!s || s->alphabet != MSA_DNA)
+        return set_error(ctx, MSA_EUNSUPPORTED, "msa_clam_partition_banded: the band network reads DNA 4-mers");
+    const PartitionBand band{state, prof, gamma, margin};
+    return clam_partition_run(ctx, s, &band, order, lo, hi, center, left, right, parent, n_nodes, stream);
+}
+
 
 msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
                           const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,

@@ -493,14 +493,13 @@ int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs) {
     return r(4 * P) * 6 + r(4 * kBandMeta) + r(16) + lev_workspace(P, n_seqs);
 }
 
-msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
-                                const int32_t *k0, int32_t *d_out, int32_t *k_used_out, void *stream) {
-    msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_banded_batch");
-    if (rc || P == 0) return rc;
-    if (!k0 || !k_used_out) return set_error(ctx, MSA_EINVAL, "msa_lev_banded_batch: null pointer");
-    if (s->n_seqs == 0) return set_error(ctx, MSA_EINVAL, "msa_lev_banded_batch: pairs given for an empty set");
-    cudaStream_t st = (cudaStream_t)stream;
-    Arena ar{ctx->ws, ctx->ws_bytes};
+}  // extern "C"
+
+namespace msa {
+
+msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const int32_t *k0,
+                          int32_t *d_out, int32_t *k_used_out, cudaStream_t st, Arena &ar) {
+    msa_status rc = MSA_OK;
     int32_t *k_cur = ar.take<int32_t>(P);
     int32_t *list_a = ar.take<int32_t>(P);
     int32_t *list_b = ar.take<int32_t>(P);
@@ -595,6 +594,20 @@ msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t
     ctx->launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(ctx, e, "band launch");
     return lev_run(ctx, s, pairs, P, d_out, st, full_list2, counts + 3, &ar);
+}
+
+}  // namespace msa
+
+extern "C" {
+
+msa_status msa_lev_banded_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P,
+                                const int32_t *k0, int32_t *d_out, int32_t *k_used_out, void *stream) {
+    msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_banded_batch");
+    if (rc || P == 0) return rc;
+    if (!k0 || !k_used_out) return set_error(ctx, MSA_EINVAL, "msa_lev_banded_batch: null pointer");
+    if (s->n_seqs == 0) return set_error(ctx, MSA_EINVAL, "msa_lev_banded_batch: pairs given for an empty set");
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    return lev_banded_run(ctx, s, pairs, P, k0, d_out, k_used_out, (cudaStream_t)stream, ar);
 }
 
 }  // extern "C"

@@ -100,6 +100,11 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
 msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const void *out,
                         const char *who);
 int64_t lev_workspace(int64_t P, int32_t n);
+// Certified banded Levenshtein over a pair list with scratch from `ar`
+// (msa_lev_banded_batch's body).
+msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, const int32_t *k0,
+                          int32_t *d_out, int32_t *k_used_out, cudaStream_t st, Arena &ar);
+
 // Bit-parallel NW for the unit cost model (nw_bv.cu), launched by nw_run.
 int64_t nw_bv_slab_bytes(int max_len);
 int nw_bv_occupancy();

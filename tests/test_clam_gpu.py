@@ -2,6 +2,7 @@
 on the GPU against the oracle: identical trees, identical MSAs."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2601_15458_gb300 import api, synth
@@ -96,3 +97,32 @@ def test_larger_tree_sampled_nodes(ctx):
     for r in rng.choice(ds.n, 50, replace=False):
         assert rows[r].tobytes().replace(b"-", b"") == seqs[order[r]]
     assert not np.any(np.all(rows == ord("-"), axis=0))
+
+
+@pytest.mark.parametrize("gamma", [0.2, -0.9])
+def test_banded_partition_same_tree(ctx, gamma):
+    """Alg. 1 with every distance batch from the network's band and the
+    certified banded DP: the same tree as the full DP, whatever the network
+    (an untrained one here; gamma = -0.9 starts almost every band too narrow,
+    so the retries decide)."""
+    model = api.BandModel(ctx, seed=0)
+    ds = synth.small_dna(seed=1)
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq, band=model, gamma=gamma, margin=0)
+    ctx.check()
+    _check_same_tree(_gpu_nodes(tree), oracle.partition(ds.seqs()))
+    ds = synth.gg16s_dna(seed=5, n=1500)
+    sq = api.upload_and_pack(ctx, ds)
+    full = api.clam_partition(ctx, sq)
+    banded = api.clam_partition(ctx, sq, band=model, gamma=gamma, margin=0)
+    ctx.check()
+    _check_same_tree(_gpu_nodes(banded), _gpu_nodes(full))
+
+
+def test_banded_partition_rejects_protein(ctx):
+    model = api.BandModel(ctx, seed=0)
+    members, _ = synth.protein_families(seed=3, n_fam=2, per_fam=5)
+    sq = api.upload_and_pack(ctx, members)
+    prof = torch.zeros((members.n, 256), dtype=torch.int16, device="cuda")
+    with pytest.raises(api.MsaError):
+        api.clam_partition(ctx, sq, band=model, prof=prof)
