@@ -35,6 +35,88 @@ Tune *create_tune();
 // word: two 16-byte loads, a 256-entry table lookup per byte, two 16-byte
 // stores of codes and B plane words.  Traffic 1 + 1 + B/8 bytes per residue.
 // ---------------------------------------------------------------------------
+// DNA, 4 residues per integer op (SWAR): for A, C, G, T (0x41, 0x43, 0x47,
+// 0x54) the code is ((c >> 1) ^ (c >> 2)) & 3 = 0, 1, 2, 3, computed for the 4
+// bytes of a word at once; the word is valid when the byte permute of "ACGT"
+// by those codes gives back the 4 bytes (compared in the order 0, 2, 1, 3,
+// the order in which c | c >> 12 lays the codes out as permute selectors);
+// plane p's 4 bits are gathered by one multiply, ((c >> p) & 0x01010101) *
+// 0x10204080 >> 28 (the partial products never overlap, so no carries).  A
+// word with another byte takes the per-byte path: the first bad byte is
+// recorded and bad bytes get code 0, as in pack_kernel.
+__device__ __forceinline__ uint32_t dna_code_of(uint32_t b) {
+    return b == 'A' ? 0u : b == 'C' ? 1u : b == 'G' ? 2u : b == 'T' ? 3u : 0xFFu;
+}
+
+__global__ void __launch_bounds__(256) pack_dna_kernel(const uint8_t *__restrict__ ascii, int64_t total,
+                                                       uint8_t *__restrict__ codes, uint32_t *__restrict__ planes,
+                                                       int64_t nwords, int32_t *err) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = w * 32;
+        uint32_t x[8];
+        const bool full = base + 32 <= total;
+        if (full) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(ascii + base);
+            const uint4 v0 = __ldg(src), v1 = __ldg(src + 1);
+            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t pos = base + 4 * i + k;
+                    v |= (uint32_t)(pos < total ? ascii[pos] : 'A') << (8 * k);   // past the end: code 0
+                }
+                x[i] = v;
+            }
+        }
+        uint32_t c[8], p0 = 0u, p1 = 0u;
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            c[i] = ((x[i] >> 1) ^ (x[i] >> 2)) & 0x03030303u;
+            const uint32_t sel = c[i] | (c[i] >> 12);
+            ok &= __byte_perm(0x54474341u, 0u, sel) == __byte_perm(x[i], 0u, 0x3120u);
+        }
+        if (!ok) {
+            int badk = -1;
+            uint32_t badb = 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                uint32_t cc = 0u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t b = (x[i] >> (8 * k)) & 0xFFu;
+                    uint32_t v = dna_code_of(b);
+                    if (v == 0xFFu) {
+                        if (badk < 0) {
+                            badk = 4 * i + k;
+                            badb = b;
+                        }
+                        v = 0u;
+                    }
+                    cc |= v << (8 * k);
+                }
+                c[i] = cc;
+            }
+            if (badk >= 0) record_error(err, kErrSymbol, base + badk, badb);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            p0 |= ((c[i] & 0x01010101u) * 0x10204080u) >> 28 << (4 * i);
+            p1 |= (((c[i] >> 1) & 0x01010101u) * 0x10204080u) >> 28 << (4 * i);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(codes + base);
+        dst[0] = make_uint4(c[0], c[1], c[2], c[3]);
+        dst[1] = make_uint4(c[4], c[5], c[6], c[7]);
+        planes[w * 2] = p0;
+        planes[w * 2 + 1] = p1;
+    }
+}
+
 template <int B>
 __global__ void __launch_bounds__(256) pack_kernel(const uint8_t *__restrict__ ascii, int64_t total,
                                                    uint8_t *__restrict__ codes,
@@ -240,8 +322,7 @@ msa_status msa_pack(msa_ctx *ctx, const msa_seqset *s, void *stream) {
     if (blocks > ctx->sm_count * 16) blocks = ctx->sm_count * 16;
     if (blocks < 1) blocks = 1;
     if (s->alphabet == MSA_DNA)
-        pack_kernel<2><<<(int)blocks, 256, 0, st>>>(s->ascii, s->total, s->codes, s->planes, nwords,
-                                                     s->alphabet, ctx->dev_err);
+        pack_dna_kernel<<<(int)blocks, 256, 0, st>>>(s->ascii, s->total, s->codes, s->planes, nwords, ctx->dev_err);
     else
         pack_kernel<5><<<(int)blocks, 256, 0, st>>>(s->ascii, s->total, s->codes, s->planes, nwords,
                                                      s->alphabet, ctx->dev_err);

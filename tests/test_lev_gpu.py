@@ -103,11 +103,39 @@ def test_bad_index_reports_edata(ctx):
     ctx.check()    # cleared
 
 
-def test_bad_symbol_reports_edata(ctx):
-    ds = synth.SeqSet.from_list([b"ACGT", b"ACNT"], "dna")
-    api.upload_and_pack(ctx, ds)
+@pytest.mark.parametrize("total", [1, 31, 32, 33, 4096 + 17, 100_003])
+def test_pack_codes_and_planes(ctx, total):
+    """Packed loader: byte codes (A0 C1 G2 T3) and the bit planes (plane p,
+    bit k of word w = bit p of the code at 32 w + k), from their definition."""
+    rng = np.random.default_rng(total)
+    arena = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=total)
+    offs = np.array([0, total // 3, total], np.int64)
+    seqs = api.DeviceSeqs.from_host(arena, offs, "dna")
+    api.pack(ctx, seqs)
+    ctx.check()
+    code = np.searchsorted(np.frombuffer(b"ACGT", np.uint8), arena)
+    np.testing.assert_array_equal(seqs.codes.cpu().numpy()[:total], code)
+    nw = (total + 31) // 32
+    planes = seqs.planes.cpu().numpy().view(np.uint32)[: 2 * nw].reshape(nw, 2)
+    padded = np.zeros(nw * 32, np.int64)
+    padded[:total] = code
+    bits = padded.reshape(nw, 32)
+    for p in (0, 1):
+        ref = ((bits >> p) & 1).astype(np.uint64) << np.arange(32, dtype=np.uint64)
+        np.testing.assert_array_equal(planes[:, p], ref.sum(1).astype(np.uint32))
+
+
+@pytest.mark.parametrize("rows", [[b"ACGT", b"ACNT"], [b"ACGT" * 20, b"ACGTACGTAC" * 3 + b"GGNAxA" + b"T" * 40]])
+def test_bad_symbol_reports_edata(ctx, rows):
+    ds = synth.SeqSet.from_list(rows, "dna")
+    seqs = api.upload_and_pack(ctx, ds)
     with pytest.raises(api.MsaError, match="outside the alphabet"):
         ctx.check()
+    # the valid residues keep their codes, the bad ones get code 0
+    code = np.array([b"ACGT".find(bytes([c])) for c in ds.arena], np.int64)
+    got = seqs.codes.cpu().numpy()[: len(ds.arena)].astype(np.int64)
+    np.testing.assert_array_equal(got[code >= 0], code[code >= 0])
+    assert np.all(got[code < 0] == 0)
 
 
 def test_tree_dna_full_size_sampled(ctx):
