@@ -21,6 +21,8 @@ computes the plain definition of what the GPU path computes:
 * :func:`partition` -- Alg. 1 ``Partition`` with the readings listed in the
   design notes (medoid sample rule, tie-breaks).
 * :func:`merge_tree` -- the post-order merge of section "Merging".
+* :func:`msa_metrics` -- the alignment quality metrics of section
+  "Evaluation": percentage of gaps, p-score, distance distortion.
 
 Functions that no independent fact pins say "parity unpinned" in their
 docstring.
@@ -500,3 +502,46 @@ def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1):
         msa[k] = ([bytes(r) for r in newL] + [bytes(r) for r in newR], ordL + ordR)
     rows, order = msa[0]
     return rows, order, merges
+
+
+# ---------------------------------------------------------------------------
+# alignment quality (section "Evaluation")
+# ---------------------------------------------------------------------------
+
+def msa_metrics(rows, seqs, gap: int = ord("-")):
+    """The three metrics of section "Evaluation" over aligned ``rows`` (equal
+    length byte strings) whose unaligned sequences are ``seqs``:
+
+    * percentage of gaps: per row, gap bytes / row length, averaged over the
+      rows, x 100;
+    * p-score: over every unordered pair of rows and every column where
+      neither row has a gap, the share of columns whose bytes differ, x 100
+      (one ratio over all such pairs of units);
+    * distance distortion: over every unordered pair of rows, the Hamming
+      distance of the aligned rows (columns whose bytes differ; a gap-gap
+      column is equal) divided by the Levenshtein distance of the unaligned
+      sequences, averaged over the pairs.
+
+    Returns ``(pct_gaps, p_score, distortion, counts)`` with the integer
+    totals behind them.  Plain loops over pairs and columns.
+    """
+    R = len(rows)
+    W = len(rows[0]) if R else 0
+    M = np.frombuffer(b"".join(bytes(r) for r in rows), np.uint8).reshape(R, W) if R else np.zeros((0, 0), np.uint8)
+    gaps = int((M == gap).sum())
+    pct = 100.0 * float(np.mean((M == gap).sum(1) / W)) if R and W else 0.0
+    compared = mismatched = 0
+    ratio_sum = 0.0
+    pairs = 0
+    for i in range(R):
+        for j in range(i + 1, R):
+            a, b = M[i], M[j]
+            both = (a != gap) & (b != gap)
+            compared += int(both.sum())
+            mismatched += int((both & (a != b)).sum())
+            h = int((a != b).sum())
+            ratio_sum += h / lev(seqs[i], seqs[j])
+            pairs += 1
+    p = 100.0 * mismatched / compared if compared else 0.0
+    dist = ratio_sum / pairs if pairs else 0.0
+    return pct, p, dist, dict(gaps=gaps, compared=compared, mismatched=mismatched, pairs=pairs)

@@ -324,3 +324,56 @@ def test_adam_first_step_closed_form():
     v = {"w": np.zeros(3)}
     out, _, _ = oracle.adam_step(p, g, m, v, t=1, lr=0.01)
     np.testing.assert_allclose(out["w"], -0.01 * g["w"] / (np.abs(g["w"]) + 1e-8))
+
+
+# ---------------------------------------------------------------------------
+# alignment quality metrics (section "Evaluation")
+# ---------------------------------------------------------------------------
+
+def test_msa_metrics_hand_example():
+    # rows AC-T / ACGT / A--T of ACT, ACGT, AT:
+    # gaps 1, 0, 2 of 4 per row -> mean 25%;
+    # compared columns (no gap in either row): pair 01 cols 0,1,3; pair 02 cols 0,3;
+    # pair 12 cols 0,3 -> 7 columns, all equal -> p-score 0;
+    # Hamming 1, 1, 2 against Levenshtein 1, 1, 2 -> distortion 1.
+    rows = [b"AC-T", b"ACGT", b"A--T"]
+    seqs = [b"ACT", b"ACGT", b"AT"]
+    pct, p, dist, n = oracle.msa_metrics(rows, seqs)
+    assert pct == pytest.approx(25.0) and p == 0.0 and dist == pytest.approx(1.0)
+    assert n == dict(gaps=3, compared=7, mismatched=0, pairs=3)
+
+
+def test_msa_metrics_mismatch_and_stretch():
+    # A-CT / AG-T: the only compared columns are 0 and 3 (both equal);
+    # Hamming 2 (columns 1, 2) against f(ACT, AGT) = 1 -> distortion 2.
+    pct, p, dist, n = oracle.msa_metrics([b"A-CT", b"AG-T"], [b"ACT", b"AGT"])
+    assert pct == pytest.approx(25.0) and p == 0.0 and dist == pytest.approx(2.0)
+    # ACGT / AGGA: 4 compared columns, 2 differ -> p-score 50; Hamming 2 = f -> 1
+    pct, p, dist, n = oracle.msa_metrics([b"ACGT", b"AGGA"], [b"ACGT", b"AGGA"])
+    assert pct == 0.0 and p == pytest.approx(50.0) and dist == pytest.approx(1.0)
+    assert n["compared"] == 4 and n["mismatched"] == 2
+
+
+def test_msa_metrics_distortion_at_least_one():
+    # an MSA restricted to two rows is an alignment of the two sequences, so
+    # its Hamming distance (gap-gap columns dropped) is at least their
+    # Levenshtein distance; a pairwise optimal alignment gives exactly 1
+    rng = np.random.default_rng(20)
+    seqs = [_rand_dna(rng, int(rng.integers(5, 30))) for _ in range(6)]
+    a, b = seqs[0], seqs[1]
+    score, ops = oracle.nw(a, b)
+    ra, rb = bytearray(), bytearray()
+    i = j = 0
+    for op in ops:
+        if op in b"MX":
+            ra.append(a[i]); rb.append(b[j]); i += 1; j += 1
+        elif op == ord("D"):
+            ra.append(a[i]); rb.append(ord("-")); i += 1
+        else:
+            ra.append(ord("-")); rb.append(b[j]); j += 1
+    _, _, dist, _ = oracle.msa_metrics([bytes(ra), bytes(rb)], [a, b])
+    assert dist == pytest.approx(1.0)
+    # a poor alignment of the same pair: everything against gaps
+    rows = [a + b"-" * len(b), b"-" * len(a) + b]
+    _, _, dist, _ = oracle.msa_metrics(rows, [a, b])
+    assert dist == pytest.approx((len(a) + len(b)) / oracle.lev(a, b))
