@@ -294,6 +294,11 @@ def clam_bench(ctx, args):
     ctx.prof_enable(False)
     rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
     ctx.check()
+    # alignment quality on a seeded 10,000-row sample (section "Evaluation")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    met = api.msa_metrics(ctx, sq, tree, rows, sample=min(10000, ds.n), seed=0)
+    t_met = time.perf_counter() - t0
     import oracle
     order = tree.order.cpu().numpy()
     rng = np.random.default_rng(0)
@@ -318,6 +323,8 @@ def clam_bench(ctx, args):
     return dict(workload=f"gg16s_dna_{ds.n}_len1400-1600", n_seqs=ds.n, partition_s=t_part, merge_s=t_merge,
                 partition_learned_band_s=t_part_b, learned_band_speedup=t_part / t_part_b,
                 learned_band_gamma=gamma, learned_band_same_tree=same_tree,
+                quality=dict(sample_rows=met["rows"], pct_gaps=met["pct_gaps"], p_score=met["p_score"],
+                             distortion=met["distortion"], pairs=met["pairs"], seconds=t_met),
                 partition_dp_ms=part_dp_ms, merge_dp_ms=merge_dp_ms, launches=part_launches + merge_launches,
                 tree_depth=int(depth.max()), msa_width=int(width[0]), nw_cells=nw_cells,
                 nw_gcups=nw_cells / (merge_dp_ms / 1e3) / 1e9 if merge_dp_ms else None,

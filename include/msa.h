@@ -318,6 +318,27 @@ msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *orde
 msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,
                         uint8_t *rows, void *stream);
 
+/* ---- alignment quality (section "Evaluation") ----------------------------- */
+/*
+ * The three metrics of section "Evaluation" over S sampled rows of an MSA
+ * (the paper uses a random sample of 10,000): rows is device u8 [R][W]
+ * (msa_msa_rows), sample_rows (device int32 [S]) the rows to use and
+ * sample_seqs (device int32 [S]) the index in s of each one's sequence.
+ *   out3[0] percentage of gaps: per row, gap bytes / W, averaged, x 100;
+ *   out3[1] p-score: over all pairs of sampled rows and all columns where
+ *           neither has a gap, the share of columns whose bytes differ, x 100;
+ *   out3[2] distance distortion: over all pairs of sampled rows, Hamming
+ *           distance of the aligned rows (bytes differ; gap-gap is equal) /
+ *           Levenshtein distance of their sequences, averaged (pairs of
+ *           identical sequences have no ratio and are left out).
+ * counts4 (host, optional): gap bytes, compared unit pairs, mismatched unit
+ * pairs, pairs in the distortion mean.  Synchronous (host outputs).  Needs
+ * workspace for S (S - 1) / 2 int32 distances plus one distance batch.
+ */
+msa_status msa_msa_metrics(msa_ctx *ctx, const msa_seqset *s, const uint8_t *rows, int32_t R, int32_t W,
+                           const int32_t *sample_rows, const int32_t *sample_seqs, int32_t S, uint8_t gap,
+                           double *out3, int64_t *counts4, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

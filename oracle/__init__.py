@@ -520,7 +520,8 @@ def msa_metrics(rows, seqs, gap: int = ord("-")):
     * distance distortion: over every unordered pair of rows, the Hamming
       distance of the aligned rows (columns whose bytes differ; a gap-gap
       column is equal) divided by the Levenshtein distance of the unaligned
-      sequences, averaged over the pairs.
+      sequences, averaged over the pairs (pairs of identical sequences, whose
+      ratio is undefined, are left out; the paper's inputs are de-duplicated).
 
     Returns ``(pct_gaps, p_score, distortion, counts)`` with the integer
     totals behind them.  Plain loops over pairs and columns.
@@ -540,7 +541,10 @@ def msa_metrics(rows, seqs, gap: int = ord("-")):
             compared += int(both.sum())
             mismatched += int((both & (a != b)).sum())
             h = int((a != b).sum())
-            ratio_sum += h / lev(seqs[i], seqs[j])
+            f = lev(seqs[i], seqs[j])
+            if f == 0:               # identical sequences have no ratio: left out
+                continue
+            ratio_sum += h / f
             pairs += 1
     p = 100.0 * mismatched / compared if compared else 0.0
     dist = ratio_sum / pairs if pairs else 0.0

@@ -399,3 +399,24 @@ def msa_rows(ctx: Context, seqs: DeviceSeqs, tree: Tree, pos: torch.Tensor, W: i
     ctx.raise_if(_lib.lib().msa_msa_rows(ctx.handle, ctypes.byref(seqs.c), _ptr(tree.order), _ptr(pos), int(W),
                                          _ptr(rows), _stream(stream)))
     return rows[: seqs.n, :W]
+
+
+def msa_metrics(ctx: Context, seqs: DeviceSeqs, tree: Tree, rows: torch.Tensor, sample: int | None = 10000,
+                seed: int = 0, gap: int = ord("-"), stream=None) -> dict:
+    """Alignment quality (section "Evaluation"; msa_msa_metrics) over a seeded
+    random sample of ``sample`` rows (all rows when None or larger)."""
+    R, W = rows.shape
+    if sample is None or sample >= R:
+        pick = np.arange(R)
+    else:
+        pick = np.sort(np.random.default_rng(seed).choice(R, size=sample, replace=False))
+    order = tree.order.cpu().numpy()
+    srows = torch.from_numpy(pick.astype(np.int32)).cuda()
+    sseqs = torch.from_numpy(order[pick].astype(np.int32)).cuda()
+    out = np.zeros(3, np.float64)
+    cnt = np.zeros(4, np.int64)
+    ctx.raise_if(_lib.lib().msa_msa_metrics(ctx.handle, ctypes.byref(seqs.c), _ptr(rows.contiguous()), R, W,
+                                            _ptr(srows), _ptr(sseqs), len(pick), gap, _np_ptr(out), _np_ptr(cnt),
+                                            _stream(stream)))
+    return dict(pct_gaps=float(out[0]), p_score=float(out[1]), distortion=float(out[2]), rows=int(len(pick)),
+                gaps=int(cnt[0]), compared=int(cnt[1]), mismatched=int(cnt[2]), pairs=int(cnt[3]), sample=pick)

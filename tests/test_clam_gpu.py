@@ -126,3 +126,39 @@ def test_banded_partition_rejects_protein(ctx):
     prof = torch.zeros((members.n, 256), dtype=torch.int16, device="cuda")
     with pytest.raises(api.MsaError):
         api.clam_partition(ctx, sq, band=model, prof=prof)
+
+
+def _metrics_check(ctx, ds, sample):
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
+    ctx.check()
+    got = api.msa_metrics(ctx, sq, tree, rows, sample=sample, seed=3)
+    order = tree.order.cpu().numpy()
+    host_rows = rows.cpu().numpy()
+    pick = got["sample"]
+    seqs = ds.seqs()
+    pct, p, dist, n = oracle.msa_metrics([host_rows[r].tobytes() for r in pick], [seqs[order[r]] for r in pick])
+    assert (got["gaps"], got["compared"], got["mismatched"], got["pairs"]) == \
+        (n["gaps"], n["compared"], n["mismatched"], n["pairs"])
+    assert got["pct_gaps"] == pytest.approx(pct, rel=1e-12, abs=1e-12)
+    assert got["p_score"] == pytest.approx(p, rel=1e-12, abs=1e-12)
+    assert got["distortion"] == pytest.approx(dist, rel=1e-12)
+    assert got["distortion"] >= 1.0
+    return got
+
+
+def test_msa_metrics_small_all_rows(ctx):
+    _metrics_check(ctx, synth.small_dna(seed=1), None)
+
+
+def test_msa_metrics_16s_sample(ctx):
+    """A seeded 130-row sample of a 1,500-sequence 16S-like MSA (two 64-row
+    tiles and a ragged one in the Hamming kernel)."""
+    _metrics_check(ctx, synth.gg16s_dna(seed=5, n=1500), 130)
+
+
+def test_msa_metrics_protein(ctx):
+    members, _ = synth.protein_families(seed=3, n_fam=3, per_fam=30)
+    _metrics_check(ctx, members, None)
