@@ -11,8 +11,10 @@ computes the plain definition of what the GPU path computes:
 * :func:`nw` / :func:`nw_pairs` -- Needleman-Wunsch (section "Merging",
   step 2) as a minimum-cost DP with a flat cost model and the traceback
   preference diagonal > up > left (``oracle.c``).
+* :func:`nw_affine` -- the same with affine gap costs (Gotoh), the cost model
+  of the paper's experiments (flat substitution costs here).
 * :func:`brute_alignments` -- every alignment of two short strings, used to
-  pin the two functions above.
+  pin the functions above.
 * :func:`kmer_counts`, :func:`pair_feature` -- 4-mer count profiles and the
   pair feature of the learned band proposer (no counterpart in the paper; the
   definition is this project's).
@@ -68,6 +70,10 @@ def _load():
             L.oracle_nw.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     i32p, u8p, i64p]
+            L.oracle_nw_affine.restype = ctypes.c_int32
+            L.oracle_nw_affine.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           i32p, u8p, i64p]
             L.oracle_lev_pairs.restype = ctypes.c_int32
             L.oracle_lev_pairs.argtypes = [u8p, i64p, i32p, ctypes.c_int64, i32p, ctypes.c_int32]
             L.oracle_nw_pairs.restype = ctypes.c_int32
@@ -122,6 +128,49 @@ def nw(a, b, match: int = 0, mismatch: int = 1, gap: int = 1):
     if rc != 0:
         raise MemoryError("oracle_nw: matrix allocation failed")
     return int(score.value), bytes(ops[: L.value])
+
+
+def nw_affine(a, b, match: int = 0, mismatch: int = 1, gap_open: int = 10, gap_ext: int = 1):
+    """Needleman-Wunsch with affine gap costs (the paper's merges use affine
+    gaps, open = 10 x extend; section "Implementation"): a run of L gap
+    positions costs ``gap_open + L * gap_ext``.  Gotoh's three matrices and
+    the traceback of ``oracle.c`` (diagonal, then up, then left; a gap run
+    closes where opening it attains, else it extends), which with
+    ``gap_open = 0`` is :func:`nw`'s traceback.  Returns ``(score, ops)``.
+    """
+    A, B = _as_u8(a), _as_u8(b)
+    ops = np.zeros(len(A) + len(B) + 1, dtype=np.uint8)
+    score = ctypes.c_int32(0)
+    L = ctypes.c_int64(0)
+    rc = _load().oracle_nw_affine(_ptr(A, ctypes.c_uint8), len(A), _ptr(B, ctypes.c_uint8), len(B),
+                                  match, mismatch, gap_open, gap_ext, ctypes.byref(score),
+                                  _ptr(ops, ctypes.c_uint8), ctypes.byref(L))
+    if rc != 0:
+        raise MemoryError("oracle_nw_affine: allocation failed")
+    return int(score.value), ops[:L.value].tobytes()
+
+
+def rescore_affine(a, b, ops, match=0, mismatch=1, gap_open=10, gap_ext=1):
+    """Cost of an alignment under affine gaps: substitutions plus, for every
+    maximal run of D (or of I) of length L, gap_open + L * gap_ext."""
+    a, b = bytes(a), bytes(b)
+    i = j = 0
+    cost = 0
+    prev = None
+    for op in bytes(ops):
+        if op in (ord("M"), ord("X")):
+            cost += match if a[i] == b[j] else mismatch
+            i += 1
+            j += 1
+        elif op == ord("D"):
+            cost += gap_ext + (gap_open if prev != op else 0)
+            i += 1
+        else:
+            cost += gap_ext + (gap_open if prev != op else 0)
+            j += 1
+        prev = op
+    assert i == len(a) and j == len(b)
+    return cost
 
 
 def lev_pairs(arena: np.ndarray, offs: np.ndarray, pairs: np.ndarray, nthreads: int | None = None) -> np.ndarray:

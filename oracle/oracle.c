@@ -27,6 +27,23 @@
  *                 'M' (diagonal, equal symbols), 'X' (diagonal, different
  *                 symbols), 'D' (up) and 'I' (left).
  *
+ *  oracle_nw_affine -- the same alignment with affine gap costs (Gotoh's
+ *                 three matrices): a run of L gap positions costs
+ *                 open + L * ext.  H[i][j] is the best cost of a_1..i against
+ *                 b_1..j, F[i][j] the best that ends with an up move, E[i][j]
+ *                 the best that ends with a left move:
+ *                   F[i][j] = min(F[i-1][j] + ext, H[i-1][j] + open + ext)
+ *                   E[i][j] = min(E[i][j-1] + ext, H[i][j-1] + open + ext)
+ *                   H[i][j] = min(H[i-1][j-1] + c(a_i, b_j), F[i][j], E[i][j])
+ *                 with H[0][0] = 0, H[i][0] = F[i][0] = open + i * ext,
+ *                 H[0][j] = E[0][j] = open + j * ext, E[i][0] = F[0][j] = inf.
+ *                 Traceback from (m, n) in state H: H takes the diagonal,
+ *                 then F, then E (the first that attains); in F every step
+ *                 emits 'D' and returns to H when opening the run there
+ *                 attains, else the run goes on; E likewise with 'I'.  With
+ *                 open = 0 this is the linear traceback exactly.  Row 0 forces
+ *                 'I', column 0 forces 'D'.
+ *
  *  oracle_lev_pairs / oracle_nw_pairs -- the same functions mapped over a
  *                 list of pairs, threads split the pair list only; each
  *                 pair's DP is the plain single-threaded one above.
@@ -56,6 +73,74 @@ int32_t oracle_lev(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n)
     int32_t d = D[m * cols + n];
     free(D);
     return d;
+}
+
+/* Returns 0 on success, -1 on allocation failure.  ops must hold m + n bytes. */
+int32_t oracle_nw_affine(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                         int32_t match, int32_t mismatch, int32_t open, int32_t ext,
+                         int32_t *score, uint8_t *ops, int64_t *ops_len)
+{
+    const int32_t INF = 1 << 29;
+    const int64_t cols = n + 1;
+    const size_t cells = (size_t)(m + 1) * (size_t)cols;
+    int32_t *H = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *E = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *F = (int32_t *)malloc(cells * sizeof(int32_t));
+    if (!H || !E || !F) {
+        free(H); free(E); free(F);
+        return -1;
+    }
+    H[0] = 0;
+    E[0] = F[0] = INF;
+    for (int64_t j = 1; j <= n; ++j) {
+        H[j] = E[j] = open + (int32_t)j * ext;
+        F[j] = INF;
+    }
+    for (int64_t i = 1; i <= m; ++i) {
+        H[i * cols] = F[i * cols] = open + (int32_t)i * ext;
+        E[i * cols] = INF;
+        for (int64_t j = 1; j <= n; ++j) {
+            const int64_t x = i * cols + j, up = (i - 1) * cols + j, lf = i * cols + j - 1;
+            F[x] = min2(F[up] + ext, H[up] + open + ext);
+            E[x] = min2(E[lf] + ext, H[lf] + open + ext);
+            const int32_t c = (a[i - 1] == b[j - 1]) ? match : mismatch;
+            H[x] = min2(H[(i - 1) * cols + j - 1] + c, min2(F[x], E[x]));
+        }
+    }
+    *score = H[m * cols + n];
+
+    int64_t i = m, j = n, k = 0;
+    int state = 0;                       /* 0: H, 1: F, 2: E */
+    while (i > 0 || j > 0) {
+        if (i == 0) { ops[k++] = 'I'; --j; continue; }
+        if (j == 0) { ops[k++] = 'D'; --i; continue; }
+        const int64_t x = i * cols + j;
+        if (state == 0) {
+            const int32_t c = (a[i - 1] == b[j - 1]) ? match : mismatch;
+            if (H[x] == H[(i - 1) * cols + j - 1] + c) {
+                ops[k++] = (a[i - 1] == b[j - 1]) ? 'M' : 'X';
+                --i; --j;
+            } else if (H[x] == F[x]) {
+                state = 1;
+            } else {
+                state = 2;
+            }
+        } else if (state == 1) {
+            ops[k++] = 'D';
+            if (F[x] == H[(i - 1) * cols + j] + open + ext) state = 0;
+            --i;
+        } else {
+            ops[k++] = 'I';
+            if (E[x] == H[i * cols + j - 1] + open + ext) state = 0;
+            --j;
+        }
+    }
+    for (int64_t p = 0, q = k - 1; p < q; ++p, --q) {
+        uint8_t t = ops[p]; ops[p] = ops[q]; ops[q] = t;
+    }
+    *ops_len = k;
+    free(H); free(E); free(F);
+    return 0;
 }
 
 /* Returns 0 on success, -1 on allocation failure.  ops must hold m + n bytes. */

@@ -377,3 +377,38 @@ def test_msa_metrics_distortion_at_least_one():
     rows = [a + b"-" * len(b), b"-" * len(a) + b]
     _, _, dist, _ = oracle.msa_metrics(rows, [a, b])
     assert dist == pytest.approx((len(a) + len(b)) / oracle.lev(a, b))
+
+
+# ---------------------------------------------------------------------------
+# affine gaps (Gotoh)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("costs", [(0, 1, 10, 1), (0, 3, 2, 1), (-1, 2, 3, 2), (0, 1, 0, 1)])
+def test_nw_affine_bruteforce(costs):
+    """Minimum affine cost over every alignment (rescored run by run) equals
+    the DP score, and the DP's own script rescores to it."""
+    rng = np.random.default_rng(sum(costs) + 50)
+    for _ in range(60):
+        a = rng.choice(list(b"ACG-"), size=int(rng.integers(0, 7))).astype(np.uint8).tobytes()
+        b = rng.choice(list(b"ACG-"), size=int(rng.integers(0, 7))).astype(np.uint8).tobytes()
+        best = min(oracle.rescore_affine(a, b, ops, *costs) for ops in oracle.brute_alignments(a, b))
+        score, ops = oracle.nw_affine(a, b, *costs)
+        assert score == best
+        assert oracle.rescore_affine(a, b, ops, *costs) == score
+
+
+def test_nw_affine_reduces_to_linear():
+    # with open = 0 a run of L gaps costs L * ext: the linear model, same script
+    rng = np.random.default_rng(51)
+    for _ in range(40):
+        a, b = _rand_dna(rng, int(rng.integers(0, 40))), _rand_dna(rng, int(rng.integers(0, 40)))
+        assert oracle.nw_affine(a, b, 0, 1, 0, 1) == oracle.nw(a, b, 0, 1, 1)
+
+
+def test_nw_affine_closed_forms():
+    # one substitution (1) is cheaper than a deletion plus an insertion (2 x 11)
+    assert oracle.nw_affine(b"ACGTACGT", b"ACGAACGT", 0, 1, 10, 1) == (1, b"MMMXMMMM")
+    # one gap run of 3 costs open + 3 ext = 13, less than 3 substitutions at 5
+    assert oracle.nw_affine(b"AAACCCGGG", b"AAAGGG", 0, 5, 10, 1) == (13, b"MMMDDDMMM")
+    assert oracle.nw_affine(b"ACGT", b"AGGT", 0, 1, 10, 1) == (1, b"MXMM")
+    assert oracle.nw_affine(b"", b"ACG", 0, 1, 10, 1) == (13, b"III")
