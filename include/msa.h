@@ -257,6 +257,21 @@ msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t 
                               void *stream);
 /* Workspace bytes msa_nw_align_batch needs to run `warps` pairs at once. */
 int64_t msa_nw_workspace_bytes(int32_t max_len, int32_t warps);
+/*
+ * The same alignment with affine gap costs (Gotoh; the paper's merges use
+ * affine gaps with open = 10 x extend, section "Implementation"): a run of L
+ * gap positions costs gap_open + L * gap_ext (gap_open >= 0, gap_ext >= 1);
+ * substitutions cost match / mismatch.  Traceback from (m, n): diagonal, then
+ * up, then left (the first that attains), and a gap run closes where opening
+ * it attains, else it extends; with gap_open = 0 the result is exactly
+ * msa_nw_align_batch's with gap = gap_ext.  Arguments and outputs as in
+ * msa_nw_align_batch; per-warp scratch is about twice as large.
+ */
+msa_status msa_nw_align_batch_affine(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                     int64_t total, int32_t max_len, const int32_t *pairs, int64_t P,
+                                     int32_t match, int32_t mismatch, int32_t gap_open, int32_t gap_ext,
+                                     int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off,
+                                     int32_t *ops_len_out, void *stream);
 
 /* ---- A11: guide tree by Alg. 1 (Partition) ------------------------------ */
 /*

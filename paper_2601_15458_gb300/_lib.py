@@ -46,6 +46,9 @@ SIGNATURES = {
     "msa_nw_align_batch": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p, c_int64,
                                      c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "msa_nw_workspace_bytes": (c_int64, [c_int32, c_int32]),
+    "msa_nw_align_batch_affine": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p,
+                                            c_int64, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p]),
     "msa_lev_banded_batch": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_int64, c_void_p, c_void_p,
                                        c_void_p, c_void_p]),
     "msa_lev_banded_workspace_bytes": (c_int64, [c_int64, c_int32]),

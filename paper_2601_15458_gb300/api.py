@@ -197,11 +197,13 @@ class ByteSeqs:
 
 
 def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_off: torch.Tensor | None = None,
-                   stream=None):
+                   stream=None, gap_open: int | None = None):
     """A5/A6: NW score, edit script (forward order, bytes M/X/D/I) per pair.
 
     Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64, ops_len[P] int32)``.
     ``seqs`` is a :class:`ByteSeqs` or a packed :class:`DeviceSeqs` (its byte codes).
+    With ``gap_open`` the gap costs are affine: a run of L gaps costs
+    ``gap_open + L * gap`` (msa_nw_align_batch_affine).
     """
     if isinstance(seqs, DeviceSeqs):
         seqs = ByteSeqs.from_device_seqs(seqs)
@@ -217,9 +219,14 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
     ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
     score = torch.empty(P, dtype=torch.int32, device=dev)
     ops_len = torch.empty(P, dtype=torch.int32, device=dev)
-    ctx.raise_if(_lib.lib().msa_nw_align_batch(ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total,
-                                               seqs.max_len, _ptr(pairs), P, match, mismatch, gap, _ptr(score),
-                                               _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    if gap_open is None:
+        ctx.raise_if(_lib.lib().msa_nw_align_batch(ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total,
+                                                   seqs.max_len, _ptr(pairs), P, match, mismatch, gap, _ptr(score),
+                                                   _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    else:
+        ctx.raise_if(_lib.lib().msa_nw_align_batch_affine(
+            ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, match,
+            mismatch, gap_open, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
     return score, ops, ops_off, ops_len
 
 

@@ -7,6 +7,7 @@
     python -m paper_2601_15458_gb300.cases pack    # packed loader, 1.1 GB arena
     python -m paper_2601_15458_gb300.cases mlp     # band network forward + one training step
     python -m paper_2601_15458_gb300.cases protein # 10,000 x 100 centre distances, 9,999 NW with traceback
+    python -m paper_2601_15458_gb300.cases nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
 
 Each case runs its call a few times (the first warms up) and prints one
 line with the call's device time.
@@ -50,6 +51,14 @@ def case_nw(ctx):
     pairs = torch.from_numpy(np.stack([np.arange(0, 2000, 2), np.arange(1, 2000, 2)], 1).astype(np.int32)).cuda()
     pairs = torch.cat([pairs, pairs.flip(1)])
     return _time(lambda: api.nw_align_batch(ctx, sq, pairs))
+
+
+def case_nw_affine(ctx):
+    ds = synth.tree_dna(seed=2, n=2000)
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = torch.from_numpy(np.stack([np.arange(0, 2000, 2), np.arange(1, 2000, 2)], 1).astype(np.int32)).cuda()
+    pairs = torch.cat([pairs, pairs.flip(1)])
+    return _time(lambda: api.nw_align_batch(ctx, sq, pairs, 0, 1, 1, gap_open=10))
 
 
 def case_band(ctx):
@@ -112,7 +121,7 @@ def case_protein(ctx):
 
 
 CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
-             protein=case_protein)
+             protein=case_protein, nw_affine=case_nw_affine)
 
 
 def main(argv):

@@ -225,6 +225,246 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Affine gap costs (Gotoh): a run of L gap positions costs open + L * ext.
+// Per cell H (best), F (best ending with an up move) and E (best ending with
+// a left move):
+//   F[i][j] = min(F[i-1][j] + ext, H[i-1][j] + open + ext)
+//   E[i][j] = min(E[i][j-1] + ext, H[i][j-1] + open + ext)
+//   H[i][j] = min(H[i-1][j-1] + c(a_i, b_j), F[i][j], E[i][j])
+// with H[i][0] = F[i][0] = open + i ext, H[0][j] = E[0][j] = open + j ext.
+// Same layout as nw_kernel (warp per pair, 16 rows per lane, skew across
+// lanes); H and F of the row above come from the lane above, E and H of the
+// previous column stay in registers.  Four bits per cell: H's move (0
+// diagonal, 1 F, 2 E, preferred in that order), whether F opened from H and
+// whether E opened from H (opening preferred when it attains); the traceback
+// runs the three-state walk from (m, n) in state H.
+// ---------------------------------------------------------------------------
+constexpr int32_t kNwInf = 1 << 29;
+
+__global__ void __launch_bounds__(kNwWarps * 32) nw_affine_kernel(NwArgs a, int32_t open, int32_t ext) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kNwWarps + (threadIdx.x >> 5);
+    char *slab = a.slabs + (int64_t)gw * a.slab_bytes;
+    int32_t *bH = reinterpret_cast<int32_t *>(slab);
+    int32_t *bF = bH + (a.max_len + 1);
+    uint2 *tb = reinterpret_cast<uint2 *>(slab + (((int64_t)a.max_len + 1) * 8 + 255) / 256 * 256);
+    const int match = a.match, mismatch = a.mismatch;
+    const int oe = open + ext;
+
+    while (true) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(a.counter, 1);
+        p = __shfl_sync(FULL, p, 0);
+        if (p >= a.P) break;
+        const int x = a.pairs[2 * p], y = a.pairs[2 * p + 1];
+        bool ok = x >= 0 && x < a.n_seqs && y >= 0 && y < a.n_seqs;
+        int64_t xa = 0, xb = 0, ya = 0, yb = 0;
+        if (ok) {
+            xa = a.offs[x], xb = a.offs[x + 1], ya = a.offs[y], yb = a.offs[y + 1];
+            ok = xa >= 0 && xa <= xb && xb <= a.total && ya >= 0 && ya <= yb && yb <= a.total;
+        }
+        if (!ok) {
+            if (lane == 0) record_error(a.err, kErrIndex, p, x);
+            continue;
+        }
+        const int m = (int)(xb - xa), n = (int)(yb - ya);
+        const uint8_t *A = a.codes + xa;
+        const uint8_t *Bq = a.codes + ya;
+        const int64_t o0 = a.ops_off[p];
+        if (a.ops_off[p + 1] - o0 < (int64_t)m + n) {
+            if (lane == 0) record_error(a.err, kErrCapacity, p, m + n);
+            continue;
+        }
+        if (m > a.max_len || n > a.max_len) {
+            if (lane == 0) record_error(a.err, kErrLength, p, max(m, n));
+            continue;
+        }
+        uint8_t *ops = a.ops + o0;
+        if (m == 0 || n == 0) {
+            for (int k = lane; k < m + n; k += 32) ops[k] = m == 0 ? 'I' : 'D';
+            if (lane == 0) {
+                a.score[p] = m + n > 0 ? open + (m + n) * ext : 0;
+                a.ops_len[p] = m + n;
+            }
+            continue;
+        }
+
+        // ---- fill -------------------------------------------------------
+        // row 0: H = E = open + j ext (H[0][0] = 0), F = inf
+        for (int j = lane; j <= n; j += 32) {
+            bH[j] = j == 0 ? 0 : open + j * ext;
+            bF[j] = kNwInf;
+        }
+        __syncwarp();
+        const int ntiles = (m + kNwTile - 1) / kNwTile;
+        int32_t H[kNwR], E[kNwR];
+        for (int t = 0; t < ntiles; ++t) {
+            const int i_first = t * kNwTile + lane * kNwR + 1;
+            int ac[kNwR];
+#pragma unroll
+            for (int r = 0; r < kNwR; ++r) {
+                const int i = i_first + r;
+                ac[r] = i <= m ? (int)A[i - 1] : -1;
+                H[r] = open + i * ext;                      // column 0
+                E[r] = kNwInf;
+            }
+            int prev_top = i_first - 1 == 0 ? 0 : open + (i_first - 1) * ext;   // H[i_first-1][0]
+            int lastH = H[kNwR - 1], lastF = kNwInf;
+            uint2 *tbl = tb + ((int64_t)t * 32 + lane) * n;
+            for (int s = 1; s <= n + 31; ++s) {
+                const int upH_in = __shfl_up_sync(FULL, lastH, 1);
+                const int upF_in = __shfl_up_sync(FULL, lastF, 1);
+                const int j = s - lane;
+                if (j >= 1 && j <= n) {
+                    const int topH = lane == 0 ? bH[j] : upH_in;
+                    const int topF = lane == 0 ? bF[j] : upF_in;
+                    const int bj = Bq[j - 1];
+                    int diag = prev_top, upH = topH, upF = topF;
+                    uint32_t c0 = 0u, c1 = 0u;
+#pragma unroll
+                    for (int r = 0; r < kNwR; ++r) {
+                        const int fx = upF + ext, fo = upH + oe;
+                        const int Fn = min(fx, fo);
+                        const int ex = E[r] + ext, eo = H[r] + oe;
+                        const int En = min(ex, eo);
+                        const int dg = diag + (ac[r] == bj ? match : mismatch);
+                        const int Hn = min(dg, min(Fn, En));
+                        const uint32_t hs = dg == Hn ? 0u : (Fn == Hn ? 1u : 2u);
+                        const uint32_t code = hs | ((uint32_t)(fo <= fx) << 2) | ((uint32_t)(eo <= ex) << 3);
+                        if (r < 8) c0 |= code << (4 * r);
+                        else c1 |= code << (4 * (r - 8));
+                        diag = H[r];
+                        H[r] = Hn;
+                        E[r] = En;
+                        upH = Hn;
+                        upF = Fn;
+                    }
+                    prev_top = topH;
+                    lastH = upH;
+                    lastF = upF;
+                    tbl[j - 1] = make_uint2(c0, c1);
+                    if (lane == 31) {
+                        bH[j] = lastH;
+                        bF[j] = lastF;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        {
+            const int lm = ((m - 1) % kNwTile) / kNwR, rm = (m - 1) % kNwR;
+            if (lane == lm) {
+                int v = 0;
+#pragma unroll
+                for (int r = 0; r < kNwR; ++r)
+                    if (r == rm) v = H[r];
+                a.score[p] = v;
+            }
+        }
+        __syncwarp();
+
+        // ---- traceback (lane 0): three-state walk, script written backwards
+        int L = 0;
+        if (lane == 0) {
+            int i = m, j = n, state = 0;
+            int64_t w = (int64_t)m + n - 1;
+            while (i > 0 && j > 0) {
+                const int t = (i - 1) / kNwTile, l = ((i - 1) % kNwTile) / kNwR, r = (i - 1) % kNwR;
+                const uint2 cw = tb[((int64_t)t * 32 + l) * n + (j - 1)];
+                const uint32_t c = ((r < 8 ? cw.x : cw.y) >> (4 * (r & 7))) & 15u;
+                if (state == 0) {
+                    const uint32_t hs = c & 3u;
+                    if (hs == 0u) {
+                        ops[w--] = A[i - 1] == Bq[j - 1] ? 'M' : 'X';
+                        --i;
+                        --j;
+                    } else {
+                        state = hs == 1u ? 1 : 2;
+                    }
+                } else if (state == 1) {
+                    ops[w--] = 'D';
+                    if (c & 4u) state = 0;
+                    --i;
+                } else {
+                    ops[w--] = 'I';
+                    if (c & 8u) state = 0;
+                    --j;
+                }
+            }
+            while (i > 0) {
+                ops[w--] = 'D';
+                --i;
+            }
+            while (j > 0) {
+                ops[w--] = 'I';
+                --j;
+            }
+            L = (int)((int64_t)m + n - 1 - w);
+            a.ops_len[p] = L;
+        }
+        L = __shfl_sync(FULL, L, 0);
+        __syncwarp();
+        const int shift = m + n - L;
+        if (shift > 0) {
+            for (int base = 0; base < L; base += 32) {
+                const int k = base + lane;
+                uint8_t v = 0;
+                if (k < L) v = ops[shift + k];
+                __syncwarp();
+                if (k < L) ops[k] = v;
+                __syncwarp();
+            }
+        }
+    }
+}
+
+int64_t nw_affine_slab_bytes(int max_len) {
+    const int64_t brow = (((int64_t)max_len + 1) * 8 + 255) / 256 * 256;
+    const int64_t tiles = (max_len + kNwTile - 1) / kNwTile;
+    const int64_t tbw = tiles * 32 * (int64_t)std::max(max_len, 1) * 8;
+    return brow + (tbw + 255) / 256 * 256;
+}
+
+msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                         int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t match,
+                         int32_t mismatch, int32_t open, int32_t ext, int32_t *score_out, uint8_t *ops_out,
+                         const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st) {
+    if (P < 0 || P >= (int64_t(1) << 31) || n_seqs < 0 || max_len < 0 || total < 0)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: negative or oversized count");
+    if (open < 0 || ext < 1)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: needs gap_open >= 0 and gap_ext >= 1");
+    if (P == 0) return MSA_OK;
+    if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: null pointer");
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_affine_kernel, kNwWarps * 32, 0);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "nw affine occupancy");
+        if (occ < 1) occ = 1;
+    }
+    int32_t *counter = ar.take<int32_t>(64);
+    const int64_t slab = nw_affine_slab_bytes(max_len);
+    const int64_t avail = counter ? ar.cap - ar.used : 0;
+    int64_t warps = std::min<int64_t>((int64_t)ctx->sm_count * occ * kNwWarps, avail / slab);
+    warps = std::min<int64_t>(warps, ((P + kNwWarps - 1) / kNwWarps) * kNwWarps);
+    warps = warps / kNwWarps * kNwWarps;
+    if (warps < kNwWarps)
+        return set_error(ctx, MSA_ENOMEM,
+                         "msa_nw_align_batch_affine: max_len %d needs %lld workspace bytes per warp group", max_len,
+                         (long long)(slab * kNwWarps + 256));
+    char *slabs = ar.take<char>(warps * slab);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
+    NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, 0, score_out, ops_out, ops_off,
+             ops_len_out, slabs, slab, max_len, counter, nullptr, nullptr, ctx->dev_err};
+    ProfScope prof(ctx, st);
+    nw_affine_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a, open, ext);
+    ++ctx->launches;
+    return cuda_check(ctx, cudaGetLastError(), "nw affine launch");
+}
+
 // Per-warp scratch, large enough for either kernel (the bit-parallel one for
 // the unit cost model, the plain DP for the rest); the two run one after the
 // other on the same slabs.
@@ -298,6 +538,16 @@ extern "C" {
 
 int64_t msa_nw_workspace_bytes(int32_t max_len, int32_t warps) {
     return 256 + (int64_t)warps * nw_slab_bytes(max_len);
+}
+
+msa_status msa_nw_align_batch_affine(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                     int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t match,
+                                     int32_t mismatch, int32_t gap_open, int32_t gap_ext, int32_t *score_out,
+                                     uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
+    if (!ctx) return MSA_EINVAL;
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    return nw_affine_run(ctx, ar, codes, offs, n_seqs, total, max_len, pairs, P, match, mismatch, gap_open, gap_ext,
+                         score_out, ops_out, ops_off, ops_len_out, (cudaStream_t)stream);
 }
 
 msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,

@@ -119,3 +119,61 @@ def test_capacity_error(ctx):
     api.nw_align_batch(ctx, seqs, np.array([[0, 1]], np.int32), ops_off=off)
     with pytest.raises(api.MsaError):
         ctx.check()
+
+
+
+# ---- affine gaps (Gotoh) -------------------------------------------------------
+
+def _check_affine(ctx, rows, pairs, costs):
+    match, mismatch, gap_open, gap_ext = costs
+    pairs = np.asarray(pairs, np.int32).reshape(-1, 2)
+    seqs = api.ByteSeqs.from_list(rows)
+    score, ops, off, ln = api.nw_align_batch(ctx, seqs, pairs, match, mismatch, gap_ext, gap_open=gap_open)
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    for p, (x, y) in enumerate(pairs):
+        rs, rops = oracle.nw_affine(rows[x], rows[y], *costs)
+        got = ops[off[p]:off[p] + ln[p]].tobytes()
+        assert score[p] == rs and got == rops, (p, len(rows[x]), len(rows[y]))
+        assert oracle.rescore_affine(rows[x], rows[y], got, *costs) == score[p]
+
+
+@pytest.mark.parametrize("costs", [(0, 1, 10, 1), (0, 3, 2, 1), (-1, 2, 3, 2), (0, 1, 0, 1)])
+def test_affine_tiny_against_oracle_and_bruteforce(ctx, costs):
+    rng = np.random.default_rng(sum(costs) + 60)
+    rows = [rng.choice(list(b"ACG-"), size=int(rng.integers(0, 7))).astype(np.uint8).tobytes() for _ in range(40)]
+    pairs = np.array([[i, (i * 7 + 3) % 40] for i in range(40)], np.int32)
+    _check_affine(ctx, rows, pairs, costs)
+    for x, y in pairs[:10]:
+        best = min(oracle.rescore_affine(rows[x], rows[y], o, *costs) for o in oracle.brute_alignments(rows[x], rows[y]))
+        assert oracle.nw_affine(rows[x], rows[y], *costs)[0] == best
+
+
+def test_affine_edge_lengths(ctx):
+    rng = np.random.default_rng(61)
+    lens = [0, 1, 15, 16, 17, 511, 512, 513, 1024, 1500]
+    rows = [rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes() for L in lens]
+    for L in lens:
+        a = bytearray(rows[lens.index(L)])
+        for k in range(0, L, 37):
+            a[k] = ord("-")
+        rows.append(bytes(a[: max(0, L - L // 5)]))
+    n = len(lens)
+    pairs = [[i, n + j] for i in range(n) for j in range(n) if (i + j) % 2 == 0]
+    _check_affine(ctx, rows, pairs, (0, 1, 10, 1))
+
+
+def test_affine_protein_and_linear_reduction(ctx):
+    members, roots = synth.protein_families(seed=3, n_fam=3, per_fam=10)
+    rows = members.seqs() + roots.seqs()
+    pairs = [[members.n + f, f * 10 + k] for f in range(3) for k in range(10)]
+    _check_affine(ctx, rows, pairs, (0, 1, 10, 1))
+    # open = 0: the linear model, same scores and scripts as the linear kernel
+    seqs = api.ByteSeqs.from_list(rows)
+    pr = np.asarray(pairs, np.int32)
+    s0, o0, f0, l0 = api.nw_align_batch(ctx, seqs, pr, 0, 1, 1, gap_open=0)
+    s1, o1, f1, l1 = api.nw_align_batch(ctx, seqs, pr, 0, 1, 1)
+    ctx.check()
+    np.testing.assert_array_equal(s0.cpu().numpy(), s1.cpu().numpy())
+    np.testing.assert_array_equal(l0.cpu().numpy(), l1.cpu().numpy())
+    np.testing.assert_array_equal(o0.cpu().numpy(), o1.cpu().numpy())
