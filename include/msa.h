@@ -328,6 +328,13 @@ msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *orde
                           const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
                           int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t *pos,
                           int32_t *width, int32_t *score, void *stream);
+/* The same merge with affine gap costs (msa_nw_align_batch_affine's model:
+ * a run of L gaps costs gap_open + L * gap_ext) for the center alignments. */
+msa_status msa_merge_tree_affine(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                                 const int32_t *hi, const int32_t *center, const int32_t *left,
+                                 const int32_t *right, int32_t n_nodes, int32_t match, int32_t mismatch,
+                                 int32_t gap_open, int32_t gap_ext, int32_t *pos, int32_t *width, int32_t *score,
+                                 void *stream);
 /* Writes the MSA rows (ASCII, '-' for gaps) in `order`: row r (W bytes at
  * rows + r*W, device) is sequence order[r]; W = width of the root. */
 msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,

@@ -500,8 +500,11 @@ def partition(seqs, dist=None):
     return nodes
 
 
-def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1):
+def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1, gap_open=None):
     """Post-order merge of section "Merging" over the tree from :func:`partition`.
+
+    With ``gap_open`` the centers are aligned by :func:`nw_affine` (a run of L
+    gaps costs ``gap_open + L * gap``) instead of :func:`nw`.
 
     A leaf is the one-row MSA of its sequence.  At an internal node the two
     children's centers, as gapped rows of the children's MSAs, are aligned by
@@ -526,7 +529,10 @@ def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1):
             msa[k] = ([bytes(seqs[s])], [s])
             continue
         L, R = nd["left"], nd["right"]
-        score, ops = nw(center_row(L), center_row(R), match, mismatch, gap)
+        if gap_open is None:
+            score, ops = nw(center_row(L), center_row(R), match, mismatch, gap)
+        else:
+            score, ops = nw_affine(center_row(L), center_row(R), match, mismatch, gap_open, gap)
         merges[k] = (score, ops)
         rowsL, ordL = msa.pop(L)
         rowsR, ordR = msa.pop(R)

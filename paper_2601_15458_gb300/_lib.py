@@ -73,6 +73,9 @@ SIGNATURES = {
     "msa_merge_tree": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                  c_void_p, c_void_p]),
+    "msa_merge_tree_affine": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p,
+                                        c_void_p, c_void_p, c_void_p]),
     "msa_msa_metrics": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                   c_int32, ctypes.c_uint8, c_void_p, c_void_p, c_void_p]),
     "msa_msa_rows": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int32, c_void_p,

@@ -388,15 +388,22 @@ def clam_partition(ctx: Context, seqs: DeviceSeqs, band: "BandModel | None" = No
     return t
 
 
-def merge_tree(ctx: Context, seqs: DeviceSeqs, tree: Tree, match=0, mismatch=1, gap=1, stream=None):
-    """A12: bottom-up merge; returns ``(pos tensor, width[n_nodes], score[n_nodes])``."""
+def merge_tree(ctx: Context, seqs: DeviceSeqs, tree: Tree, match=0, mismatch=1, gap=1, stream=None,
+               gap_open: int | None = None):
+    """A12: bottom-up merge; returns ``(pos tensor, width[n_nodes], score[n_nodes])``.
+
+    With ``gap_open`` the center alignments use affine gaps (a run of L gaps
+    costs ``gap_open + L * gap``; msa_merge_tree_affine)."""
     pos = torch.empty(max(seqs.total, 1), dtype=torch.int32, device="cuda")
     width = np.zeros(max(tree.n_nodes, 1), np.int32)
     score = np.zeros(max(tree.n_nodes, 1), np.int32)
-    ctx.raise_if(_lib.lib().msa_merge_tree(ctx.handle, ctypes.byref(seqs.c), _ptr(tree.order), _np_ptr(tree.lo),
-                                           _np_ptr(tree.hi), _np_ptr(tree.center), _np_ptr(tree.left),
-                                           _np_ptr(tree.right), tree.n_nodes, match, mismatch, gap, _ptr(pos),
-                                           _np_ptr(width), _np_ptr(score), _stream(stream)))
+    tr = (ctypes.byref(seqs.c), _ptr(tree.order), _np_ptr(tree.lo), _np_ptr(tree.hi), _np_ptr(tree.center),
+          _np_ptr(tree.left), _np_ptr(tree.right), tree.n_nodes, match, mismatch)
+    outs = (_ptr(pos), _np_ptr(width), _np_ptr(score), _stream(stream))
+    if gap_open is None:
+        ctx.raise_if(_lib.lib().msa_merge_tree(ctx.handle, *tr, gap, *outs))
+    else:
+        ctx.raise_if(_lib.lib().msa_merge_tree_affine(ctx.handle, *tr, gap_open, gap, *outs))
     return pos, width[: tree.n_nodes], score[: tree.n_nodes]
 
 

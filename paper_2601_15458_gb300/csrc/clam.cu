@@ -490,10 +490,13 @@ msa_status msa_clam_partition_banded(msa_ctx *ctx, const msa_seqset *s, const vo
 }
 
 
-msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
-                          const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
-                          int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t *pos,
-                          int32_t *width, int32_t *score, void *stream) {
+}  // extern "C"
+
+// gap_open < 0: linear gaps (gap per position); else a run of L gaps costs gap_open + L * gap
+static msa_status merge_tree_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                                 const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
+                                 int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t gap_open,
+                                 int32_t *pos, int32_t *width, int32_t *score, void *stream) {
     if (!ctx || !s) return MSA_EINVAL;
     if (!order || !lo || !hi || !center || !left || !right || !pos || !width || !score)
         return set_error(ctx, MSA_EINVAL, "msa_merge_tree: null pointer");
@@ -592,9 +595,11 @@ msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *orde
         center_rows_kernel<<<std::min(2 * M, 65535), 256, 0, st>>>(s->codes, s->offs, pos, d_rc, d_roff, 2 * M,
                                                                    gap_code, rows);
         ++ctx->launches;
-        if ((rc = nw_run(ctx, ar, rows, d_roff, 2 * M, roff[2 * M], maxw, d_pairs, M, match, mismatch, gap, d_score,
-                         ops, d_ooff, d_len, st)))
-            return rc;
+        rc = gap_open < 0 ? nw_run(ctx, ar, rows, d_roff, 2 * M, roff[2 * M], maxw, d_pairs, M, match, mismatch, gap,
+                                   d_score, ops, d_ooff, d_len, st)
+                          : nw_affine_run(ctx, ar, rows, d_roff, 2 * M, roff[2 * M], maxw, d_pairs, M, match,
+                                          mismatch, gap_open, gap, d_score, ops, d_ooff, d_len, st);
+        if (rc) return rc;
         column_maps_kernel<<<(M + 127) / 128, 128, 0, st>>>(ops, d_ooff, d_len, d_roff, M, maps);
         const int64_t members = seg_start[2 * M];
         apply_maps_kernel<<<(int)std::min<int64_t>((members + 7) / 8, 65535), 256, 0, st>>>(
@@ -612,6 +617,26 @@ msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *orde
         }
     }
     return MSA_OK;
+}
+
+extern "C" {
+
+msa_status msa_merge_tree(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                          const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
+                          int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t *pos,
+                          int32_t *width, int32_t *score, void *stream) {
+    return merge_tree_run(ctx, s, order, lo, hi, center, left, right, n_nodes, match, mismatch, gap, -1, pos, width,
+                          score, stream);
+}
+
+msa_status msa_merge_tree_affine(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                                 const int32_t *hi, const int32_t *center, const int32_t *left,
+                                 const int32_t *right, int32_t n_nodes, int32_t match, int32_t mismatch,
+                                 int32_t gap_open, int32_t gap_ext, int32_t *pos, int32_t *width, int32_t *score,
+                                 void *stream) {
+    if (ctx && gap_open < 0) return set_error(ctx, MSA_EINVAL, "msa_merge_tree_affine: gap_open < 0");
+    return merge_tree_run(ctx, s, order, lo, hi, center, left, right, n_nodes, match, mismatch, gap_ext, gap_open,
+                          pos, width, score, stream);
 }
 
 msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,

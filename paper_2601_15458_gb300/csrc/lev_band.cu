@@ -52,7 +52,10 @@ static const int kBandGHost[kBandBuckets] = BAND_G_LIST;
 static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
 // a band whose rows per column (k + H) exceed this share of the column goes
 // to the full bit-vector DP, whose kernels need no band bookkeeping
-constexpr float kBandMaxShare = 0.75f;
+#ifndef MSA_BAND_MAX_SHARE
+#define MSA_BAND_MAX_SHARE 0.75f
+#endif
+constexpr float kBandMaxShare = MSA_BAND_MAX_SHARE;
 constexpr int kBandRounds = 8;
 constexpr int kBandThreads = 128;
 #ifndef MSA_BAND_HEADROOM

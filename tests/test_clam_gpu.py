@@ -34,10 +34,10 @@ def _check_same_tree(gpu, ref):
         assert g == r
 
 
-def _full(ctx, ds):
+def _full(ctx, ds, gap_open=None):
     sq = api.upload_and_pack(ctx, ds)
     tree = api.clam_partition(ctx, sq)
-    pos, width, score = api.merge_tree(ctx, sq, tree)
+    pos, width, score = api.merge_tree(ctx, sq, tree, gap_open=gap_open)
     rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
     ctx.check()
     return sq, tree, width, score, rows.cpu().numpy()
@@ -162,3 +162,20 @@ def test_msa_metrics_16s_sample(ctx):
 def test_msa_metrics_protein(ctx):
     members, _ = synth.protein_families(seed=3, n_fam=3, per_fam=30)
     _metrics_check(ctx, members, None)
+
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.small_dna(seed=1),
+                                   lambda: synth.protein_families(seed=3, n_fam=3, per_fam=30)[0]])
+def test_affine_merge_matches_oracle(ctx, maker):
+    """The merge with affine gaps (open 10, extend 1): identical MSA rows and
+    per-merge scores to the oracle's post-order merge."""
+    ds = maker()
+    seqs = ds.seqs()
+    sq, tree, width, score, rows = _full(ctx, ds, gap_open=10)
+    ref_nodes = oracle.partition(seqs)
+    ref_rows, ref_order, merges = oracle.merge_tree(seqs, ref_nodes, gap=1, gap_open=10)
+    assert list(tree.order.cpu().numpy()) == ref_order
+    assert [r.tobytes() for r in rows] == ref_rows
+    for k, (sc, _) in merges.items():
+        assert score[k] == sc
