@@ -197,13 +197,15 @@ class ByteSeqs:
 
 
 def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_off: torch.Tensor | None = None,
-                   stream=None, gap_open: int | None = None):
+                   stream=None, gap_open: int | None = None, ops: torch.Tensor | None = None):
     """A5/A6: NW score, edit script (forward order, bytes M/X/D/I) per pair.
 
     Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64, ops_len[P] int32)``.
     ``seqs`` is a :class:`ByteSeqs` or a packed :class:`DeviceSeqs` (its byte codes).
     With ``gap_open`` the gap costs are affine: a run of L gaps costs
-    ``gap_open + L * gap`` (msa_nw_align_batch_affine).
+    ``gap_open + L * gap`` (msa_nw_align_batch_affine).  A caller that passes
+    both ``ops_off`` and an ``ops`` buffer of ``ops_off[-1]`` bytes makes the
+    call without a host synchronisation.
     """
     if isinstance(seqs, DeviceSeqs):
         seqs = ByteSeqs.from_device_seqs(seqs)
@@ -215,8 +217,9 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
         cap = lens[pairs[:, 0].long()] + lens[pairs[:, 1].long()]
         ops_off = torch.zeros(P + 1, dtype=torch.int64, device=dev)
         torch.cumsum(cap, 0, out=ops_off[1:])
-    cap_total = int(ops_off[-1].item()) if P else 0
-    ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
+    if ops is None:                      # sized from the offsets (one device read)
+        cap_total = int(ops_off[-1].item()) if P else 0
+        ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
     score = torch.empty(P, dtype=torch.int32, device=dev)
     ops_len = torch.empty(P, dtype=torch.int32, device=dev)
     if gap_open is None:

