@@ -39,18 +39,52 @@ constexpr int kBvTileRows = 32 * kBvTileWords;
 constexpr int kBvWarps = 4;
 constexpr uint32_t kBvFull = 0xffffffffu;
 
+// Two columns per pipeline step: lane l computes columns 2q - 1 and 2q at
+// step q + l, so the shuffle and the loop are paid once per two columns.
 // Moves of one pair: uint2 {diagonal plane, up plane} per (tile, step, lane,
-// word), step = column + lane: the 32 lanes of one pipeline step write one
-// contiguous 512-byte run.
-__host__ __device__ inline int64_t nw_bv_steps(int max_len) { return (int64_t)max_len + 32; }
+// column of the step, word): the 32 lanes of one step write one contiguous
+// 1 KB run.
+__host__ __device__ inline int64_t nw_bv_steps(int max_len) { return ((int64_t)max_len + 1) / 2 + 32; }
 __host__ __device__ inline int64_t nw_bv_move_bytes(int max_len) {
     const int64_t tiles = (max_len + kBvTileRows - 1) / kBvTileRows;
-    return tiles * nw_bv_steps(max_len) * 32 * kBvWpl * 8;
+    return tiles * nw_bv_steps(max_len) * 32 * 2 * kBvWpl * 8;
 }
-// index (in uint2) of the moves of word W (over all rows) at column j
+// index (in uint2) of the moves of word W (over all rows) at column j >= 1
 __device__ __forceinline__ int64_t nw_bv_move_index(int W, int j, int max_len) {
     const int T = W / kBvTileWords, L = (W % kBvTileWords) / kBvWpl, w = W % kBvWpl;
-    return ((T * nw_bv_steps(max_len) + j + L) * 32 + L) * kBvWpl + w;
+    const int q = (j + 1) >> 1, c = (j - 1) & 1;
+    return ((T * nw_bv_steps(max_len) + q + L) * 32 + L) * (2 * kBvWpl) + c * kBvWpl + w;
+}
+
+// One column over the lane's words; returns the Ph bit and carry sent down
+// and writes the column's move planes.
+__device__ __forceinline__ uint32_t nw_bv_column(const uint32_t (&eq)[kBvWpl], uint32_t (&Pv)[kBvWpl],
+                                                 uint32_t (&Mv)[kBvWpl], uint32_t bits, uint2 *dst) {
+    const uint32_t ph_in = bits & 1u, cin = (bits >> 1) & 1u;
+    uint32_t u[kBvWpl], sum[kBvWpl], pv[kBvWpl];
+#pragma unroll
+    for (int w = 0; w < kBvWpl; ++w) {
+        pv[w] = Pv[w];
+        u[w] = eq[w] & pv[w];
+    }
+    const uint32_t cout = CarryChainIn<kBvWpl>::add(sum, u, pv, cin);
+    uint32_t php = ph_in << 31;
+    uint2 mvw[kBvWpl];
+#pragma unroll
+    for (int w = 0; w < kBvWpl; ++w) {
+        const uint32_t mhs = sum[w] ^ u[w] ^ pv[w];
+        const uint32_t ph = Mv[w] | ~(sum[w] | pv[w] | eq[w]);
+        const uint32_t phs = __funnelshift_l(php, ph, 1);
+        php = ph;
+        const uint32_t xv = eq[w] | Mv[w];
+        const uint32_t diag = eq[w] | ~((sum[w] ^ pv[w]) | Mv[w]);
+        Pv[w] = mhs | ~(xv | phs);
+        Mv[w] = phs & xv;
+        mvw[w] = make_uint2(diag, Pv[w]);
+    }
+#pragma unroll
+    for (int w = 0; w < kBvWpl; ++w) dst[w] = mvw[w];
+    return (php >> 31) | (cout << 1);
 }
 
 struct NwBvArgs {
@@ -175,74 +209,59 @@ __global__ void __launch_bounds__(kBvWarps * 32) nw_bv_kernel(NwBvArgs a) {
                 Pv[w] = kBvFull;
                 Mv[w] = 0u;
             }
-            uint2 *mv_tile = moves + (int64_t)t * nw_bv_steps(a.max_len) * 32 * kBvWpl;
+            uint2 *mv_tile = moves + (int64_t)t * nw_bv_steps(a.max_len) * 32 * 2 * kBvWpl;
             // lanes whose rows all lie past m feed nobody: they idle
             const bool live = row0 < m;
-            // the next column's masks are read one step ahead (its byte two
-            // steps ahead), off the carry chain's critical path
-            uint32_t eqn[kBvWpl];
-            // bytes of the lane's next columns j + 1 .. j + 4, loaded 4 steps ahead
-            int bq1 = n > 1 ? (int)__ldg(Bq + 1) : 0, bq2 = n > 2 ? (int)__ldg(Bq + 2) : 0;
-            int bq3 = n > 3 ? (int)__ldg(Bq + 3) : 0, bq4 = n > 4 ? (int)__ldg(Bq + 4) : 0;
-            {
-                const int ci = lut[Bq[0]];
+            // masks of the next step's two columns are read one step ahead
+            // (their bytes two steps ahead), off the carry chain's critical path
+            auto masks = [&](int byte, uint32_t (&e)[kBvWpl]) {
+                const int ci = lut[byte];
 #pragma unroll
                 for (int w = 0; w < kBvWpl; ++w) {
-                    const uint32_t e = sPeq[wid][w][ci & 31][lane];     // index kept in range
-                    eqn[w] = ci == 0xFF ? 0u : e;
+                    const uint32_t v = sPeq[wid][w][ci & 31][lane];     // index kept in range
+                    e[w] = ci == 0xFF ? 0u : v;
                 }
-            }
+            };
+            uint32_t eqA[kBvWpl], eqB[kBvWpl];
+            masks(Bq[0], eqA);
+            masks(n > 1 ? (int)Bq[1] : 0, eqB);
+            int bA = n > 2 ? (int)__ldg(Bq + 2) : 0, bB = n > 3 ? (int)__ldg(Bq + 3) : 0;
+            const int nq = (n + 1) / 2;
             uint32_t out = 0u;
-            for (int s = 1; s <= n + 31; ++s) {
+            for (int s = 1; s <= nq + 31; ++s) {
                 const uint32_t in = __shfl_up_sync(FULL, out, 1);
-                const int j = s - lane;
-                if (live && j >= 1 && j <= n) {
+                const int q = s - lane;
+                if (live && q >= 1 && q <= nq) {
+                    const int j1 = 2 * q - 1, j2 = 2 * q;          // j2 may be n + 1: computed, never read
                     uint32_t bits = in;
-                    if (lane == 0) bits = t == 0 ? 1u : (uint32_t)brow[j];
-                    const uint32_t ph_in = bits & 1u, cin = (bits >> 1) & 1u;
-                    uint32_t eq[kBvWpl], u[kBvWpl], sum[kBvWpl], pv[kBvWpl];
-#pragma unroll
-                    for (int w = 0; w < kBvWpl; ++w) eq[w] = eqn[w];
-                    if (j < n) {
-                        const int ci = lut[bq1];
-#pragma unroll
-                        for (int w = 0; w < kBvWpl; ++w) {
-                            const uint32_t e = sPeq[wid][w][ci & 31][lane];
-                            eqn[w] = ci == 0xFF ? 0u : e;
-                        }
-                        bq1 = bq2;
-                        bq2 = bq3;
-                        bq3 = bq4;
-                        bq4 = j + 4 < n ? (int)__ldg(Bq + j + 4) : 0;
-                    }
+                    if (lane == 0) bits = t == 0 ? 5u : ((uint32_t)brow[j1] | (j2 <= n ? (uint32_t)brow[j2] << 2 : 0u));
+                    uint32_t e1[kBvWpl], e2[kBvWpl];
 #pragma unroll
                     for (int w = 0; w < kBvWpl; ++w) {
-                        pv[w] = Pv[w];
-                        u[w] = eq[w] & pv[w];
+                        e1[w] = eqA[w];
+                        e2[w] = eqB[w];
                     }
-                    const uint32_t cout = CarryChainIn<kBvWpl>::add(sum, u, pv, cin);
-                    uint32_t php = ph_in << 31;
-                    uint2 mvw[kBvWpl];
-#pragma unroll
-                    for (int w = 0; w < kBvWpl; ++w) {
-                        const uint32_t mhs = sum[w] ^ u[w] ^ pv[w];
-                        const uint32_t ph = Mv[w] | ~(sum[w] | pv[w] | eq[w]);
-                        const uint32_t phs = __funnelshift_l(php, ph, 1);
-                        php = ph;
-                        const uint32_t xv = eq[w] | Mv[w];
-                        const uint32_t diag = eq[w] | ~((sum[w] ^ pv[w]) | Mv[w]);
-                        Pv[w] = mhs | ~(xv | phs);
-                        Mv[w] = phs & xv;
-                        mvw[w] = make_uint2(diag, Pv[w]);
+                    if (q < nq) {
+                        masks(bA, eqA);
+                        masks(bB, eqB);
+                        bA = j2 + 2 < n ? (int)__ldg(Bq + j2 + 2) : 0;
+                        bB = j2 + 3 < n ? (int)__ldg(Bq + j2 + 3) : 0;
                     }
-                    uint2 *dst = mv_tile + ((int64_t)s * 32 + lane) * kBvWpl;     // s = j + lane
-#pragma unroll
-                    for (int w = 0; w < kBvWpl; ++w) dst[w] = mvw[w];
-                    out = (php >> 31) | (cout << 1);
-                    if (lane == 31) brow[j] = (uint8_t)out;
-                    if (j == n) {
+                    uint2 *dst = mv_tile + ((int64_t)s * 32 + lane) * (2 * kBvWpl);   // s = q + lane
+                    const uint32_t o1 = nw_bv_column(e1, Pv, Mv, bits, dst);
+                    if (j1 == n) {
 #pragma unroll
                         for (int w = 0; w < kBvWpl; ++w) part += __popc(Pv[w] & maskw[w]) - __popc(Mv[w] & maskw[w]);
+                    }
+                    const uint32_t o2 = nw_bv_column(e2, Pv, Mv, bits >> 2, dst + kBvWpl);
+                    if (j2 == n) {
+#pragma unroll
+                        for (int w = 0; w < kBvWpl; ++w) part += __popc(Pv[w] & maskw[w]) - __popc(Mv[w] & maskw[w]);
+                    }
+                    out = o1 | (o2 << 2);
+                    if (lane == 31) {
+                        brow[j1] = (uint8_t)o1;
+                        if (j2 <= n) brow[j2] = (uint8_t)o2;
                     }
                 }
             }
