@@ -8,6 +8,7 @@
     python -m paper_2601_15458_gb300.cases mlp     # band network forward + one training step
     python -m paper_2601_15458_gb300.cases protein # 10,000 x 100 centre distances, 9,999 NW with traceback
     python -m paper_2601_15458_gb300.cases nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
+    python -m paper_2601_15458_gb300.cases metrics # MSA quality of a 3,000-sequence MSA, 2,000-row sample
 
 Each case runs its call a few times (the first warms up) and prints one
 line with the call's device time.
@@ -73,6 +74,22 @@ def case_nw_affine(ctx):
     return _time(lambda: api.nw_align_batch(ctx, sq, pairs, 0, 1, 1, ops_off=off, gap_open=10, ops=ops))
 
 
+def case_metrics(ctx):
+    ds = synth.gg16s_dna(seed=5, n=3000)
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0]))
+    t0 = time.perf_counter()
+    api.msa_metrics(ctx, sq, tree, rows, sample=2000, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = api.msa_metrics(ctx, sq, tree, rows, sample=2000, seed=0)
+    ms = (time.perf_counter() - t0) * 1e3
+    print({k: v for k, v in m.items() if k != "sample"})
+    return ms
+
+
 def case_band(ctx):
     ev = synth.divergent_pairs(seed=40, n_pairs=100000)
     sq = api.upload_and_pack(ctx, ev)
@@ -134,7 +151,7 @@ def case_protein(ctx):
 
 
 CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
-             protein=case_protein, nw_affine=case_nw_affine)
+             protein=case_protein, nw_affine=case_nw_affine, metrics=case_metrics)
 
 
 def main(argv):
