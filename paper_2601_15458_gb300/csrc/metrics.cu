@@ -103,8 +103,9 @@ __global__ void metric_pairs_kernel(const int32_t *__restrict__ seq_of, int S, i
 __global__ void __launch_bounds__(256) metric_hamming_kernel(const uint32_t *__restrict__ planes, int S, int64_t Wp,
                                                              const int32_t *__restrict__ lev, int ntile,
                                                              double *sum, unsigned long long *cnt) {
-    __shared__ uint32_t sI[kMetTile][kMetChunk][8];
-    __shared__ uint32_t sJ[kMetTile][kMetChunk][8];
+    // rows padded to 65 words: threads reading 16 different rows hit 16 banks
+    __shared__ uint32_t sI[kMetTile][kMetChunk * 8 + 1];
+    __shared__ uint32_t sJ[kMetTile][kMetChunk * 8 + 1];
     __shared__ double red[256];
     __shared__ unsigned long long redc[256];
     // tile (ti, tj) with ti <= tj from the block index
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(256) metric_hamming_kernel(const uint32_t *__r
             const int r = e / (kMetChunk * 8), w = (e / 8) % kMetChunk, p = e % 8;
             const int64_t wg = w0 + w;
             const int ri = I0 + r, rj = J0 + r;
-            sI[r][w][p] = (ri < S && wg < Wp) ? planes[((int64_t)ri * Wp + wg) * 8 + p] : 0u;
-            sJ[r][w][p] = (rj < S && wg < Wp) ? planes[((int64_t)rj * Wp + wg) * 8 + p] : 0u;
+            sI[r][w * 8 + p] = (ri < S && wg < Wp) ? planes[((int64_t)ri * Wp + wg) * 8 + p] : 0u;
+            sJ[r][w * 8 + p] = (rj < S && wg < Wp) ? planes[((int64_t)rj * Wp + wg) * 8 + p] : 0u;
         }
         __syncthreads();
         for (int w = 0; w < kMetChunk; ++w) {
@@ -138,8 +139,8 @@ __global__ void __launch_bounds__(256) metric_hamming_kernel(const uint32_t *__r
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
-                    x[a][p] = sI[ty + 16 * a][w][p];
-                    y[a][p] = sJ[tx + 16 * a][w][p];
+                    x[a][p] = sI[ty + 16 * a][w * 8 + p];
+                    y[a][p] = sJ[tx + 16 * a][w * 8 + p];
                 }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
