@@ -177,6 +177,9 @@ def peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, sm_max_mhz=2070.0), "fallback"
 
 
+HELD_OUT_PAIRS = 20000   # per held-out set (calibration; margin timing)
+
+
 def band_bench(ctx, args, stream):
     """Learned band vs full DP on 100,000 fresh DNA pairs (lengths 1,000-10,000,
     divergence U(1%, 30%)), every distance checked against the full DP."""
@@ -186,12 +189,17 @@ def band_bench(ctx, args, stream):
     X, y, tinfo = learned_band.training_set(ctx, seed=4)
     model, minfo = learned_band.train(ctx, X, y, epochs=8, batch=4096, lr=2e-3, tau=0.9)
     del X, y
-    # the band margin is picked on held-out pairs of another seed, never on the evaluation pairs
-    val = synth.divergent_pairs(seed=41, n_pairs=5000)
-    vs = api.upload_and_pack(ctx, val)
-    vprof = api.kmer_profile(ctx, vs)
-    vp = torch.from_numpy(np.stack([np.arange(0, val.n, 2), np.arange(1, val.n, 2)], 1).astype(np.int32)).cuda()
-    gamma, _ = learned_band.pick_gamma(ctx, model, vs, vprof, vp)
+    # calibration and band margin come from held-out pairs of two other
+    # seeds, never from the evaluation pairs
+    def held_out(seed):
+        val = synth.divergent_pairs(seed=seed, n_pairs=HELD_OUT_PAIRS)
+        vs = api.upload_and_pack(ctx, val)
+        vp = torch.from_numpy(np.stack([np.arange(0, val.n, 2), np.arange(1, val.n, 2)], 1).astype(np.int32))
+        return vs, api.kmer_profile(ctx, vs), vp.cuda()
+
+    cal_set, gam_set = held_out(41), held_out(42)
+    gamma_raw, _ = learned_band.pick_gamma(ctx, model, *gam_set)
+    cal_tau, gamma, _ = learned_band.pick_band(ctx, model, cal_set, gam_set)
     setup_s = time.perf_counter() - t0
     ev = synth.divergent_pairs(seed=40, n_pairs=args.band_pairs)
     es = api.upload_and_pack(ctx, ev)
@@ -201,7 +209,12 @@ def band_bench(ctx, args, stream):
     lens = np.diff(ev.offs)
     cells = int((lens[0::2].astype(np.int64) * lens[1::2]).sum())
     d_full = api.lev_batch(ctx, es, pairs)
+    knots = model.state[-64:].clone()
+    model.calibrate(None, None)                    # the network alone, for comparison
+    _, k_raw = model.predict_band(es, prof, pairs, gamma=gamma_raw, margin=8)
+    model.state[-64:].copy_(knots)
     yhat, k = model.predict_band(es, prof, pairs, gamma=gamma, margin=8)
+    d_raw, _ = api.lev_banded_batch(ctx, es, pairs, k_raw)
     d_band, k_used = api.lev_banded_batch(ctx, es, pairs, k)
     # non-learned start: the 4-mer L1 lower bound, ceil(L1 / 8) <= f
     cnt = prof.int() & 0xFFFF
@@ -211,7 +224,8 @@ def band_bench(ctx, args, stream):
     k_l1 = torch.maximum(dl, ((l1 + 7) // 8).int())
     d_l1, _ = api.lev_banded_batch(ctx, es, pairs, k_l1)
     ctx.check()
-    mism = int((d_band != d_full).sum().item()) + int((d_l1 != d_full).sum().item())
+    mism = (int((d_band != d_full).sum().item()) + int((d_l1 != d_full).sum().item())
+            + int((d_raw != d_full).sum().item()))
     first = float((k_used.cpu().numpy() < np.maximum(lens[0::2], lens[1::2])).mean())
     import oracle
     rng = np.random.default_rng(9)
@@ -237,12 +251,18 @@ def band_bench(ctx, args, stream):
     t_band = timed(lambda: (model.predict_band(es, prof, pairs, gamma=gamma, margin=8),
                             api.lev_banded_batch(ctx, es, pairs, k, d_band, k_used)), reps)
     t_l1 = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_l1, d_l1), reps)
+    t_raw = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_raw, d_raw), reps)
     ctx.check()
     args.band_model = (model, gamma)
     return dict(workload=f"divergent_dna_pairs_{P}_len1000-10000_div1-30pct", pairs=P, cells=cells,
                 pairs_per_s_learned=P / (t_band / 1e3), pairs_per_s_full=P / (t_full / 1e3),
                 pairs_per_s_l1_bound=P / (t_l1 / 1e3), speedup_learned_vs_full=t_full / t_band,
                 speedup_learned_vs_l1_bound=t_l1 / t_band,
+                speedup_uncalibrated_vs_full=t_full / t_raw,
+                calibration=dict(tau=cal_tau, pairs=HELD_OUT_PAIRS, gamma_uncalibrated=gamma_raw,
+                                 k_mean_over_f=float((k.double() / d_full.double().clamp(min=1)).mean().item()),
+                                 k_mean_over_f_uncalibrated=float(
+                                     (k_raw.double() / d_full.double().clamp(min=1)).mean().item())),
                 gcups_full=cells / (t_full / 1e3) / 1e9, gcups_equiv_learned=cells / (t_band / 1e3) / 1e9,
                 ms_learned=t_band, ms_full=t_full, mismatches=mism, oracle_sample=len(samp),
                 certified_by_band=first, gamma=gamma, train_pairs=tinfo["pairs"], train_steps=minfo["steps"],

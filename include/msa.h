@@ -124,12 +124,31 @@ msa_status msa_pack(msa_ctx *ctx, const msa_seqset *s, void *stream);
 msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
                          int64_t P, int32_t *d_out, void *stream);
 
-/* Selects the kernel schedule of msa_lev_batch (lane-versus-warp threshold,
- * targets per task) by running this batch under each candidate and timing it
- * with CUDA events; the fastest is kept in ctx for later calls.  d_out ends
- * up holding the distances, as after msa_lev_batch.  Synchronises `stream`. */
+/* Selects the kernel schedule of msa_lev_batch (the target-count thresholds
+ * between the kernels, targets per task) by running this batch under each
+ * candidate and timing it with CUDA events; the fastest is kept in ctx for
+ * later calls.  d_out ends up holding the distances, as after
+ * msa_lev_batch.  Synchronises `stream`. */
 msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
                             int64_t P, int32_t *d_out, void *stream);
+
+/*
+ * The schedule msa_lev_batch uses, as 4 ints:
+ *   [0] lane_min_targets: a query (first index) with at least this many
+ *       targets gets a warp of its own, one target per lane (default 32);
+ *   [1] slot_min_targets: a query with fewer targets than [0] but at least
+ *       this many shares a warp with up to 7 others, the 32 lanes taking the
+ *       targets of all of them (default 2; >= [0] turns this kernel off);
+ *   [2] lane_per_task: targets per warp task of the first kernel (0: from
+ *       the batch size);
+ *   [3] warp_per_task: targets per task of the warp-per-pair kernel, which
+ *       takes every other query (default 4).
+ * Any choice gives the same distances.  msa_lev_tune_set leaves an entry
+ * unchanged where the value is negative (0 is accepted only for [2]);
+ * MSA_EINVAL for [0], [1] or [3] equal to 0.  Host-only calls.
+ */
+msa_status msa_lev_tune_get(msa_ctx *ctx, int32_t *tune4);
+msa_status msa_lev_tune_set(msa_ctx *ctx, const int32_t *tune4);
 
 /*
  * Allocation-free variant of msa_lev_batch (the paper has no counterpart;
@@ -187,9 +206,12 @@ int64_t msa_lev_banded_workspace_bytes(int64_t P, int32_t n_seqs);
  *
  * Model state: one device buffer of msa_mlp_state_bytes() bytes that starts
  * with the msa_mlp_num_params() fp32 parameters in the order
- * W1 (out-major, [128][256]), b1, W2 ([64][128]), b2, W3 [64], b3; the rest
- * (Adam moments, gradient, bf16 copies) is private.  After writing the
- * parameters, call msa_mlp_sync() (bf16 copies, zero moments and step).
+ * W1 (out-major, [128][256]), b1, W2 ([64][128]), b2, W3 [64], b3, and ends
+ * with 64 floats of band calibration ([0] = 1 when fitted, [1..33] the
+ * knots, see msa_band_calibrate; all zero = none); the rest (Adam moments,
+ * gradient, bf16 copies) is private.  After writing the parameters, call
+ * msa_mlp_sync() (bf16 copies, zero moments and step; the calibration is
+ * left as it is).
  */
 int32_t msa_mlp_num_params(void);
 int64_t msa_mlp_state_bytes(void);
@@ -221,12 +243,34 @@ msa_status msa_mlp_read_grad(msa_ctx *ctx, void *state, float *grad_out, void *s
 /*
  * Fused features + forward + band policy for each pair:
  *   yhat[p] = network output, k_out[p] = max(|m - n|,
- *   ceil((1 + gamma) * max(yhat, 0) * max(m, n)) + margin).
+ *   ceil((1 + gamma) * c * max(m, n)) + margin),
+ * with c = max(yhat, 0), or c = c(yhat) of msa_band_calibrate when the state
+ * holds a calibration (both products rounded to fp32 in that order).
  * prof from msa_kmer_profile of the same set.
  */
 msa_status msa_band_predict(msa_ctx *ctx, const void *state, const msa_seqset *s, const uint16_t *prof,
                             const int32_t *pairs, int64_t P, float gamma, int32_t margin, float *yhat,
                             int32_t *k_out, void *stream);
+/*
+ * Band calibration (this library's addition to the learned band: the
+ * network is trained on one population of pairs and its output need not be
+ * a calibrated quantile on another).  From N held-out pairs with network
+ * outputs yhat[j] and true y[j] = f / max(m, n) (device fp32 arrays), fits
+ * the 33 knots of a monotone map c at yhat = 0, 1/32, ..., 1 and stores them
+ * in the state:
+ *   bin(yhat) = min(32, max(0, floor(yhat * 32 + 0.5)))   (fp32),
+ *   knot i = the tau-quantile of min(1, max(0, y)) over the pairs of bin i,
+ *     the smallest v with #{y <= v} >= ceil(tau * n_i) (n_i >= 16; a bin with
+ *     fewer pairs keeps i / 32),
+ *   then knot i = max(knot 0 .. knot i).
+ * c(yhat) interpolates the knots linearly at min(1, max(0, yhat)) * 32 (fp32,
+ * each operation rounded).  Every distance stays exact whatever the band
+ * (the certificate of msa_lev_banded_batch decides), so the map only moves
+ * the starting band.  N = 0 removes the calibration.  tau in (0, 1].
+ * One single-block kernel, 5 passes over the inputs per knot; asynchronous.
+ */
+msa_status msa_band_calibrate(msa_ctx *ctx, void *state, const float *yhat, const float *y, int64_t N, float tau,
+                              void *stream);
 
 /* ---- A5/A6: Needleman-Wunsch with traceback ----------------------------- */
 /*

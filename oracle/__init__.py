@@ -20,6 +20,8 @@ computes the plain definition of what the GPU path computes:
   definition is this project's).
 * :func:`mlp_forward`, :func:`mlp_backward`, :func:`adam_step` -- the band
   proposer network 256->128->64->1 in float64 on bf16-rounded operands.
+* :func:`band_policy`, :func:`band_calibrate` -- the starting band from the
+  network's output and its per-bin quantile calibration (this project's).
 * :func:`partition` -- Alg. 1 ``Partition`` with the readings listed in the
   design notes (medoid sample rule, tie-breaks).
 * :func:`merge_tree` -- the post-order merge of section "Merging".
@@ -419,6 +421,59 @@ def adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
         vh = v[k] / (1 - beta2 ** t)
         out[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
     return out, m, v
+
+
+# Band policy and its calibration.  The paper's band proposer turns the
+# network's output into a Ukkonen band; these two functions are this
+# project's definition of that step (parity unpinned beyond the pins in the
+# tests: identity reduction, quantile definition, monotonicity).
+
+CAL_KNOTS = 33          # knots at yhat = 0, 1/32, ..., 1
+CAL_MIN_PAIRS = 16      # a bin with fewer held-out pairs keeps the identity
+
+
+def band_calibrate(yhat, y, tau: float = 0.95) -> np.ndarray:
+    """Knots of the monotone map c(yhat): knot i is the tau-quantile (the
+    smallest value v with #{y <= v} >= ceil(tau * n), the inverted-CDF
+    quantile) of the true y = f / max(m, n), clamped to [0, 1], over the
+    held-out pairs whose yhat rounds to i / 32; a bin with fewer than
+    CAL_MIN_PAIRS pairs keeps the identity i / 32; then a running maximum
+    makes the map non-decreasing.  All in float32 as the kernel does."""
+    yh = np.asarray(yhat, np.float32)
+    yv = np.fmin(np.fmax(np.asarray(y, np.float32), np.float32(0)), np.float32(1))
+    x = np.fmin(np.fmax(yh * np.float32(32) + np.float32(0.5), np.float32(0)), np.float32(32))
+    b = x.astype(np.int64)
+    knots = np.empty(CAL_KNOTS, np.float32)
+    for i in range(CAL_KNOTS):
+        v = np.sort(yv[b == i])
+        if len(v) < CAL_MIN_PAIRS:
+            knots[i] = np.float32(i) / np.float32(32)
+        else:
+            r = int(np.ceil(np.float64(np.float32(tau)) * len(v)))
+            knots[i] = v[min(max(r, 1), len(v)) - 1]
+    return np.maximum.accumulate(knots).astype(np.float32)
+
+
+def band_calibrated(knots: np.ndarray, yhat) -> np.ndarray:
+    """c(yhat): linear interpolation of the knots at clamp(yhat, 0, 1) * 32,
+    every operation rounded to float32."""
+    yh = np.fmin(np.fmax(np.asarray(yhat, np.float32), np.float32(0)), np.float32(1))
+    x = (yh * np.float32(32)).astype(np.float32)
+    i = np.minimum(x.astype(np.int64), CAL_KNOTS - 2)
+    f = (x - i.astype(np.float32)).astype(np.float32)
+    k0, k1 = knots[i], knots[i + 1]
+    return (k0 + (f * (k1 - k0)).astype(np.float32)).astype(np.float32)
+
+
+def band_policy(yhat, la, lb, gamma: float, margin: int, knots=None) -> np.ndarray:
+    """Starting band k = max(|m - n|, ceil((1 + gamma) * c * max(m, n)) +
+    margin) with c = max(yhat, 0), or c(yhat) of the calibration knots; the
+    products in float32 left to right."""
+    yh = np.asarray(yhat, np.float32)
+    c = np.fmax(yh, np.float32(0)) if knots is None else band_calibrated(knots, yh)
+    mx = np.maximum(la, lb).astype(np.float32)
+    kf = np.ceil(((np.float32(1) + np.float32(gamma)) * c).astype(np.float32) * mx).astype(np.int64)
+    return np.maximum(np.abs(np.asarray(la, np.int64) - lb), kf + margin)
 
 
 # ---------------------------------------------------------------------------

@@ -233,6 +233,17 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
     return score, ops, ops_off, ops_len
 
 
+def lev_schedule(ctx: Context, lane_min_targets: int = -1, slot_min_targets: int = -1, lane_per_task: int = -1,
+                 warp_per_task: int = -1) -> dict:
+    """Sets the entries of msa_lev_batch's schedule that are given (>= 0;
+    see ``msa_lev_tune_set``) and returns the schedule in force."""
+    v = (ctypes.c_int32 * 4)(lane_min_targets, slot_min_targets, lane_per_task, warp_per_task)
+    if any(x >= 0 for x in v):
+        ctx.raise_if(_lib.lib().msa_lev_tune_set(ctx.handle, v))
+    ctx.raise_if(_lib.lib().msa_lev_tune_get(ctx.handle, v))
+    return dict(lane_min_targets=v[0], slot_min_targets=v[1], lane_per_task=v[2], warp_per_task=v[3])
+
+
 def lev_autotune(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None = None, stream=None):
     """A7: choose the schedule for batches like this one; returns the distances."""
     pairs = _pairs_tensor(pairs)
@@ -314,6 +325,21 @@ class BandModel:
         g = torch.empty(self.np, dtype=torch.float32, device="cuda")
         self.ctx.raise_if(_lib.lib().msa_mlp_read_grad(self.ctx.handle, _ptr(self.state), _ptr(g), _stream(stream)))
         return unflatten_params(g.cpu().numpy())
+
+    def calibrate(self, yhat: torch.Tensor, y: torch.Tensor, tau: float = 0.95, stream=None):
+        """Fits the band calibration from held-out network outputs and true
+        y = f / max(m, n) (device fp32); ``calibrate(None, None)`` removes it."""
+        N = 0 if yhat is None else int(yhat.numel())
+        if N:
+            assert y.numel() == N and yhat.dtype == torch.float32 and y.dtype == torch.float32
+        self.ctx.raise_if(_lib.lib().msa_band_calibrate(self.ctx.handle, _ptr(self.state),
+                                                        _ptr(yhat) if N else None, _ptr(y) if N else None, N,
+                                                        float(tau), _stream(stream)))
+
+    def calibration(self):
+        """The 33 calibration knots, or None when the state holds none."""
+        cal = self.state[-64:].cpu().numpy()
+        return cal[1:34].copy() if cal[0] != 0 else None
 
     def predict_band(self, seqs: DeviceSeqs, prof: torch.Tensor, pairs, gamma: float = 0.1, margin: int = 8,
                      stream=None):

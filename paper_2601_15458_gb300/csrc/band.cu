@@ -31,12 +31,20 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH1 * kF, kOffW2 = kOffB1 + kH1, kOf
 constexpr int kS1 = kF + 8, kS2 = kH1 + 8, kS3 = kH2 + 8;  // padded smem row strides (bf16 elements)
 constexpr int kMlpWarps = 8;
 
-// state buffer: params | m | v | grad (fp32, NP each) | bf16 weights (NP) | loss/aux
+// state buffer: params | m | v | grad (fp32, NP each) | bf16 weights (NP) |
+// 64 spare | loss/aux (64) | band calibration (64)
 struct MlpState {
     float *p, *m, *v, *g;
     __nv_bfloat16 *h;
     float *aux;   // [0] loss sum of the last step, [1] step count
+    float *cal;   // [0] 1 when fitted, [1 .. kCalKnots] knots of c(yhat)
 };
+
+// Band calibration: knots of a monotone piecewise-linear map at yhat =
+// 0, 1/32, ..., 1 (the table is this library's addition to the band policy).
+constexpr int kCalKnots = 33;
+constexpr int kCalMinPairs = 16;
+constexpr int kCalFloats = 64;
 
 __host__ __device__ inline int64_t np_round(int64_t x) { return (x + 63) / 64 * 64; }
 
@@ -50,6 +58,7 @@ static MlpState state_of(void *base) {
     s.g = f + 3 * R;
     s.h = reinterpret_cast<__nv_bfloat16 *>(f + 4 * R);
     s.aux = f + 4 * R + R / 2 + 64;
+    s.cal = s.aux + 64;
     return s;
 }
 
@@ -263,8 +272,20 @@ struct FwdArgs {
     int32_t margin;
 };
 
+// c(yhat): the calibration knots interpolated at clamp(yhat, 0, 1) * 32,
+// each operation rounded on its own (no fused multiply-add), so a float32
+// restatement reproduces it bit for bit.
+__device__ __forceinline__ float band_cal(const float *knots, float y) {
+    const float x = __fmul_rn(fminf(fmaxf(y, 0.f), 1.f), 32.f);
+    const int i = min((int)x, kCalKnots - 2);
+    const float f = __fsub_rn(x, (float)i);
+    const float k0 = knots[i], k1 = knots[i + 1];
+    return __fadd_rn(k0, __fmul_rn(f, __fsub_rn(k1, k0)));
+}
+
 // Forward over P rows; with k_out also the band policy
-//   k = max(|m - n|, ceil((1 + gamma) * max(yhat, 0) * max(m, n)) + margin).
+//   k = max(|m - n|, ceil((1 + gamma) * c * max(m, n)) + margin),
+// c = max(yhat, 0), or c(yhat) once the state holds a calibration.
 __global__ void __launch_bounds__(kMlpWarps * 32) mlp_forward_kernel(FwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *W1s = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
@@ -307,12 +328,87 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_forward_kernel(FwdArgs a) 
                     }
                     const int lx = (int)(a.offs[x + 1] - a.offs[x]), lz = (int)(a.offs[z + 1] - a.offs[z]);
                     const int mx = max(lx, lz);
-                    const float kf = ceilf((1.f + a.gamma) * fmaxf(y, 0.f) * (float)mx);
+                    const float c = a.st.cal[0] != 0.f ? band_cal(a.st.cal + 1, y) : fmaxf(y, 0.f);
+                    const float kf = ceilf(__fmul_rn(__fmul_rn(1.f + a.gamma, c), (float)mx));
                     const int kk = (int)fminf(kf, 2.0e9f) + a.margin;
                     a.k_out[p] = max(abs(lx - lz), kk);
                 }
             }
         }
+    }
+}
+
+// Calibration fit, one block: for each knot i, the tau-quantile of the
+// clamped y over the pairs whose yhat rounds to i / 32 (smallest v with
+// #{y <= v} >= ceil(tau n)), found by a radix select on the float bits (y in
+// [0, 1] orders like its bits), 8 bits per pass; bins with fewer than
+// kCalMinPairs pairs keep the identity; a running maximum makes the map
+// monotone.  4 passes over the inputs per knot.
+__device__ __forceinline__ int cal_bin(float yh) {
+    const float x = fminf(fmaxf(__fadd_rn(__fmul_rn(yh, 32.f), 0.5f), 0.f), 32.f);
+    return (int)x;
+}
+
+__global__ void __launch_bounds__(1024) band_calibrate_kernel(const float *__restrict__ yhat,
+                                                              const float *__restrict__ y, int64_t N, double tau,
+                                                              float *cal) {
+    __shared__ uint32_t hist[256];
+    __shared__ unsigned long long s_cnt;
+    __shared__ uint32_t s_prefix;
+    __shared__ long long s_rank;
+    __shared__ float s_knot[kCalKnots];
+    const int tid = threadIdx.x;
+    for (int b = 0; b < kCalKnots; ++b) {
+        if (tid == 0) s_cnt = 0ull;
+        __syncthreads();
+        unsigned long long c = 0;
+        for (int64_t j = tid; j < N; j += blockDim.x) c += cal_bin(yhat[j]) == b;
+        atomicAdd(&s_cnt, c);
+        __syncthreads();
+        const long long nb = (long long)s_cnt;
+        if (nb < kCalMinPairs) {
+            if (tid == 0) s_knot[b] = -1.f;
+            __syncthreads();
+            continue;
+        }
+        long long r = (long long)ceil(tau * (double)nb);
+        r = r < 1 ? 1 : (r > nb ? nb : r);
+        uint32_t prefix = 0;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (int64_t j = tid; j < N; j += blockDim.x) {
+                if (cal_bin(yhat[j]) != b) continue;
+                const uint32_t bits = __float_as_uint(fminf(fmaxf(y[j], 0.f), 1.f));
+                if (shift == 24 || (bits >> (shift + 8)) == prefix) atomicAdd(&hist[(bits >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                long long cum = 0;
+                int dg = 0;
+                for (; dg < 255; ++dg) {
+                    if (cum + (long long)hist[dg] >= r) break;
+                    cum += hist[dg];
+                }
+                s_rank = r - cum;
+                s_prefix = (prefix << 8) | (uint32_t)dg;
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            r = s_rank;
+            __syncthreads();
+        }
+        if (tid == 0) s_knot[b] = __uint_as_float(prefix);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        float run = 0.f;
+        for (int b = 0; b < kCalKnots; ++b) {
+            const float k = s_knot[b] < 0.f ? (float)b / 32.f : s_knot[b];
+            run = fmaxf(run, k);
+            cal[1 + b] = run;
+        }
+        cal[0] = 1.f;
     }
 }
 
@@ -572,7 +668,21 @@ extern "C" {
 
 int32_t msa_mlp_num_params(void) { return kNP; }
 
-int64_t msa_mlp_state_bytes(void) { return (4 * np_round(kNP) + np_round(kNP) / 2 + 64 + 64) * 4; }
+int64_t msa_mlp_state_bytes(void) { return (4 * np_round(kNP) + np_round(kNP) / 2 + 64 + 64 + kCalFloats) * 4; }
+
+msa_status msa_band_calibrate(msa_ctx *ctx, void *state, const float *yhat, const float *y, int64_t N, float tau,
+                              void *stream) {
+    if (!ctx || !state) return MSA_EINVAL;
+    if (N < 0) return set_error(ctx, MSA_EINVAL, "msa_band_calibrate: N < 0");
+    if (!(tau > 0.f && tau <= 1.f)) return set_error(ctx, MSA_EINVAL, "msa_band_calibrate: tau %g not in (0, 1]", tau);
+    const cudaStream_t st = (cudaStream_t)stream;
+    MlpState S = state_of(state);
+    if (N == 0) return cuda_check(ctx, cudaMemsetAsync(S.cal, 0, sizeof(float), st), "msa_band_calibrate reset");
+    if (!yhat || !y) return set_error(ctx, MSA_EINVAL, "msa_band_calibrate: null pointer");
+    band_calibrate_kernel<<<1, 1024, 0, st>>>(yhat, y, N, (double)tau, S.cal);
+    ++ctx->launches;
+    return cuda_check(ctx, cudaGetLastError(), "msa_band_calibrate");
+}
 
 msa_status msa_mlp_sync(msa_ctx *ctx, void *state, void *stream) {
     if (!ctx || !state) return MSA_EINVAL;

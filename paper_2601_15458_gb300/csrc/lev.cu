@@ -28,7 +28,8 @@ namespace msa {
 constexpr int kMaxBuckets = 64;
 
 struct Tune {
-    int lane_min_targets = 12;  // below this a query goes to the warp kernel
+    int lane_min_targets = 32;  // a query with fewer targets shares a warp (slot kernel)
+    int slot_min_targets = 2;   // below this a query goes to the warp kernel
     int lane_per_task = 0;      // targets per task, lane kernel (0: from the batch size)
     int warp_per_task = 4;      // targets per task, warp kernel
     int occupancy[2][kMaxBuckets] = {};  // blocks per SM, per alphabet and bucket
@@ -37,18 +38,23 @@ struct Tune {
 Tune *create_tune() { return new Tune(); }
 void destroy_tune(Tune *t) { delete t; }
 
+// Buckets: [lane kernels | slot kernels (same word counts) | warp kernels].
 struct Registry {
     const LevKernelInfo *lane;
     int nlane;
+    const LevKernelInfo *slot;
     const LevKernelInfo *warp;
     int nwarp;
-    int count() const { return nlane + nwarp; }
-    const LevKernelInfo &at(int b) const { return b < nlane ? lane[b] : warp[b - nlane]; }
+    int count() const { return 2 * nlane + nwarp; }
+    const LevKernelInfo &at(int b) const {
+        return b < nlane ? lane[b] : b < 2 * nlane ? slot[b - nlane] : warp[b - 2 * nlane];
+    }
 };
 
 static Registry registry(int alphabet) {
-    if (alphabet == MSA_DNA) return {kLevLaneDna, kLevLaneDnaCount, kLevWarpDna, kLevWarpDnaCount};
-    return {kLevLaneProt, kLevLaneProtCount, kLevWarpProt, kLevWarpProtCount};
+    static_assert(2 * 23 + 16 <= kMaxBuckets, "bucket table too small");
+    if (alphabet == MSA_DNA) return {kLevLaneDna, kLevLaneDnaCount, kLevSlotDna, kLevWarpDna, kLevWarpDnaCount};
+    return {kLevLaneProt, kLevLaneProtCount, kLevSlotProt, kLevWarpProt, kLevWarpProtCount};
 }
 
 struct PlanParams {
@@ -56,17 +62,22 @@ struct PlanParams {
     int lane_words[32];
     int warp_words[32];
     int lane_min_targets;
+    int slot_min_targets;
     int lane_per_task;
     int warp_per_task;
 };
 
+// Lane kernel for queries with many targets, slot kernel (several queries
+// per warp) for those with a few, warp kernel for single targets and for
+// queries longer than the lane kernels' registers hold.
 __device__ __forceinline__ int pick_bucket(const PlanParams &pp, int W, int c) {
-    if (W <= pp.lane_words[pp.nlane - 1] && c >= pp.lane_min_targets) {
+    if (W <= pp.lane_words[pp.nlane - 1] && c >= pp.slot_min_targets) {
+        const int base = c >= pp.lane_min_targets ? 0 : pp.nlane;
         for (int b = 0; b < pp.nlane; ++b)
-            if (pp.lane_words[b] >= W) return b;
+            if (pp.lane_words[b] >= W) return base + b;
     }
     for (int b = 0; b < pp.nwarp; ++b)
-        if (32 * pp.warp_words[b] >= W) return pp.nlane + b;
+        if (32 * pp.warp_words[b] >= W) return 2 * pp.nlane + b;
     return -1;
 }
 
@@ -148,9 +159,9 @@ __global__ void __launch_bounds__(256) task_kernel(const int64_t *__restrict__ o
                                                    const int32_t *__restrict__ qstart, PlanParams pp,
                                                    int32_t *__restrict__ bcount, int32_t *__restrict__ bfill,
                                                    int32_t *__restrict__ boff, int2 *__restrict__ tasks,
-                                                   int32_t *err) {
+                                                   int32_t *__restrict__ bsum, int32_t *err) {
     __shared__ int32_t sboff[kMaxBuckets];
-    const int NB = pp.nlane + pp.nwarp;
+    const int NB = 2 * pp.nlane + pp.nwarp;
     if (PASS == 1) {
         if (threadIdx.x == 0) {
             int run = 0;
@@ -172,10 +183,12 @@ __global__ void __launch_bounds__(256) task_kernel(const int64_t *__restrict__ o
             if (PASS == 0) record_error(err, kErrLength, q, m);
             continue;
         }
-        const int per = b < pp.nlane ? pp.lane_per_task : pp.warp_per_task;
+        // a slot-kernel query is one entry; the others split into tasks
+        const int per = b < pp.nlane ? pp.lane_per_task : b < 2 * pp.nlane ? c : pp.warp_per_task;
         const int parts = (c + per - 1) / per;
         if (PASS == 0) {
             atomicAdd(bcount + b, parts);
+            if (b >= pp.nlane && b < 2 * pp.nlane) atomicAdd(bsum + b, c);
         } else {
             const int base = sboff[b] + atomicAdd(bfill + b, parts);
             for (int i = 0; i < parts; ++i) tasks[base + i] = make_int2((int)q, i);
@@ -188,7 +201,7 @@ static int grid_for(int blocks) { return blocks < 1 ? 1 : blocks; }
 int64_t lev_workspace(int64_t P, int32_t n) {
     auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
     return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 2 + r(8 * (P + n + 1)) +
-           r(4 * kMaxBuckets) * 4;
+           r(4 * kMaxBuckets) * 5;
 }
 
 static PlanParams plan_params(const Registry &R, const Tune &T, int64_t P, int sm_count) {
@@ -198,6 +211,7 @@ static PlanParams plan_params(const Registry &R, const Tune &T, int64_t P, int s
     for (int b = 0; b < R.nlane; ++b) pp.lane_words[b] = R.lane[b].words;
     for (int b = 0; b < R.nwarp; ++b) pp.warp_words[b] = R.warp[b].words;
     pp.lane_min_targets = T.lane_min_targets;
+    pp.slot_min_targets = std::min(T.slot_min_targets, T.lane_min_targets);
     if (T.lane_per_task > 0) {
         pp.lane_per_task = T.lane_per_task;
     } else {
@@ -255,12 +269,13 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     int32_t *bfill = ar.take<int32_t>(kMaxBuckets);
     int32_t *boff = ar.take<int32_t>(kMaxBuckets);
     int32_t *bcounter = ar.take<int32_t>(kMaxBuckets);
-    if (!bcounter)
+    int32_t *bsum = ar.take<int32_t>(kMaxBuckets);
+    if (!bsum)
         return set_error(ctx, MSA_ENOMEM, "msa_lev_batch: needs %lld workspace bytes, context has %lld",
                          (long long)lev_workspace(P, n), (long long)ctx->ws_bytes);
     // the three per-query arrays are contiguous: one memset
     cudaError_t e = cudaMemsetAsync(qcount, 0, (char *)qstart - (char *)qcount, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bcount, 0, (char *)bcounter - (char *)bcount + 4 * kMaxBuckets, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bcount, 0, (char *)bsum - (char *)bcount + 4 * kMaxBuckets, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_batch memset");
 
     const int gP = grid_for((int)std::min<int64_t>((P + 255) / 256, ctx->sm_count * 8));
@@ -271,8 +286,8 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     scan_kernel<<<1, 1024, 0, st>>>(qcount, n, qstart);
     scatter_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
     const PlanParams pp = plan_params(R, T, P, ctx->sm_count);
-    task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
-    task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, ctx->dev_err);
+    task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, bsum, ctx->dev_err);
+    task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, bsum, ctx->dev_err);
 
     LevArgs a{};
     a.planes = s->planes;
@@ -286,6 +301,7 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     a.boff = boff;
     a.bcount = bcount;
     a.bcounter = bcounter;
+    a.bsum = bsum;
     a.d_out = d_out;
     a.err = ctx->dev_err;
     a.one = 1u;
@@ -308,9 +324,8 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     // uneven buckets do not leave the GPU idle one after another
     std::vector<int> launch_list;
     for (int b = 0; b < R.count(); ++b) {
-        const bool is_lane = b < R.nlane;
-        if (is_lane && b > lane_last) continue;
-        if (!is_lane && b - R.nlane > warp_last) continue;
+        if (b < 2 * R.nlane ? b % R.nlane > lane_last : b - 2 * R.nlane > warp_last) continue;
+        if (b >= R.nlane && b < 2 * R.nlane && pp.slot_min_targets >= pp.lane_min_targets) continue;
         launch_list.push_back(b);
     }
     ProfScope prof(ctx, st);
@@ -355,6 +370,28 @@ msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs
     return lev_run(ctx, s, pairs, P, d_out, (cudaStream_t)stream, nullptr, nullptr, nullptr);
 }
 
+msa_status msa_lev_tune_get(msa_ctx *ctx, int32_t *tune4) {
+    if (!ctx || !tune4) return MSA_EINVAL;
+    const Tune &T = *ctx->tune;
+    tune4[0] = T.lane_min_targets;
+    tune4[1] = T.slot_min_targets;
+    tune4[2] = T.lane_per_task;
+    tune4[3] = T.warp_per_task;
+    return MSA_OK;
+}
+
+msa_status msa_lev_tune_set(msa_ctx *ctx, const int32_t *tune4) {
+    if (!ctx || !tune4) return MSA_EINVAL;
+    if (tune4[0] == 0 || tune4[1] == 0 || tune4[3] == 0)
+        return set_error(ctx, MSA_EINVAL, "msa_lev_tune_set: zero target threshold or task size");
+    Tune &T = *ctx->tune;
+    if (tune4[0] > 0) T.lane_min_targets = tune4[0];
+    if (tune4[1] > 0) T.slot_min_targets = tune4[1];
+    if (tune4[2] >= 0) T.lane_per_task = tune4[2];
+    if (tune4[3] > 0) T.warp_per_task = tune4[3];
+    return MSA_OK;
+}
+
 msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
                             void *stream) {
     msa_status rc = lev_validate(ctx, s, pairs, P, d_out, "msa_lev_autotune");
@@ -364,17 +401,21 @@ msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pa
     Tune &T = *ctx->tune;
     const Tune keep = T;
     struct Cand {
-        int lane_min, lane_per, warp_per;
+        int lane_min, slot_min, lane_per, warp_per;
     };
-    const Cand cands[] = {{12, 0, 4},   {4, 0, 4},    {32, 0, 4},   {12, 64, 4},       {12, 128, 4},
-                          {12, 256, 4}, {12, 512, 4}, {12, 0, 1},   {12, 0, 16},  {1 << 30, 0, 4}};
+    // {1 << 30, 1 << 30, ...}: warp kernel only; slot_min >= lane_min: no slot kernel
+    const Cand cands[] = {{32, 2, 0, 4},   {16, 2, 0, 4},   {64, 2, 0, 4},   {32, 3, 0, 4},
+                          {12, 12, 0, 4},  {4, 4, 0, 4},    {32, 2, 64, 4},  {32, 2, 128, 4},
+                          {32, 2, 256, 4}, {32, 2, 512, 4}, {32, 2, 0, 1},   {32, 2, 0, 16},
+                          {1 << 30, 1 << 30, 0, 4}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    Cand pick = {keep.lane_min_targets, keep.lane_per_task, keep.warp_per_task};
+    Cand pick = {keep.lane_min_targets, keep.slot_min_targets, keep.lane_per_task, keep.warp_per_task};
     for (const Cand &c : cands) {
         T.lane_min_targets = c.lane_min;
+        T.slot_min_targets = c.slot_min;
         T.lane_per_task = c.lane_per;
         T.warp_per_task = c.warp_per;
         float ms_best = 1e30f;
@@ -396,6 +437,7 @@ msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pa
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     T.lane_min_targets = pick.lane_min;
+    T.slot_min_targets = pick.slot_min;
     T.lane_per_task = pick.lane_per;
     T.warp_per_task = pick.warp_per;
     if (rc) return rc;

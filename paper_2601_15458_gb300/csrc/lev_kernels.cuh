@@ -42,6 +42,7 @@ struct LevArgs {
     const int32_t *boff;      // [NB] first task of each bucket
     const int32_t *bcount;    // [NB] tasks per bucket
     int32_t *bcounter;        // [NB] tasks handed out per bucket
+    const int32_t *bsum;      // [NB] targets per bucket (slot kernels)
     int32_t *d_out;
     int32_t *err;
     int32_t bucket;
@@ -162,6 +163,13 @@ __device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv,
 // symbols never conflict; lanes reading the same symbol share a broadcast).
 __host__ __device__ constexpr int lane_peq_stride(int WC) {
     return ((WC + 3) / 4 * 4) % 8 == 0 ? (WC + 3) / 4 * 4 + 4 : (WC + 3) / 4 * 4;
+}
+
+// shared memory of one warp of the lane kernel, in words: SLOTS mask tables
+// and, with several slots, 4 * SLOTS + 4 words of slot bookkeeping (a
+// multiple of 4, so every table stays 16-byte aligned)
+__host__ __device__ constexpr int lane_smem_words(int WC, int SIGMA, int SLOTS) {
+    return SLOTS * lane_peq_stride(WC) * SIGMA + (SLOTS > 1 ? 4 * SLOTS + 4 : 0);
 }
 
 // One column over WC words, in chunks of up to 8 words: the chunk's
@@ -325,6 +333,10 @@ __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
 // Match masks of the query live in shared memory, layout [c][k] with a padded
 // stride (lane_peq_stride), read 4 words per load.  Pv/Mv: WC words in
 // registers.
+// SLOTS > 1 gives a warp up to SLOTS queries with few targets each, the
+// masks of all of them in shared memory: lane l takes targets l, l + 32, ...
+// of the concatenated target lists, so a batch of queries with 2..31 targets
+// keeps the lanes busy, where a warp per query would leave most of them idle.
 // ---------------------------------------------------------------------------
 #ifndef MSA_LANE_MINB
 #define MSA_LANE_MINB 1
@@ -332,31 +344,89 @@ __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
 // MSA_LANE_MINB = 4 caps registers for 4 resident blocks (16 warps per SM)
 // where the bit vectors still fit (up to 52 words); measured slower than the
 // uncapped build (53.6-54.7 vs 55.9 TCUPS on 2,000 x 1,500 all pairs)
-template <int WC, int B, int SIGMA>
+template <int WC, int B, int SIGMA, int SLOTS = 1>
 __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_kernel(LevArgs a) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
     constexpr int S = lane_peq_stride(WC);
-    uint32_t *sPeq = smem + (threadIdx.x >> 5) * (S * SIGMA);
+    // per warp: SLOTS mask tables, then (SLOTS > 1) the slots' query, first
+    // sorted target, length and prefix sums of their target counts
+    uint32_t *sPeq = smem + (threadIdx.x >> 5) * lane_smem_words(WC, SIGMA, SLOTS);
+    int32_t *sQ = (int32_t *)(sPeq + SLOTS * S * SIGMA);
+    int32_t *sBeg = sQ + SLOTS, *sM = sBeg + SLOTS, *sPre = sM + SLOTS;
     const uint32_t one = a.one, two = a.two;
-    const int ntasks = a.bcount[a.bucket];
+    const int nent = a.bcount[a.bucket];
+    // queries per warp: as many as make about 32 targets (one per lane, so
+    // no lane runs two targets one after another), 32 / (mean targets per
+    // query), and all SLOTS once the bucket gives every resident warp that
+    // many anyway (then lanes kept busy matter more than the length of one
+    // warp's work)
+    int ns = 1;
+    if constexpr (SLOTS > 1) {
+        const int resident = gridDim.x * (blockDim.x >> 5);
+        const long long tot = max(1, a.bsum[a.bucket]);
+        const long long per = 32ll * nent / tot;
+        const int one_round = per < SLOTS ? (int)per : SLOTS;
+        ns = max(1, max(one_round, min(SLOTS, nent / resident)));
+    }
+    const int ntasks = (nent + ns - 1) / ns;
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
 
     for (int task = next_task(counter, lane); task < ntasks; task = next_task(counter, lane)) {
-        const int q = tasks[task].x;
-        const int64_t qpos = a.offs[q];
-        const int m = (int)(a.offs[q + 1] - qpos);
+        int q = -1, m = 0, cbeg = 0, cnt = 0, total = 0;
+        const uint32_t *peq = sPeq;
         __syncwarp();
-        for (int k = lane; k < WC; k += 32) {
-            uint32_t pl[B], mask;
-            query_planes<B>(a.planes, qpos, m, k, pl, mask);
+        if constexpr (SLOTS == 1) {
+            q = tasks[task].x;
+            const int64_t qpos = a.offs[q];
+            m = (int)(a.offs[q + 1] - qpos);
+            for (int k = lane; k < WC; k += 32) {
+                uint32_t pl[B], mask;
+                query_planes<B>(a.planes, qpos, m, k, pl, mask);
 #pragma unroll
-            for (int c = 0; c < SIGMA; ++c) sPeq[c * S + k] = match_mask<B, SIGMA>(pl, mask, c);
+                for (int c = 0; c < SIGMA; ++c) sPeq[c * S + k] = match_mask<B, SIGMA>(pl, mask, c);
+            }
+            cbeg = a.qstart[q];
+            cnt = a.qstart[q + 1] - cbeg;
+        } else {
+            // lane i < ns reads slot i; a slot past ns or the bucket's end is empty
+            int cq = -1, cc = 0, cb = 0, cm = 0;
+            const int ent = task * ns + lane;
+            if (lane < ns && ent < nent) {
+                cq = tasks[ent].x;
+                cb = a.qstart[cq];
+                cc = a.qstart[cq + 1] - cb;
+                cm = (int)(a.offs[cq + 1] - a.offs[cq]);
+            }
+            int incl = cc;
+#pragma unroll
+            for (int o = 1; o < SLOTS; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < SLOTS) {
+                sQ[lane] = cq;
+                sBeg[lane] = cb;
+                sM[lane] = cm;
+                sPre[lane + 1] = incl;
+            }
+            if (lane == 0) sPre[0] = 0;
+            total = __shfl_sync(kFull, incl, SLOTS - 1);
+            __syncwarp();
+            for (int t = lane; t < SLOTS * WC; t += 32) {
+                const int sl = t / WC, k = t - sl * WC;
+                const int qs = sQ[sl];
+                if (qs < 0) continue;
+                const int64_t qpos = a.offs[qs];
+                uint32_t pl[B], mask;
+                query_planes<B>(a.planes, qpos, sM[sl], k, pl, mask);
+                uint32_t *dst = sPeq + sl * (S * SIGMA);
+#pragma unroll
+                for (int c = 0; c < SIGMA; ++c) dst[c * S + k] = match_mask<B, SIGMA>(pl, mask, c);
+            }
         }
         __syncwarp();
-        const int cbeg = a.qstart[q];
-        const int cnt = a.qstart[q + 1] - cbeg;
 
         // warp-synchronous stream: every iteration starts with a vote over
         // the whole warp, so lanes that switch targets rejoin the others
@@ -367,17 +437,29 @@ __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_
             Pv[k] = kFull;
             Mv[k] = 0u;
         }
-        int n = 0, j = 0, pid = -1, c_next = 0, c_next2 = 0;
+        int n = 0, j = 0, pid = -1, c_next = 0, c_next2 = 0, idx = lane;
         bool has = false, more = true;
         const uint8_t *tc = nullptr;
         while (true) {
             if (!has && more) {
-                const int idx = atomicAdd(a.qcursor + q, 1);
-                if (idx >= cnt) {
+                int pos = -1;
+                if constexpr (SLOTS == 1) {
+                    idx = atomicAdd(a.qcursor + q, 1);
+                    if (idx < cnt) pos = cbeg + idx;
+                } else if (idx < total) {
+                    int sl = 0;
+#pragma unroll
+                    for (int i = 1; i < SLOTS; ++i) sl += sPre[i] <= idx;
+                    pos = sBeg[sl] + idx - sPre[sl];
+                    m = sM[sl];
+                    peq = sPeq + sl * (S * SIGMA);
+                    idx += 32;
+                }
+                if (pos < 0) {
                     more = false;
                 } else {
-                    const int t = a.sorted_t[cbeg + idx];
-                    pid = a.sorted_p[cbeg + idx];
+                    const int t = a.sorted_t[pos];
+                    pid = a.sorted_p[pos];
                     const int64_t tp = a.offs[t];
                     n = (int)(a.offs[t + 1] - tp);
                     tc = a.codes + tp;
@@ -406,14 +488,14 @@ __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_
                     const int c0 = c_next, c1 = c_next2;
                     c_next = j + 2 < n ? __ldg(tc + j + 2) : 0;
                     c_next2 = j + 3 < n ? __ldg(tc + j + 3) : 0;
-                    lane_column_chain<WC>(sPeq + c0 * S, Pv, Mv, one, two);
-                    lane_column_chain<WC>(sPeq + c1 * S, Pv, Mv, one, two);
+                    lane_column_chain<WC>(peq + c0 * S, Pv, Mv, one, two);
+                    lane_column_chain<WC>(peq + c1 * S, Pv, Mv, one, two);
                     j += 2;
                 } else if (j < n) {
                     const int c = c_next;
                     c_next = c_next2;
                     c_next2 = j + 2 < n ? __ldg(tc + j + 2) : 0;
-                    const uint32_t *row = sPeq + c * S;
+                    const uint32_t *row = peq + c * S;
 #if MSA_LANE_CHAIN
                     lane_column_chain<WC>(row, Pv, Mv, one, two);
 #else
@@ -579,9 +661,9 @@ struct LevKernelInfo {
     const void *fn;
 };
 
-template <int WC, int B, int SIGMA>
+template <int WC, int B, int SIGMA, int SLOTS = 1>
 void launch_lane(const LevArgs &a, int grid, cudaStream_t st) {
-    lev_lane_kernel<WC, B, SIGMA><<<grid, 128, 4 * lane_peq_stride(WC) * SIGMA * sizeof(uint32_t), st>>>(a);
+    lev_lane_kernel<WC, B, SIGMA, SLOTS><<<grid, 128, 4 * lane_smem_words(WC, SIGMA, SLOTS) * sizeof(uint32_t), st>>>(a);
 }
 
 template <int WPL, int B, int SIGMA>
@@ -594,6 +676,12 @@ extern const LevKernelInfo kLevLaneDna[];
 extern const int kLevLaneDnaCount;
 extern const LevKernelInfo kLevLaneProt[];
 extern const int kLevLaneProtCount;
+// lane kernel with 8 queries per warp (4 lanes each)
+constexpr int kLevSlots = 8;
+extern const LevKernelInfo kLevSlotDna[];
+extern const int kLevSlotDnaCount;
+extern const LevKernelInfo kLevSlotProt[];
+extern const int kLevSlotProtCount;
 extern const LevKernelInfo kLevWarpDna[];
 extern const int kLevWarpDnaCount;
 extern const LevKernelInfo kLevWarpProt[];

@@ -92,6 +92,26 @@ def train(ctx: api.Context, X: torch.Tensor, y: torch.Tensor, epochs: float = 4.
     return model, info
 
 
+def calibrate(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof: torch.Tensor,
+              pairs: torch.Tensor, tau: float = 0.95):
+    """Fits the network's band calibration (``msa_band_calibrate``) on
+    held-out pairs: the network's outputs beside the exact full-DP distances.
+
+    The network is trained on pairs from simulated trees; on another
+    population its output is not the tau-quantile it was trained for (on the
+    divergent-pair evaluation recipe it runs high by 0.1 and more in y where
+    most of the band cost lies), and one global margin cannot fix a bias
+    that depends on yhat.  Returns the knots."""
+    yhat, _ = model.predict_band(seqs, prof, pairs, gamma=0.0, margin=0)
+    d = api.lev_batch(ctx, seqs, pairs)
+    lens = seqs.offs[1:] - seqs.offs[:-1]
+    mx = torch.maximum(lens[pairs[:, 0].long()], lens[pairs[:, 1].long()]).clamp(min=1)
+    y = (d.double() / mx.double()).float()
+    model.calibrate(yhat, y, tau=tau)
+    ctx.check()
+    return model.calibration()
+
+
 def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof: torch.Tensor,
                pairs: torch.Tensor, candidates=(-0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 2):
     """The band margin gamma with the fastest certified banded run on a
@@ -112,3 +132,24 @@ def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, pro
         if t < best_t:
             best, best_t = g, t
     return best, best_t
+
+
+def pick_band(ctx: api.Context, model: api.BandModel, cal_set, gamma_set, taus=(0.95, 0.99, 1.0),
+              candidates=(-0.1, -0.05, 0.0, 0.05, 0.1, 0.15, 0.2, 0.35), margin: int = 8):
+    """Calibration quantile tau and margin gamma together: for each tau the
+    calibration is fitted on ``cal_set`` and gamma picked by timing on
+    ``gamma_set`` (each a ``(seqs, prof, pairs)`` of held-out pairs, large
+    enough to fill the GPU, or the timing favours wide bands); the model is
+    left calibrated with the best tau.  Returns ``(tau, gamma, ms)``; tau
+    None is the network without calibration, when that is fastest."""
+    best = (None, *pick_gamma(ctx, model, *gamma_set, candidates=candidates, margin=margin))
+    for tau in taus:
+        calibrate(ctx, model, *cal_set, tau=tau)
+        g, t = pick_gamma(ctx, model, *gamma_set, candidates=candidates, margin=margin)
+        if t < best[2]:
+            best = (tau, g, t)
+    if best[0] is None:
+        model.calibrate(None, None)
+    else:
+        calibrate(ctx, model, *cal_set, tau=best[0])
+    return best

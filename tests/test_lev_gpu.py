@@ -72,6 +72,32 @@ def test_edge_lengths_both_kernels(ctx, alphabet):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("alphabet", ["dna", "protein"])
+def test_few_targets_per_query_slot_kernel(ctx, alphabet):
+    """Queries with 1..40 targets: single targets go to the warp kernel, 2..31
+    share warps in the slot kernel, 32+ take a warp each.  Query lengths span
+    several word counts; empty query and target; the number of queries per
+    bucket is not a multiple of the 8 a warp takes."""
+    rng = np.random.default_rng(11)
+    letters = np.frombuffer(synth.DNA if alphabet == "dna" else synth.PROTEIN, np.uint8)
+    lens = [0, 1, 17, 32, 33, 100, 250, 700, 1100, 1530, 2100]
+    seqs = [letters[rng.integers(0, len(letters), L)].tobytes() for L in lens]
+    for i in range(90):
+        L = int(rng.integers(1, 1600))
+        seqs.append(letters[rng.integers(0, len(letters), L)].tobytes())
+    n = len(seqs)
+    pairs = []
+    for q in range(n):
+        c = int(rng.integers(1, 41)) if q >= len(lens) else 3 + q
+        pairs += [[q, int(t)] for t in rng.integers(0, n, c)]
+    pairs += [[1, 0], [0, 5], [0, 0]]
+    pairs = np.array(pairs, np.int32)
+    got = _run(ctx, synth.SeqSet.from_list(seqs, alphabet), pairs)
+    ds = synth.SeqSet.from_list(seqs, alphabet)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_random_pairs_schedule_independent(ctx):
     ds = synth.tree_dna(seed=9, n=120, root_len=400)
     pairs = synth.random_pairs(5, ds.n, 3000)
@@ -81,6 +107,46 @@ def test_random_pairs_schedule_independent(ctx):
     ctx.check()
     np.testing.assert_array_equal(got.cpu().numpy(), ref)
     np.testing.assert_array_equal(api.lev_batch(ctx, seqs, pairs).cpu().numpy(), ref)
+
+
+def test_slot_kernel_full_warps(ctx):
+    """Enough few-target queries for 8 queries per warp (the bucket holds more
+    than 8 per resident warp: up to 16 blocks of 4 warps on each of 152 SMs
+    for these short queries), with a ragged last task."""
+    ds = synth.tree_dna(seed=13, n=90003, root_len=60)
+    rng = np.random.default_rng(13)
+    pairs = []
+    for q in range(ds.n):
+        c = int(rng.integers(2, 12))
+        pairs += [[q, int(t)] for t in rng.integers(0, ds.n, c)]
+    pairs = np.array(pairs, np.int32)
+    seqs = api.upload_and_pack(ctx, ds)
+    got = api.lev_batch(ctx, seqs, pairs).cpu().numpy()
+    ctx.check()
+    np.testing.assert_array_equal(got, oracle.lev_pairs(ds.arena, ds.offs, pairs))
+
+
+def test_explicit_schedules_same_distances(ctx):
+    """Every schedule gives the oracle's distances: slot kernel on and off,
+    other thresholds, small tasks; the schedule in force is restored."""
+    ds = synth.tree_dna(seed=12, n=300, root_len=700)
+    pairs = synth.random_pairs(6, ds.n, 2500)             # ~8 targets per query
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    seqs = api.upload_and_pack(ctx, ds)
+    keep = api.lev_schedule(ctx)
+    try:
+        for sched in [dict(lane_min_targets=32, slot_min_targets=2), dict(lane_min_targets=12, slot_min_targets=12),
+                      dict(lane_min_targets=4, slot_min_targets=3), dict(lane_min_targets=1 << 30, slot_min_targets=1 << 30),
+                      dict(lane_min_targets=1 << 30, slot_min_targets=1), dict(lane_per_task=32, warp_per_task=1)]:
+            got = api.lev_schedule(ctx, **sched)
+            for k, v in sched.items():
+                assert got[k] == v
+            np.testing.assert_array_equal(api.lev_batch(ctx, seqs, pairs).cpu().numpy(), ref, err_msg=str(sched))
+        with pytest.raises(api.MsaError):
+            api.lev_schedule(ctx, warp_per_task=0)
+    finally:
+        api.lev_schedule(ctx, **keep)
+    ctx.check()
 
 
 def test_protein_families_to_centers_sample(ctx):

@@ -173,3 +173,59 @@ def test_band_policy_and_learned_gain(ctx):
     t_l1 = timed(lambda: api.lev_banded_batch(ctx, sq, pt, k_l1))
     t_band = timed(lambda: api.lev_banded_batch(ctx, sq, pt, k))
     assert t_band < t_l1, (t_band, t_l1)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.9, 0.95, 1.0])
+def test_band_calibration_knots_exact(ctx, tau):
+    """The knots of msa_band_calibrate equal the oracle's bit for bit: dense
+    and sparse bins (16 and 15 pairs), ties, outputs outside [0, 1], y
+    clamped, bin-edge outputs."""
+    rng = np.random.default_rng(int(tau * 100))
+    N = 40000
+    yhat = rng.uniform(-0.1, 0.7, N).astype(np.float32)
+    y = np.clip(yhat * 0.75 + rng.normal(0, 0.04, N), -0.05, 1.05).astype(np.float32)
+    y[::7] = np.round(y[::7], 2)                                  # ties
+    yhat[:16] = 0.8                                               # bin 26: exactly 16 pairs
+    yhat[16:31] = 0.9                                             # bin 29: 15 pairs
+    yhat[31:40] = 1.3                                             # above 1: bin 32
+    yhat[40:60] = np.nextafter(np.float32(12.5 / 32), np.float32(0))
+    model = api.BandModel(ctx, seed=0)
+    assert model.calibration() is None
+    model.calibrate(torch.from_numpy(yhat).cuda(), torch.from_numpy(y).cuda(), tau=tau)
+    got = model.calibration()
+    ctx.check()
+    np.testing.assert_array_equal(got, oracle.band_calibrate(yhat, y, tau))
+
+
+def test_band_predict_with_calibration(ctx):
+    """With a calibration in the state, msa_band_predict's band equals the
+    oracle's calibrated policy on the same outputs; removing it gives back the
+    plain policy; the banded distances stay exact."""
+    ds = synth.divergent_pairs(seed=44, n_pairs=3000, len_lo=500, len_hi=3000, div_lo=0.01, div_hi=0.30)
+    sq = api.upload_and_pack(ctx, ds)
+    prof = api.kmer_profile(ctx, sq)
+    pairs = np.stack([np.arange(0, ds.n, 2), np.arange(1, ds.n, 2)], 1).astype(np.int32)
+    pt = torch.from_numpy(pairs).cuda()
+    model = api.BandModel(ctx, seed=3)
+    lens = np.diff(ds.offs)
+    la, lb = lens[pairs[:, 0]], lens[pairs[:, 1]]
+    yhat0, k0 = model.predict_band(sq, prof, pt, gamma=0.05, margin=8)
+    # an arbitrary monotone map fitted from made-up targets
+    rng = np.random.default_rng(2)
+    yh = yhat0.cpu().numpy()
+    yt = np.clip(rng.random(yh.size) * 0.4, 0, 1).astype(np.float32)
+    model.calibrate(yhat0, torch.from_numpy(yt).cuda(), tau=0.9)
+    knots = model.calibration()
+    yhat1, k1 = model.predict_band(sq, prof, pt, gamma=0.05, margin=8)
+    ctx.check()
+    np.testing.assert_array_equal(yhat1.cpu().numpy(), yh)
+    np.testing.assert_array_equal(k1.cpu().numpy(), oracle.band_policy(yh, la, lb, 0.05, 8, knots=knots))
+    d_full = api.lev_batch(ctx, sq, pt)
+    d_band, _ = api.lev_banded_batch(ctx, sq, pt, k1)
+    np.testing.assert_array_equal(d_band.cpu().numpy(), d_full.cpu().numpy())
+    model.calibrate(None, None)
+    _, k2 = model.predict_band(sq, prof, pt, gamma=0.05, margin=8)
+    np.testing.assert_array_equal(k2.cpu().numpy(), k0.cpu().numpy())
+    np.testing.assert_array_equal(k0.cpu().numpy(), oracle.band_policy(yh, la, lb, 0.05, 8))
+    with pytest.raises(api.MsaError):
+        model.calibrate(yhat0, torch.from_numpy(yt).cuda(), tau=0.0)

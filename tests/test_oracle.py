@@ -412,3 +412,65 @@ def test_nw_affine_closed_forms():
     assert oracle.nw_affine(b"AAACCCGGG", b"AAAGGG", 0, 5, 10, 1) == (13, b"MMMDDDMMM")
     assert oracle.nw_affine(b"ACGT", b"AGGT", 0, 1, 10, 1) == (1, b"MXMM")
     assert oracle.nw_affine(b"", b"ACG", 0, 1, 10, 1) == (13, b"III")
+
+
+# ---------------------------------------------------------------------------
+# band policy and calibration
+# ---------------------------------------------------------------------------
+
+def test_band_policy_hand_examples():
+    # gamma 0, yhat 0.25, lengths 1000/900: ceil(0.25 * 1000) + 8 = 258
+    assert oracle.band_policy([0.25], [1000], [900], 0.0, 8)[0] == 258
+    # the length difference dominates: max(500, ceil(0.01 * 1000) + 8)
+    assert oracle.band_policy([0.01], [1000], [500], 0.0, 8)[0] == 500
+    # negative outputs count as 0
+    assert oracle.band_policy([-0.3], [64], [64], 0.5, 3)[0] == 3
+
+
+def test_calibration_quantile_is_inverted_cdf():
+    rng = np.random.default_rng(3)
+    y = rng.random(1001).astype(np.float32)
+    yhat = np.full(1001, 0.25, np.float32)            # every pair in bin 8
+    for tau in (0.5, 0.9, 0.95, 1.0):
+        knots = oracle.band_calibrate(yhat, y, tau)
+        q = np.float32(np.quantile(y.astype(np.float64), tau, method="inverted_cdf"))
+        assert knots[8] == q
+        # bins 0..7 keep the identity, later bins the running maximum
+        np.testing.assert_array_equal(knots[:8], np.arange(8, dtype=np.float32) / 32)
+        np.testing.assert_array_equal(knots[9:], np.maximum(np.arange(9, 33, dtype=np.float32) / 32, q))
+
+
+def test_calibration_sparse_bins_identity_and_monotone():
+    rng = np.random.default_rng(4)
+    yhat = rng.random(20000).astype(np.float32) * 0.6
+    y = np.clip(yhat * 0.7 + rng.normal(0, 0.03, 20000), 0, None).astype(np.float32)
+    yhat[:15] = 0.95                                  # 15 pairs in bin 30: too few
+    knots = oracle.band_calibrate(yhat, y, 0.9)
+    assert np.all(np.diff(knots) >= 0)
+    assert knots[30] == max(np.float32(30) / 32, knots[29])
+    # where the network runs high, the fitted map lies below the identity
+    assert knots[16] < np.float32(16) / 32
+    # bin edges: yhat just below (i + 0.5) / 32 belongs to bin i
+    yb = np.array([np.nextafter(np.float32(8.5 / 32), np.float32(0))] * 16 + [np.float32(8.5 / 32)] * 16, np.float32)
+    vals = np.array([0.5] * 16 + [0.7] * 16, np.float32)
+    kb = oracle.band_calibrate(yb, vals, 1.0)
+    assert kb[8] == np.float32(0.5) and kb[9] == np.float32(0.7)
+
+
+def test_calibrated_policy_reductions():
+    # identity knots reproduce the uncalibrated policy exactly on [0, 1]
+    ident = np.arange(33, dtype=np.float32) / 32
+    rng = np.random.default_rng(5)
+    yhat = rng.uniform(-0.2, 1.0, 5000).astype(np.float32)
+    la = rng.integers(1, 20000, 5000)
+    lb = rng.integers(1, 20000, 5000)
+    np.testing.assert_array_equal(oracle.band_policy(yhat, la, lb, 0.1, 8, knots=ident),
+                                  oracle.band_policy(yhat, la, lb, 0.1, 8))
+    # at a knot the map returns the knot; halfway between two it returns their mean
+    knots = np.sort(rng.random(33).astype(np.float32))
+    at = np.arange(33, dtype=np.float32) / 32
+    np.testing.assert_array_equal(oracle.band_calibrated(knots, at), knots)
+    mid = (np.arange(32, dtype=np.float32) + np.float32(0.5)) / 32
+    np.testing.assert_allclose(oracle.band_calibrated(knots, mid), (knots[:-1] + knots[1:]) / 2, rtol=1e-6)
+    # outputs above 1 use the last knot
+    assert oracle.band_calibrated(knots, np.array([1.7], np.float32))[0] == knots[32]
