@@ -92,8 +92,9 @@ def make_workload(n):
     return ds, pairs, cells, words
 
 
-def cpu_oracle_sample(ds, pairs, seconds, seed=7):
-    """Time the oracle on a seeded sample of pairs sized to about `seconds`."""
+def cpu_oracle_sample(ds, pairs, seconds, seed=7, single=True):
+    """Time the oracle on a seeded sample of pairs sized to about `seconds`
+    on all host cores, and (single) on one thread over part of it."""
     import oracle
     threads = oracle.cpu_threads()
     rng = np.random.default_rng(seed)
@@ -109,8 +110,20 @@ def cpu_oracle_sample(ds, pairs, seconds, seed=7):
     oracle.lev_pairs(ds.arena, ds.offs, sample, nthreads=threads)
     dt = time.perf_counter() - t0
     cells = int((lens[sample[:, 0]].astype(np.int64) * lens[sample[:, 1]]).sum())
-    return dict(value=cells / dt / 1e9, unit="GCUPS", cores=threads, kind="oracle",
-                sample=f"{k} random pairs of the workload ({cells:.3e} cells, {dt:.1f} s)"), cells, dt
+    info = dict(value=cells / dt / 1e9, unit="GCUPS", cores=threads, kind="oracle",
+                sample=f"{k} random pairs of the workload ({cells:.3e} cells, {dt:.1f} s)")
+    if not single:
+        return info, cells, dt
+    # the same oracle on one thread, over a sample of about a fifth of the time
+    k1 = int(max(1, min(len(pairs), seconds / 5 / max(per_pair * threads, 1e-9))))
+    s1 = sample[:k1]
+    t0 = time.perf_counter()
+    oracle.lev_pairs(ds.arena, ds.offs, s1, nthreads=1)
+    dt1 = time.perf_counter() - t0
+    cells1 = int((lens[s1[:, 0]].astype(np.int64) * lens[s1[:, 1]]).sum())
+    info["single_thread"] = dict(value=cells1 / dt1 / 1e9, unit="GCUPS", cores=1,
+                                 sample=f"the first {k1} of those pairs ({cells1:.3e} cells, {dt1:.1f} s)")
+    return info, cells, dt
 
 
 class ClockSampler:
@@ -362,7 +375,7 @@ def run_reference(args, rank, world):
     total_t = 0.0
     info = None
     for s in range(args.warmup + args.steps):
-        info, c, dt = cpu_oracle_sample(ds, pairs, per_step, seed=100 + s)
+        info, c, dt = cpu_oracle_sample(ds, pairs, per_step, seed=100 + s, single=False)
         if s >= args.warmup:
             vals.append(info["value"])
             total_cells += c

@@ -124,6 +124,19 @@ msa_status msa_pack(msa_ctx *ctx, const msa_seqset *s, void *stream);
 msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
                          int64_t P, int32_t *d_out, void *stream);
 
+/*
+ * d_out[i] = f(seq[query], seq[idx[i]]) for i < n: one query against many
+ * targets, the batch shape of Alg. 1's c, l and r distances (the query's
+ * match masks are built once per warp and shared by its lanes).  idx: device
+ * int32 [n]; an index outside [0, n_seqs) is reported as MSA_EDATA by
+ * msa_ctx_check, query outside it as MSA_EINVAL.  Same kernels and results as
+ * msa_lev_batch on the pairs (query, idx[i]).  Needs
+ * msa_lev_one_to_many_workspace_bytes(n, n_seqs) of workspace.
+ */
+msa_status msa_lev_one_to_many(msa_ctx *ctx, const msa_seqset *s, int32_t query, const int32_t *idx, int64_t n,
+                               int32_t *d_out, void *stream);
+int64_t msa_lev_one_to_many_workspace_bytes(int64_t n, int32_t n_seqs);
+
 /* Selects the kernel schedule of msa_lev_batch (the target-count thresholds
  * between the kernels, targets per task) by running this batch under each
  * candidate and timing it with CUDA events; the fastest is kept in ctx for

@@ -65,6 +65,9 @@ SIGNATURES = {
     "msa_mlp_read_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "msa_band_predict": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int64,
                                    c_float, c_int32, c_void_p, c_void_p, c_void_p]),
+    "msa_lev_one_to_many": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_int32, c_void_p, c_int64, c_void_p,
+                                      c_void_p]),
+    "msa_lev_one_to_many_workspace_bytes": (c_int64, [c_int64, c_int32]),
     "msa_lev_tune_get": (c_int32, [c_void_p, c_void_p]),
     "msa_lev_tune_set": (c_int32, [c_void_p, c_void_p]),
     "msa_band_calibrate": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_void_p]),

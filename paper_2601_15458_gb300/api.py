@@ -152,6 +152,21 @@ def lev_batch(ctx: Context, seqs: DeviceSeqs, pairs, out: torch.Tensor | None = 
     return out
 
 
+def lev_one_to_many(ctx: Context, seqs: DeviceSeqs, query: int, idx, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Distances from sequence ``query`` to every sequence of ``idx``
+    (msa_lev_one_to_many); int32 [n]."""
+    if not isinstance(idx, torch.Tensor):
+        idx = torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int32))
+    idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+    n = idx.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=idx.device)
+    ctx.raise_if(_lib.lib().msa_lev_one_to_many(ctx.handle, ctypes.byref(seqs.c), int(query), _ptr(idx), n,
+                                                _ptr(out), _stream(stream)))
+    return out
+
+
 def lev_banded_batch(ctx: Context, seqs: DeviceSeqs, pairs, k0, out: torch.Tensor | None = None,
                      k_used: torch.Tensor | None = None, stream=None):
     """A4: exact distances by certified Ukkonen bands starting at ``k0``.

@@ -198,6 +198,15 @@ __global__ void __launch_bounds__(256) task_kernel(const int64_t *__restrict__ o
 
 static int grid_for(int blocks) { return blocks < 1 ? 1 : blocks; }
 
+// pairs (query, idx[i]) of a one-to-many batch
+__global__ void __launch_bounds__(256) one_to_many_pairs_kernel(int32_t query, const int32_t *__restrict__ idx,
+                                                                int64_t n, int32_t *__restrict__ pairs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        pairs[2 * i] = query;
+        pairs[2 * i + 1] = idx[i];
+    }
+}
+
 int64_t lev_workspace(int64_t P, int32_t n) {
     auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
     return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 2 + r(8 * (P + n + 1)) +
@@ -368,6 +377,28 @@ msa_status msa_lev_batch(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs
     if (rc || P == 0) return rc;
     if (s->n_seqs == 0) return set_error(ctx, MSA_EINVAL, "msa_lev_batch: pairs given for an empty set");
     return lev_run(ctx, s, pairs, P, d_out, (cudaStream_t)stream, nullptr, nullptr, nullptr);
+}
+
+int64_t msa_lev_one_to_many_workspace_bytes(int64_t n, int32_t n_seqs) {
+    return ((8 * n + 255) & ~int64_t(255)) + lev_workspace(n, n_seqs);
+}
+
+msa_status msa_lev_one_to_many(msa_ctx *ctx, const msa_seqset *s, int32_t query, const int32_t *idx, int64_t n,
+                               int32_t *d_out, void *stream) {
+    msa_status rc = lev_validate(ctx, s, idx, n, d_out, "msa_lev_one_to_many");
+    if (rc || n == 0) return rc;
+    if (query < 0 || query >= s->n_seqs)
+        return set_error(ctx, MSA_EINVAL, "msa_lev_one_to_many: query %d outside [0, %d)", query, s->n_seqs);
+    const cudaStream_t st = (cudaStream_t)stream;
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    int32_t *pairs = ar.take<int32_t>(2 * n);
+    if (!pairs || ar.cap - ar.used < lev_workspace(n, s->n_seqs))
+        return set_error(ctx, MSA_ENOMEM, "msa_lev_one_to_many: needs %lld workspace bytes, context has %lld",
+                         (long long)msa_lev_one_to_many_workspace_bytes(n, s->n_seqs), (long long)ctx->ws_bytes);
+    const int g = grid_for((int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8));
+    one_to_many_pairs_kernel<<<g, 256, 0, st>>>(query, idx, n, pairs);
+    ++ctx->launches;
+    return lev_run(ctx, s, pairs, n, d_out, st, nullptr, nullptr, &ar);
 }
 
 msa_status msa_lev_tune_get(msa_ctx *ctx, int32_t *tune4) {

@@ -35,7 +35,7 @@ namespace noalloc {
 
 constexpr int64_t kMaxPairs = int64_t(1) << 18;   // 262,144 pairs per call
 constexpr int32_t kMaxSeqs = int32_t(1) << 16;    // 65,536 sequences in the set
-constexpr int kNB = 64;                           // kernel buckets (>= lane + warp configurations)
+constexpr int kNB = 64;                           // kernel buckets (>= 2 x lane + warp configurations)
 constexpr int kMaxDevices = 64;
 
 struct Scratch {
@@ -50,6 +50,7 @@ struct Scratch {
     int32_t bfill[kNB];
     int32_t boff[kNB];
     int32_t bcounter[kNB];
+    int32_t bsum[kNB];
     int32_t err[4];
 };
 
@@ -111,19 +112,24 @@ __global__ void na_scatter(Scratch *S, const int32_t *__restrict__ pairs, int64_
     }
 }
 
+// buckets [lane | slot | warp], the default schedule of msa_lev_batch: a warp
+// per query from 32 targets, shared warps (slot kernel) from 2, the
+// warp-per-pair kernel for single targets and long queries
 __device__ __forceinline__ int na_bucket(const Plan &pl, int W, int c) {
-    if (W <= pl.lane_words[pl.nlane - 1] && c >= 12)
+    if (W <= pl.lane_words[pl.nlane - 1] && c >= 2) {
+        const int base = c >= 32 ? 0 : pl.nlane;
         for (int b = 0; b < pl.nlane; ++b)
-            if (pl.lane_words[b] >= W) return b;
+            if (pl.lane_words[b] >= W) return base + b;
+    }
     for (int b = 0; b < pl.nwarp; ++b)
-        if (32 * pl.warp_words[b] >= W) return pl.nlane + b;
+        if (32 * pl.warp_words[b] >= W) return 2 * pl.nlane + b;
     return -1;
 }
 
 template <int PASS>
 __global__ void __launch_bounds__(256) na_tasks(Scratch *S, const int64_t *__restrict__ offs, int32_t n, Plan pl) {
     __shared__ int32_t sboff[kNB];
-    const int NB = pl.nlane + pl.nwarp;
+    const int NB = 2 * pl.nlane + pl.nwarp;
     if (PASS == 1) {
         if (threadIdx.x == 0) {
             int run = 0;
@@ -141,15 +147,26 @@ __global__ void __launch_bounds__(256) na_tasks(Scratch *S, const int64_t *__res
         const int m = (int)(offs[q + 1] - offs[q]);
         const int b = na_bucket(pl, max(1, (m + 31) / 32), c);
         if (b < 0) continue;   // too long for the kernels: its pairs keep d_out = -1
-        const int per = b < pl.nlane ? pl.lane_per_task : 4;
+        const int per = b < pl.nlane ? pl.lane_per_task : b < 2 * pl.nlane ? c : 4;
         const int parts = (c + per - 1) / per;
         if (PASS == 0) {
             atomicAdd(&S->bcount[b], parts);
+            if (b >= pl.nlane && b < 2 * pl.nlane) atomicAdd(&S->bsum[b], c);
         } else {
             const int base = sboff[b] + atomicAdd(&S->bfill[b], parts);
             for (int i = 0; i < parts; ++i) S->tasks[base + i] = make_int2((int)q, i);
         }
     }
+}
+
+// Kernel of bucket b: lane kernels, then the same word counts with 8 query
+// slots, then the warp-per-pair kernels.
+static const LevKernelInfo &kernel_at(int alphabet, int b) {
+    const bool dna = alphabet == MSA_DNA;
+    const int nl = dna ? kLevLaneDnaCount : kLevLaneProtCount;
+    if (b < nl) return (dna ? kLevLaneDna : kLevLaneProt)[b];
+    if (b < 2 * nl) return (dna ? kLevSlotDna : kLevSlotProt)[b - nl];
+    return (dna ? kLevWarpDna : kLevWarpProt)[b - 2 * nl];
 }
 
 // Per-device set-up: the scratch address, SM count and kernel occupancies.
@@ -173,13 +190,12 @@ static msa_status setup(int dev, int alphabet, DeviceInfo **out) {
         d.scratch = static_cast<Scratch *>(ptr);
         d.ready = true;
     }
-    const LevKernelInfo *lane = alphabet == MSA_DNA ? kLevLaneDna : kLevLaneProt;
-    const LevKernelInfo *warp = alphabet == MSA_DNA ? kLevWarpDna : kLevWarpProt;
     const int nl = alphabet == MSA_DNA ? kLevLaneDnaCount : kLevLaneProtCount;
     const int nw = alphabet == MSA_DNA ? kLevWarpDnaCount : kLevWarpProtCount;
-    for (int b = 0; b < nl + nw; ++b) {
+    if (2 * nl + nw > kNB) return MSA_EUNSUPPORTED;
+    for (int b = 0; b < 2 * nl + nw; ++b) {
         if (d.occ[alphabet][b] > 0) continue;
-        const LevKernelInfo &K = b < nl ? lane[b] : warp[b - nl];
+        const LevKernelInfo &K = kernel_at(alphabet, b);
         const size_t smem = K.smem_per_warp * 4;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -215,7 +231,7 @@ extern "C" msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *
     const int32_t n = s->n_seqs;
     // the scratch keeps the last call's contents: clear what must start at zero
     if (cudaMemsetAsync(S->qcount, 0, sizeof(int32_t) * 3 * kMaxSeqs, st) != cudaSuccess ||
-        cudaMemsetAsync(S->bcount, 0, sizeof(int32_t) * 4 * kNB, st) != cudaSuccess ||
+        cudaMemsetAsync(S->bcount, 0, sizeof(int32_t) * 5 * kNB, st) != cudaSuccess ||
         cudaMemsetAsync(d_out, 0xff, sizeof(int32_t) * P, st) != cudaSuccess)
         return MSA_ECUDA;
     const int gP = (int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, D->sm_count * 8));
@@ -247,18 +263,20 @@ extern "C" msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *
     a.boff = S->boff;
     a.bcount = S->bcount;
     a.bcounter = S->bcounter;
+    a.bsum = S->bsum;
     a.d_out = d_out;
     a.err = S->err;
     a.one = 1u;
     a.two = 2u;
     const int Wmax = std::max(1, (s->max_len + 31) / 32);
-    for (int b = 0; b < pl.nlane + pl.nwarp; ++b) {
-        const bool is_lane = b < pl.nlane;
-        const LevKernelInfo &K = is_lane ? lane[b] : warp[b - pl.nlane];
+    for (int b = 0; b < 2 * pl.nlane + pl.nwarp; ++b) {
+        const bool is_warp = b >= 2 * pl.nlane;
+        const int first = is_warp ? 2 * pl.nlane : (b < pl.nlane ? 0 : pl.nlane);
+        const LevKernelInfo &K = kernel_at(s->alphabet, b);
         // a bucket whose smaller neighbour already holds the longest sequence is never used
-        if (b > 0 && b != pl.nlane) {
-            const LevKernelInfo &prev = is_lane ? lane[b - 1] : warp[b - pl.nlane - 1];
-            const int cap_prev = is_lane ? prev.words : 32 * prev.words;
+        if (b > first) {
+            const LevKernelInfo &prev = kernel_at(s->alphabet, b - 1);
+            const int cap_prev = is_warp ? 32 * prev.words : prev.words;
             if (cap_prev >= Wmax) continue;
         }
         a.bucket = b;

@@ -126,6 +126,29 @@ def test_slot_kernel_full_warps(ctx):
     np.testing.assert_array_equal(got, oracle.lev_pairs(ds.arena, ds.offs, pairs))
 
 
+@pytest.mark.parametrize("alphabet", ["dna", "protein"])
+def test_one_to_many(ctx, alphabet):
+    """msa_lev_one_to_many equals the oracle for a query against repeated,
+    empty and long targets; bad indices are reported; n = 0 is a no-op."""
+    rng = np.random.default_rng(21)
+    letters = np.frombuffer(synth.DNA if alphabet == "dna" else synth.PROTEIN, np.uint8)
+    seqs = [letters[rng.integers(0, len(letters), L)].tobytes() for L in (700, 0, 1, 2049, 64, 1500)]
+    seqs += [letters[rng.integers(0, len(letters), int(rng.integers(1, 1800)))].tobytes() for _ in range(300)]
+    ds = synth.SeqSet.from_list(seqs, alphabet)
+    sq = api.upload_and_pack(ctx, ds)
+    for q, idx in [(0, np.arange(ds.n)), (1, np.array([0, 1, 3, 3, 3])), (3, rng.integers(0, ds.n, 5000))]:
+        got = api.lev_one_to_many(ctx, sq, q, idx).cpu().numpy()
+        ctx.check()
+        pairs = np.stack([np.full(len(idx), q), idx], 1).astype(np.int32)
+        np.testing.assert_array_equal(got, oracle.lev_pairs(ds.arena, ds.offs, pairs))
+    assert api.lev_one_to_many(ctx, sq, 0, np.zeros(0, np.int32)).numel() == 0
+    with pytest.raises(api.MsaError):
+        api.lev_one_to_many(ctx, sq, ds.n, np.array([0], np.int32))
+    api.lev_one_to_many(ctx, sq, 0, np.array([1, ds.n + 5], np.int32))
+    with pytest.raises(api.MsaError):
+        ctx.check()
+
+
 def test_explicit_schedules_same_distances(ctx):
     """Every schedule gives the oracle's distances: slot kernel on and off,
     other thresholds, small tasks; the schedule in force is restored."""

@@ -49,7 +49,7 @@ def test_noalloc_matches_lev_batch_two_calls(ctx, alphabet):
         ds = synth.protein_families(seed=3, n_fam=6, per_fam=40)[0]
     seqs = api.upload_and_pack(ctx, ds)
     calls = [torch.from_numpy(synth.all_pairs(ds.n)).cuda(),            # one-to-many: lane kernels
-             torch.from_numpy(synth.random_pairs(14, ds.n, 5000)).cuda()]  # few targets per query: warp kernels
+             torch.from_numpy(synth.random_pairs(14, ds.n, 5000)).cuda()]  # few targets per query: slot and warp kernels
     for pairs in calls:
         ref = api.lev_batch(ctx, seqs, pairs)
         ctx.check()
