@@ -46,6 +46,16 @@ def case_lev(ctx):
     return _time(lambda: api.lev_batch(ctx, sq, pairs, out))
 
 
+def case_lev_few(ctx):
+    """20,000 DNA sequences of ~1,500, 100,000 random pairs: ~5 targets per
+    query, the slot kernel's batch shape."""
+    ds = synth.tree_dna(seed=3, n=20000)
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = torch.from_numpy(synth.random_pairs(7, ds.n, 100000)).cuda()
+    out = torch.empty(pairs.shape[0], dtype=torch.int32, device="cuda")
+    return _time(lambda: api.lev_batch(ctx, sq, pairs, out))
+
+
 def _nw_offsets(sq, pairs):
     lens = sq.offs[1:] - sq.offs[:-1]
     cap = lens[pairs[:, 0].long()] + lens[pairs[:, 1].long()]
@@ -150,7 +160,7 @@ def case_protein(ctx):
     return t_lev + t_nw
 
 
-CASES = dict(lev=case_lev, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
+CASES = dict(lev=case_lev, lev_few=case_lev_few, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
              protein=case_protein, nw_affine=case_nw_affine, metrics=case_metrics)
 
 
