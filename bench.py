@@ -35,7 +35,7 @@ ALU_OPS_PER_WORD = 9
 # workload, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # (profiles/launches_tree_dna_allpairs_2000x1500.md); valid only while the
 # kernel source is the one that was measured.
-TRAFFIC = dict(kernel_sha256_16="a315aa91f6ae4f6f", bytes_per_launch=19.9e6)
+TRAFFIC = dict(kernel_sha256_16="a315aa91f6ae4f6f", bytes_per_launch=20.1e6)
 WORKLOAD = "tree_dna_allpairs_2000x1500"
 
 
@@ -530,7 +530,8 @@ def main():
                     scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
                     config=dict(workload=WORKLOAD, n_seqs=ds.n, pairs=len(pairs), cells=cells,
                                 pairs_per_s=world * len(pairs) * args.steps / (total_ms / 1e3),
-                                l2="flushed between timed steps (256 MB write)", step="msa_pack + msa_lev_batch"),
+                                l2="flushed between timed steps (256 MB write)", step="msa_pack + msa_lev_batch",
+                                schedule=dict(api.lev_schedule(ctx), autotuned=not args.no_autotune)),
                     roofline=roof, cpu_baseline=cpu,
                     e2e=dict(value=e2e_value, unit="GCUPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                              output_matches_device=bool(ok)),

@@ -435,10 +435,12 @@ msa_status msa_lev_autotune(msa_ctx *ctx, const msa_seqset *s, const int32_t *pa
         int lane_min, slot_min, lane_per, warp_per;
     };
     // {1 << 30, 1 << 30, ...}: warp kernel only; slot_min >= lane_min: no slot kernel
+    // lane_per = 32: one target per lane per task (fastest on long DNA all-pairs
+    // batches, slower on short protein ones)
     const Cand cands[] = {{32, 2, 0, 4},   {16, 2, 0, 4},   {64, 2, 0, 4},   {32, 3, 0, 4},
-                          {12, 12, 0, 4},  {4, 4, 0, 4},    {32, 2, 64, 4},  {32, 2, 128, 4},
-                          {32, 2, 256, 4}, {32, 2, 512, 4}, {32, 2, 0, 1},   {32, 2, 0, 16},
-                          {1 << 30, 1 << 30, 0, 4}};
+                          {12, 12, 0, 4},  {4, 4, 0, 4},    {32, 2, 32, 4},  {32, 2, 64, 4},
+                          {32, 2, 128, 4}, {32, 2, 256, 4}, {32, 2, 512, 4}, {32, 2, 0, 1},
+                          {32, 2, 0, 16},  {1 << 30, 1 << 30, 0, 4}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
