@@ -102,9 +102,12 @@ struct BandEq {
 // widened to whole chunks (a superset of the band, so still exact), and the
 // lane above sends the Ph/Mh bits of all CPS columns in one word.
 constexpr int kBandCps = MSA_BAND_CPS;
-static_assert(kBandCps >= 1 && 2 * kBandCps <= 8, "columns per step");
+// The word sent down holds 2 bits per column below T, the value of D on the
+// row above (at most m + n <= 32,768 for sequences of up to 16,384), so
+// 2 CPS + 16 bits must fit in 32.
+static_assert(kBandCps >= 1 && 2 * kBandCps + 16 <= 32, "columns per step");
 // the carry word of a top block: Ph = 1, Mh (carry) = 0 for each column
-constexpr uint32_t kBandTopBits = 0x55u & ((1u << (2 * kBandCps)) - 1u);
+constexpr uint32_t kBandTopBits = 0x55555555u & ((1u << (2 * kBandCps)) - 1u);
 // capacity of a (G, WPL) group at CPS columns per step: the lane that holds
 // block b must have finished it before block b + G needs it
 __host__ __device__ constexpr int band_capacity(int G, int WPL) { return (G - 1) * 32 * WPL - 2 * kBandCps; }
