@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lev_kernels.cuh"
+#include "warp_agg.cuh"
 #include "msa_internal.cuh"
 
 namespace msa {
@@ -102,14 +103,23 @@ struct PairList {
 __global__ void count_kernel(PairList L, int32_t n, const int64_t *__restrict__ offs, int64_t total,
                              int32_t *__restrict__ qcount, int32_t *err) {
     const int64_t P = L.size();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = L.id(k);
-        const int q = L.pairs[2 * p], t = L.pairs[2 * p + 1];
-        if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) {
-            record_error(err, kErrIndex, p, seq_ok(offs, n, total, q) ? t : q);
-            continue;
+    // warp-uniform loop (the warp's lanes take consecutive pairs) so that the
+    // counts can be aggregated per warp
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); k0 < P; k0 += stride) {
+        const int64_t k = k0 + (threadIdx.x & 31);
+        bool act = k < P;
+        int q = 0;
+        if (act) {
+            const int64_t p = L.id(k);
+            q = L.pairs[2 * p];
+            const int t = L.pairs[2 * p + 1];
+            if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) {
+                record_error(err, kErrIndex, p, seq_ok(offs, n, total, q) ? t : q);
+                act = false;
+            }
         }
-        atomicAdd(qcount + q, 1);
+        warp_agg_inc(qcount, q, act);
     }
 }
 
@@ -142,13 +152,24 @@ __global__ void scatter_kernel(PairList L, int32_t n, const int64_t *__restrict_
                                const int32_t *__restrict__ qstart, int32_t *__restrict__ qfill,
                                int32_t *__restrict__ sorted_t, int32_t *__restrict__ sorted_p) {
     const int64_t P = L.size();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = L.id(k);
-        const int q = L.pairs[2 * p], t = L.pairs[2 * p + 1];
-        if (!seq_ok(offs, n, total, q) || !seq_ok(offs, n, total, t)) continue;
-        const int pos = qstart[q] + atomicAdd(qfill + q, 1);
-        sorted_t[pos] = t;
-        sorted_p[pos] = (int32_t)p;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); k0 < P; k0 += stride) {
+        const int64_t k = k0 + (threadIdx.x & 31);
+        bool act = k < P;
+        int64_t p = 0;
+        int q = 0, t = 0;
+        if (act) {
+            p = L.id(k);
+            q = L.pairs[2 * p];
+            t = L.pairs[2 * p + 1];
+            act = seq_ok(offs, n, total, q) && seq_ok(offs, n, total, t);
+        }
+        const int r = warp_agg_inc(qfill, q, act);
+        if (act) {
+            const int pos = qstart[q] + r;
+            sorted_t[pos] = t;
+            sorted_p[pos] = (int32_t)p;
+        }
     }
 }
 

@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "lev_kernels.cuh"
+#include "warp_agg.cuh"
 
 namespace msa {
 namespace noalloc {
@@ -72,9 +73,16 @@ __device__ __forceinline__ bool ok_seq(const int64_t *offs, int32_t n, int64_t t
 
 __global__ void na_count(Scratch *S, const int32_t *__restrict__ pairs, int64_t P, int32_t n,
                          const int64_t *__restrict__ offs, int64_t total) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int q = pairs[2 * p], t = pairs[2 * p + 1];
-        if (ok_seq(offs, n, total, q) && ok_seq(offs, n, total, t)) atomicAdd(&S->qcount[q], 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); p0 < P; p0 += stride) {
+        const int64_t p = p0 + (threadIdx.x & 31);
+        int q = 0;
+        bool act = p < P;
+        if (act) {
+            q = pairs[2 * p];
+            act = ok_seq(offs, n, total, q) && ok_seq(offs, n, total, pairs[2 * p + 1]);
+        }
+        warp_agg_inc(S->qcount, q, act);
     }
 }
 
@@ -103,12 +111,22 @@ __global__ void __launch_bounds__(1024) na_scan(Scratch *S, int32_t n) {
 
 __global__ void na_scatter(Scratch *S, const int32_t *__restrict__ pairs, int64_t P, int32_t n,
                            const int64_t *__restrict__ offs, int64_t total) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int q = pairs[2 * p], t = pairs[2 * p + 1];
-        if (!ok_seq(offs, n, total, q) || !ok_seq(offs, n, total, t)) continue;
-        const int pos = S->qstart[q] + atomicAdd(&S->qfill[q], 1);
-        S->sorted_t[pos] = t;
-        S->sorted_p[pos] = (int32_t)p;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); p0 < P; p0 += stride) {
+        const int64_t p = p0 + (threadIdx.x & 31);
+        int q = 0, t = 0;
+        bool act = p < P;
+        if (act) {
+            q = pairs[2 * p];
+            t = pairs[2 * p + 1];
+            act = ok_seq(offs, n, total, q) && ok_seq(offs, n, total, t);
+        }
+        const int r = warp_agg_inc(S->qfill, q, act);
+        if (act) {
+            const int pos = S->qstart[q] + r;
+            S->sorted_t[pos] = t;
+            S->sorted_p[pos] = (int32_t)p;
+        }
     }
 }
 
