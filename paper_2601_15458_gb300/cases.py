@@ -1,6 +1,8 @@
 """Small fixed workloads that run one kernel family each, for profiling.
 
     python -m paper_2601_15458_gb300.cases lev     # lane kernel, 400 x 1,500 DNA all pairs
+    python -m paper_2601_15458_gb300.cases lev_few # slot kernel, 20,000 x 1,500 DNA, 100,000 random pairs
+    python -m paper_2601_15458_gb300.cases tree    # guide tree of 50,000 16S-like DNA sequences
     python -m paper_2601_15458_gb300.cases nw      # NW fill + traceback, 2,000 pairs of ~1,500
     python -m paper_2601_15458_gb300.cases band    # certified bands, 100,000 pairs 1,000-10,000
     python -m paper_2601_15458_gb300.cases band_small  # the same on 20,000 pairs (for ncu captures)
@@ -54,6 +56,19 @@ def case_lev_few(ctx):
     pairs = torch.from_numpy(synth.random_pairs(7, ds.n, 100000)).cuda()
     out = torch.empty(pairs.shape[0], dtype=torch.int32, device="cuda")
     return _time(lambda: api.lev_batch(ctx, sq, pairs, out))
+
+
+def case_tree(ctx):
+    """Guide tree (Alg. 1) of 50,000 16S-like DNA sequences, one partition."""
+    ds = synth.gg16s_dna(seed=5, n=50000)
+    sq = api.upload_and_pack(ctx, ds)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = api.clam_partition(ctx, sq)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
+    print(f"guide tree: {tree.n_nodes} nodes, {ms:.1f} ms")
+    return ms
 
 
 def _nw_offsets(sq, pairs):
@@ -160,7 +175,7 @@ def case_protein(ctx):
     return t_lev + t_nw
 
 
-CASES = dict(lev=case_lev, lev_few=case_lev_few, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
+CASES = dict(lev=case_lev, lev_few=case_lev_few, tree=case_tree, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
              protein=case_protein, nw_affine=case_nw_affine, metrics=case_metrics)
 
 
