@@ -56,7 +56,12 @@ static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
 #define MSA_BAND_MAX_SHARE 0.75f
 #endif
 constexpr float kBandMaxShare = MSA_BAND_MAX_SHARE;
-constexpr int kBandRounds = 8;
+// rounds of band retries per call (all enqueued; pairs still pending after
+// the last one go to the full DP)
+#ifndef MSA_BAND_ROUNDS
+#define MSA_BAND_ROUNDS 3
+#endif
+constexpr int kBandRounds = MSA_BAND_ROUNDS;
 constexpr int kBandThreads = 128;
 #ifndef MSA_BAND_HEADROOM
 #define MSA_BAND_HEADROOM 0.0f
