@@ -196,7 +196,7 @@ msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *pairs, int6
  * grows to min(result, 2k + 1) (at most a doubling; the result is itself an
  * upper bound of f, so that band always certifies) for up to 3 attempts, and
  * pairs still pending, or whose band reaches the whole matrix (or the
- * largest window this build holds in registers), are computed by the full
+ * largest window the library's kernels hold in registers), are computed by the full
  * DP of msa_lev_batch.  k_used_out[p] (device int32 [P]) receives the band that
  * certified the pair (>= k0[p]), or max(m, n) when the full DP decided it.
  * Any k0 (even 0) gives the exact distance; a good k0 only saves work.

@@ -380,7 +380,7 @@ msa_status lev_validate(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs,
         return set_error(ctx, MSA_EINVAL, "%s: null pointer", who);
     if (s->n_seqs < 0 || s->max_len < 0) return set_error(ctx, MSA_EINVAL, "%s: negative size", who);
     if (s->max_len > 32 * 32 * 16)
-        return set_error(ctx, MSA_EUNSUPPORTED, "%s: max_len %d above the 16384 this build supports", who, s->max_len);
+        return set_error(ctx, MSA_EUNSUPPORTED, "%s: max_len %d above the 16384 the kernels support", who, s->max_len);
     return MSA_OK;
 }
 
