@@ -423,10 +423,11 @@ def adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
     return out, m, v
 
 
-# Band policy and its calibration.  The paper's band proposer turns the
-# network's output into a Ukkonen band; these two functions are this
-# project's definition of that step (parity unpinned beyond the pins in the
-# tests: identity reduction, quantile definition, monotonicity).
+# Band policy and its calibration.  The band proposer turns the network's
+# output into a Ukkonen band; these functions are this project's definition
+# of that step, pinned in the tests by numpy's inverted-CDF quantile, the
+# exact reduction of identity knots to the plain policy, the map's values at
+# and halfway between knots, monotonicity and hand-worked bands.
 
 CAL_KNOTS = 33          # knots at yhat = 0, 1/32, ..., 1
 CAL_MIN_PAIRS = 16      # a bin with fewer held-out pairs keeps the identity
