@@ -24,6 +24,12 @@
  *    (j = 0..n).  Levenshtein is symmetric; NW output is defined for the
  *    order given.
  *  - Empty sequences are allowed; P = 0 is a no-op returning MSA_OK.
+ *  - Calls on one context share its workspace, its side streams (on which
+ *    independent kernels of one call run side by side, joined back into
+ *    `stream` before the call's work ends) and its error word: order them
+ *    on the GPU (one stream, or events) and make them from one host thread
+ *    at a time.  Work that must overlap takes one context per stream.
+ *    msa_lev_batch_noalloc has no context and its own rule (below).
  */
 #ifndef MSA_H
 #define MSA_H
