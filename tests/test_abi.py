@@ -43,6 +43,10 @@ def test_size_helpers(lib):
     assert lib.msa_plane_words(64, 0) == (2 + 1) * 2
     assert lib.msa_plane_words(65, 1) == (3 + 1) * 5
     assert lib.msa_lev_workspace_bytes(1000, 10) > 1000 * 8
+    for n, ns in [(0, 1), (1, 1), (1000, 10), (123457, 50000)]:
+        # the pair list (2 int32 per target, 256-byte rounded) plus the batch's own workspace
+        assert lib.msa_lev_one_to_many_workspace_bytes(n, ns) == \
+            (8 * n + 255) // 256 * 256 + lib.msa_lev_workspace_bytes(n, ns)
     assert b"sm_103a" in lib.msa_version()
 
 
