@@ -180,14 +180,20 @@ msa_status msa_lev_tune_set(msa_ctx *ctx, const int32_t *tune4);
  * context and no cudaMalloc / cudaFree / allocating library call: its scratch
  * is one fixed device array inside the library (about 5.8 MB, held on every
  * GPU that loads the library until the process exits).
- *  - Limits: P <= 262144 pairs and n_seqs <= 65536 per call; larger calls
- *    return MSA_EINVAL before anything is enqueued.
+ *  - Limits: P <= 262144 pairs and 1 <= n_seqs <= 65536 per call; larger
+ *    calls, null pointers and an unknown alphabet return MSA_EINVAL, and
+ *    max_len < 0 MSA_EINVAL, max_len > 16384 MSA_EUNSUPPORTED, before
+ *    anything is enqueued.
  *  - The first call on a device looks the array up with that device
- *    current (cudaGetSymbolAddress); make it before any stream capture.
+ *    current (cudaGetSymbolAddress), sets kernel attributes and queries
+ *    occupancies; make it before any stream capture.  This set-up belongs to
+ *    the device's CUDA context: after the context is destroyed and recreated
+ *    (cudaDeviceReset), the next call redoes it, so that call too should
+ *    come before any capture.
  *  - Every call shares the array: calls that overlap on the GPU (other
  *    streams or threads) race; issue them on one stream.
  *  - No error word: a pair with an index outside the set, or whose first
- *    sequence is longer than the kernels hold (16384), gets d_out[p] = -1.
+ *    sequence is longer than s->max_len, gets d_out[p] = -1.
  */
 msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *pairs, int64_t P, int32_t *d_out,
                                  void *stream);

@@ -20,8 +20,6 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libmsa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-# developer knob for A/B builds of kernel variants, e.g. MSA_NVCC_FLAGS="-DMSA_BV_VARIANT=0"
-EXTRA = os.environ.get("MSA_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -45,7 +43,7 @@ def _stale(obj: str, src: str, hdr_mtime: float) -> bool:
 def build(verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "flags.txt")
-    flags_now = " ".join(EXTRA)
+    flags_now = " ".join(ARCH + FLAGS)
     if not os.path.exists(stamp) or open(stamp).read() != flags_now:
         for o in glob.glob(os.path.join(BUILD, "*.o")):
             os.remove(o)
@@ -63,7 +61,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
 
     def compile_one(item):
         src, obj = item
-        cmd = [cc, *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj + ".tmp"]
+        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

@@ -650,13 +650,12 @@ __global__ void sync_kernel(MlpState st) {
 }
 
 static msa_status ensure_mlp_smem(msa_ctx *ctx) {
-    static bool done = false;
-    if (done) return MSA_OK;
+    if (ctx->mlp_smem_set) return MSA_OK;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(train_fwd_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "mlp smem attribute");
-    done = true;
+    ctx->mlp_smem_set = true;
     return MSA_OK;
 }
 

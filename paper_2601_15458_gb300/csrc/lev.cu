@@ -334,8 +334,6 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     a.bsum = bsum;
     a.d_out = d_out;
     a.err = ctx->dev_err;
-    a.one = 1u;
-    a.two = 2u;
     // buckets that no sequence of this set can reach are not launched
     const int Wmax = std::max(1, (s->max_len + 31) / 32);
     int lane_last = R.nlane - 1;

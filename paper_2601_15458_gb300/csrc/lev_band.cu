@@ -52,23 +52,11 @@ static const int kBandGHost[kBandBuckets] = BAND_G_LIST;
 static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
 // a band whose rows per column (k + H) exceed this share of the column goes
 // to the full bit-vector DP, whose kernels need no band bookkeeping
-#ifndef MSA_BAND_MAX_SHARE
-#define MSA_BAND_MAX_SHARE 0.75f
-#endif
-constexpr float kBandMaxShare = MSA_BAND_MAX_SHARE;
+constexpr float kBandMaxShare = 0.75f;
 // rounds of band retries per call (all enqueued; pairs still pending after
 // the last one go to the full DP)
-#ifndef MSA_BAND_ROUNDS
-#define MSA_BAND_ROUNDS 3
-#endif
-constexpr int kBandRounds = MSA_BAND_ROUNDS;
+constexpr int kBandRounds = 3;
 constexpr int kBandThreads = 128;
-#ifndef MSA_BAND_HEADROOM
-#define MSA_BAND_HEADROOM 0.0f
-#endif
-// a pair's first group holds a band this share wider than requested, so that
-// a near miss retries in place (its retry band is min(d_k, 2k + 1))
-constexpr float kBandHeadroom = MSA_BAND_HEADROOM;
 
 struct BandArgs {
     const uint32_t *planes;
@@ -98,15 +86,12 @@ struct BandEq {
     uint32_t pl[kShared ? 1 : WPL][kShared ? 1 : B];
 };
 
-#ifndef MSA_BAND_CPS
-#define MSA_BAND_CPS 4
-#endif
 // Columns per pipeline step: each step a block computes a chunk of CPS
 // consecutive columns, so the per-step bookkeeping (the shuffle, the live
 // tests, the vote) is paid once per chunk.  A block's live columns are
 // widened to whole chunks (a superset of the band, so still exact), and the
 // lane above sends the Ph/Mh bits of all CPS columns in one word.
-constexpr int kBandCps = MSA_BAND_CPS;
+constexpr int kBandCps = 4;
 // The word sent down holds 2 bits per column below T, the value of D on the
 // row above (at most m + n <= 32,768 for sequences of up to 16,384), so
 // 2 CPS + 16 bits must fit in 32.
@@ -441,7 +426,7 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
         int b = -1;
         if (ly > 0 && lx > 0) {
             for (int c = 0; c < nb; ++c)
-                if ((float)band_capacity(kBandG[c], kBandWPL[c]) >= (float)k * (1.f + kBandHeadroom)) {
+                if (band_capacity(kBandG[c], kBandWPL[c]) >= k) {
                     b = c;
                     break;
                 }
@@ -538,14 +523,9 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
         const int c1 = band_capacity(kBandGHost[b], kBandWPLHost[b]);
         if (c1 <= c0) return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table not increasing at %d", b);
     }
-    static int occ[2][kBandBuckets] = {};
+    int occ[kBandBuckets];
     for (int b = 0; b < nb; ++b)
-        if (occ[s->alphabet][b] == 0) {
-            int o = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[b], kBandThreads, 0);
-            if (e != cudaSuccess) return cuda_check(ctx, e, "band occupancy");
-            occ[s->alphabet][b] = std::max(o, 1);
-        }
+        if ((rc = occupancy(ctx, fns[b], kBandThreads, 0, &occ[b]))) return rc;
     // buckets beyond the first that holds a band as wide as the longest
     // sequence of this set are never used
     int last = nb - 1;
@@ -581,7 +561,7 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
             e = run_concurrent(ctx, st, last + 1, [&](int b, cudaStream_t s2) {
                 BandArgs ab = a;
                 ab.bucket = b;
-                launch[b](ab, ctx->sm_count * occ[s->alphabet][b], s2);
+                launch[b](ab, ctx->sm_count * occ[b], s2);
             }, 0, 8, /*join=*/r != 0);
             ctx->launches += last + 1;
             if (e != cudaSuccess) return cuda_check(ctx, e, "band launch");

@@ -46,7 +46,6 @@ struct LevArgs {
     int32_t *d_out;
     int32_t *err;
     int32_t bucket;
-    uint32_t one, two;        // 1 and 2, as runtime values (see bv_word)
 };
 
 // 32 match bits of the query for rows 32k+1 .. 32k+32 and every symbol c.
@@ -81,82 +80,6 @@ __device__ __forceinline__ uint32_t match_mask(const uint32_t (&pl)[B], uint32_t
     return eq;
 }
 
-// One 32-row word of one column.  ph_in/mh_in: top bits of the previous
-// word's Ph/Mh (row 0: ph_in = 1, mh_in = 0); they are replaced by this
-// word's top bits on return.
-//
-// The carry of the addition into the word's first row equals mh_in, and it
-// is folded into Eq for the addition only (Xh of the first row is
-// Eq | Mh[row above]; Xv keeps the plain Eq).  The adds, the shifts by one
-// and the top-bit extractions are issued as integer multiply-adds
-// (x * 1 + y, x * 2 + b, hi(x * 2)) with the factors in registers, so that
-// they run on the FMA pipe beside the logic ops on the ALU pipe.  Three
-// variants are kept for measurement (MSA_BV_VARIANT): 0 (default) all ALU;
-// 1 also the top bits as hi(x * 2); 2 add and shifts by one on the FMA pipe.
-// Measured on GB300 (2,000 x 1,500 all pairs): 48.9 / 45.4 / 47.5 TCUPS:
-// the multiply-adds lengthen the carry chain more than they relieve the
-// ALU pipe at the occupancy the register arrays allow.
-__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ uint32_t imul_hi(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
-#ifndef MSA_BV_VARIANT
-#define MSA_BV_VARIANT 0
-#endif
-
-__device__ __forceinline__ void bv_word(uint32_t eq, uint32_t &pv, uint32_t &mv, uint32_t &ph_in,
-                                        uint32_t &mh_in, uint32_t one, uint32_t two) {
-#if MSA_BV_VARIANT == 0
-    // all logic, adds and shifts on the ALU pipe
-    const uint32_t sum = (eq & pv) + pv + mh_in;
-    const uint32_t xh = (sum ^ pv) | eq;
-    const uint32_t ph = mv | ~(xh | pv);
-    const uint32_t mh = pv & xh;
-    const uint32_t phs = (ph << 1) | ph_in;
-    const uint32_t mhs = (mh << 1) | mh_in;
-    ph_in = ph >> 31;
-    mh_in = mh >> 31;
-#elif MSA_BV_VARIANT == 1
-    // adds, shifts and top-bit extractions as integer multiply-adds
-    const uint32_t eqc = eq | mh_in;
-    const uint32_t sum = imad(eqc & pv, one, pv);
-    const uint32_t xh = (sum ^ pv) | eqc;
-    const uint32_t ph = mv | ~(xh | pv);
-    const uint32_t mh = pv & xh;
-    const uint32_t phs = imad(ph, two, ph_in);
-    const uint32_t mhs = imad(mh, two, mh_in);
-    ph_in = imul_hi(ph, two);
-    mh_in = imul_hi(mh, two);
-#else
-    // the add and the two shifts by one as multiply-adds, top bits by shifts
-    const uint32_t eqc = eq | mh_in;
-    const uint32_t sum = imad(eqc & pv, one, pv);
-    const uint32_t xh = (sum ^ pv) | eqc;
-    const uint32_t ph = mv | ~(xh | pv);
-    const uint32_t mh = pv & xh;
-    const uint32_t phs = imad(ph, two, ph_in);
-    const uint32_t mhs = imad(mh, two, mh_in);
-    ph_in = ph >> 31;
-    mh_in = mh >> 31;
-#endif
-    pv = mhs | ~(eq | mv | phs);
-    mv = phs & (eq | mv);
-}
-
-#ifndef MSA_LANE_CHAIN
-#define MSA_LANE_CHAIN 3
-#endif
-#ifndef MSA_LANE_UNROLL
-#define MSA_LANE_UNROLL 2
-#endif
-
 // Lane kernel match masks: [symbol][word], WC words padded to a stride of 4
 // mod 8 words, so a 16-byte load of 4 words starts aligned and the 4 symbols'
 // rows fall on disjoint bank groups (lanes of a warp reading different
@@ -174,23 +97,15 @@ __host__ __device__ constexpr int lane_smem_words(int WC, int SIGMA, int SLOTS) 
 
 // One column over WC words, in chunks of up to 8 words: the chunk's
 // (Eq & Pv) + Pv additions run on the hardware carry chain (add.cc/addc), and
-// the shifts by one take the lower word's top bit by funnel shift, so no
-// carry or top bit is extracted by separate instructions.
+// the Ph shift by one takes the lower word's top bit by funnel shift.
 //
-// Variants 3 and 4 use that the carry into row i of the addition is Mh of
-// row i - 1 (and the word's carry-in for its first row): the shifted Mh
-// vector is the carry-in vector sum ^ u ^ Pv, one logic op, and with it
-// neither Mh nor Xh is formed (Ph = Mv | ~(Xh | Pv) = Mv | ~(sum | Pv | Eq)),
-// 9 ops per word instead of 10.  Variants 2 and 4 issue the addition as a
-// multiply-add by a runtime one (madc), on the FMA pipe; variant 5 the Ph
-// shift as ph * 2 + hi(ph_below * 2).  Measured on 2,000 x 1,500 all pairs:
-// variant 3 (default) 57.3-57.6 TCUPS, 5: 55.6-55.9, 4: 51.8 (one column
-// per iteration).
+// The carry into row i of the addition is Mh of row i - 1 (and the word's
+// carry-in for its first row), so the shifted Mh vector is the carry-in
+// vector sum ^ u ^ Pv, one logic op, and with it neither Mh nor Xh is formed
+// (Ph = Mv | ~(Xh | Pv) = Mv | ~(sum | Pv | Eq)): 9 ops per word.
 template <int WC>
-__device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t (&Pv)[WC], uint32_t (&Mv)[WC],
-                                                  uint32_t one, uint32_t two) {
-    uint32_t cy = 0u, ph_prev = 0u, mh_prev = 0u;
-    (void)mh_prev;
+__device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t (&Pv)[WC], uint32_t (&Mv)[WC]) {
+    uint32_t cy = 0u, ph_prev = 0u;
 #pragma unroll
     for (int k0 = 0; k0 < WC; k0 += 8) {
         constexpr int kMax = 8;
@@ -206,34 +121,14 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 pv[w] = Pv[k0 + w];
                 u[w] = eq[w] & pv[w];
             }
-#if MSA_LANE_CHAIN == 2 || MSA_LANE_CHAIN == 4
-            cy = CarryChainMadIn<8>::add(s, u, pv, cy, one);
-#else
             cy = CarryChainIn<8>::add(s, u, pv, cy);
-            (void)one;
-#endif
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
                 const int k = k0 + w;
-#if MSA_LANE_CHAIN >= 3
                 const uint32_t mhs = s[w] ^ u[w] ^ pv[w];
                 const uint32_t ph = Mv[k] | ~(s[w] | pv[w] | eq[w]);
-#if MSA_LANE_CHAIN == 5
-                // the shift on the FMA pipe: ph * 2 + top bit of the word below (hi(x * 2))
-                const uint32_t phs = imad(ph, two, k == 0 ? one : imul_hi(ph_prev, two));
-#else
                 const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
-#endif
                 ph_prev = ph;
-#else
-                const uint32_t xh = (s[w] ^ pv[w]) | eq[w];
-                const uint32_t ph = Mv[k] | ~(xh | pv[w]);
-                const uint32_t mh = pv[w] & xh;
-                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
-                const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
-                ph_prev = ph;
-                mh_prev = mh;
-#endif
                 const uint32_t xv = eq[w] | Mv[k];
                 Pv[k] = mhs | ~(xv | phs);
                 Mv[k] = phs & xv;
@@ -250,20 +145,10 @@ __device__ __forceinline__ void lane_column_chain(const uint32_t *row, uint32_t 
                 const uint64_t t = (uint64_t)u + pv + cy;
                 const uint32_t sum = (uint32_t)t;
                 cy = (uint32_t)(t >> 32);
-#if MSA_LANE_CHAIN >= 3
                 const uint32_t mhs = sum ^ u ^ pv;
                 const uint32_t ph = Mv[k] | ~(sum | pv | eq);
                 const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
                 ph_prev = ph;
-#else
-                const uint32_t xh = (sum ^ pv) | eq;
-                const uint32_t ph = Mv[k] | ~(xh | pv);
-                const uint32_t mh = pv & xh;
-                const uint32_t phs = k == 0 ? (ph << 1) | 1u : __funnelshift_l(ph_prev, ph, 1);
-                const uint32_t mhs = k == 0 ? (mh << 1) : __funnelshift_l(mh_prev, mh, 1);
-                ph_prev = ph;
-                mh_prev = mh;
-#endif
                 const uint32_t xv = eq | Mv[k];
                 Pv[k] = mhs | ~(xv | phs);
                 Mv[k] = phs & xv;
@@ -338,14 +223,8 @@ __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
 // of the concatenated target lists, so a batch of queries with 2..31 targets
 // keeps the lanes busy, where a warp per query would leave most of them idle.
 // ---------------------------------------------------------------------------
-#ifndef MSA_LANE_MINB
-#define MSA_LANE_MINB 1
-#endif
-// MSA_LANE_MINB = 4 caps registers for 4 resident blocks (16 warps per SM)
-// where the bit vectors still fit (up to 52 words); measured slower than the
-// uncapped build (53.6-54.7 vs 55.9 TCUPS on 2,000 x 1,500 all pairs)
 template <int WC, int B, int SIGMA, int SLOTS = 1>
-__global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_kernel(LevArgs a) {
+__global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
     constexpr int S = lane_peq_stride(WC);
@@ -354,7 +233,6 @@ __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_
     uint32_t *sPeq = smem + (threadIdx.x >> 5) * lane_smem_words(WC, SIGMA, SLOTS);
     int32_t *sQ = (int32_t *)(sPeq + SLOTS * S * SIGMA);
     int32_t *sBeg = sQ + SLOTS, *sM = sBeg + SLOTS, *sPre = sM + SLOTS;
-    const uint32_t one = a.one, two = a.two;
     const int nent = a.bcount[a.bucket];
     // queries per warp: as many as make about 32 targets (one per lane, so
     // no lane runs two targets one after another), 32 / (mean targets per
@@ -475,34 +353,24 @@ __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_
                 }
             }
             if (!__any_sync(kFull, has)) break;
-#if MSA_LANE_UNROLL == 2
             // two columns per iteration while every busy lane has two left:
             // the second column's first words overlap the first column's
             // last ones, and the vote is paid once per two columns
             const bool pair2 = __all_sync(kFull, !has || j + 1 < n);
-#else
-            const bool pair2 = false;
-#endif
             if (has) {
                 if (pair2) {
                     const int c0 = c_next, c1 = c_next2;
                     c_next = j + 2 < n ? __ldg(tc + j + 2) : 0;
                     c_next2 = j + 3 < n ? __ldg(tc + j + 3) : 0;
-                    lane_column_chain<WC>(peq + c0 * S, Pv, Mv, one, two);
-                    lane_column_chain<WC>(peq + c1 * S, Pv, Mv, one, two);
+                    lane_column_chain<WC>(peq + c0 * S, Pv, Mv);
+                    lane_column_chain<WC>(peq + c1 * S, Pv, Mv);
                     j += 2;
                 } else if (j < n) {
                     const int c = c_next;
                     c_next = c_next2;
                     c_next2 = j + 2 < n ? __ldg(tc + j + 2) : 0;
                     const uint32_t *row = peq + c * S;
-#if MSA_LANE_CHAIN
-                    lane_column_chain<WC>(row, Pv, Mv, one, two);
-#else
-                    uint32_t ph_in = 1u, mh_in = 0u;
-#pragma unroll
-                    for (int k = 0; k < WC; ++k) bv_word(row[k], Pv[k], Mv[k], ph_in, mh_in, one, two);
-#endif
+                    lane_column_chain<WC>(row, Pv, Mv);
                     ++j;
                 }
                 if (j == n) {
@@ -531,9 +399,6 @@ __global__ void __launch_bounds__(128, (WC <= 52 ? MSA_LANE_MINB : 1)) lev_lane_
 // Match masks: layout [w][c][lane], conflict-free for any mix of symbols.
 // ---------------------------------------------------------------------------
 constexpr int kRing = 32;
-#ifndef MSA_WARP_CHAIN
-#define MSA_WARP_CHAIN 1
-#endif
 
 template <int WPL, int B, int SIGMA>
 __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
@@ -545,7 +410,6 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
     int32_t *ring_p = ring_t + kRing;
     int32_t *ring_n = ring_p + kRing;
     volatile int32_t *end_step = ring_n + kRing;
-    const uint32_t one = a.one, two = a.two;
     const int ntasks = a.bcount[a.bucket];
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
@@ -624,18 +488,11 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
                     uint32_t ph_in = lane == 0 ? 1u : (uint32_t)(msg_in & 1);
                     uint32_t mh_in = lane == 0 ? 0u : (uint32_t)((msg_in >> 1) & 1);
                     const uint32_t *col = sPeq + c * 32 + lane;
-#if MSA_WARP_CHAIN
                     uint32_t eq[WPL], ph_out, mh_out;
 #pragma unroll
                     for (int w = 0; w < WPL; ++w) eq[w] = col[w * SIGMA * 32];
                     bv_column<WPL>(eq, Pv, Mv, ph_in, mh_in, ph_out, mh_out);
                     msg = (int)(ph_out | (mh_out << 1));
-#else
-#pragma unroll
-                    for (int w = 0; w < WPL; ++w)
-                        bv_word(col[w * SIGMA * 32], Pv[w], Mv[w], ph_in, mh_in, one, two);
-                    msg = (int)(ph_in | (mh_in << 1));
-#endif
                     ++j;
                     if (j == n) {
                         int part = lane == 0 ? 0 : (msg_in >> 2);

@@ -18,11 +18,18 @@
 //    overlaps on the GPU (other streams, other host threads) race.  Serialise
 //    them on one stream.
 //  * The first call on a device looks the array's address up
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
-//  * No context, so no error word: pairs with an index outside the set, or a
-//    query longer than the kernels hold, get d_out = -1.
+//    (cudaGetSymbolAddress) with that device current, sets the kernels'
+//    shared-memory limits and queries their occupancy; make that first call
+//    before any stream capture.  The set-up is kept per CUDA context: after
+//    the device's context is destroyed and recreated (cudaDeviceReset), the
+//    next call on it does the set-up again, so that first call should also
+//    come before any capture.
+//  * No context, so no error word: pairs with an index outside the set, or
+//    whose first sequence is longer than s->max_len, get d_out = -1.
+//    max_len < 0 is rejected with MSA_EINVAL, max_len above the 16,384 the
+//    kernels hold with MSA_EUNSUPPORTED.
 //  * It calls no cudaMalloc, cudaFree or allocating library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +45,7 @@ constexpr int64_t kMaxPairs = int64_t(1) << 18;   // 262,144 pairs per call
 constexpr int32_t kMaxSeqs = int32_t(1) << 16;    // 65,536 sequences in the set
 constexpr int kNB = 64;                           // kernel buckets (>= 2 x lane + warp configurations)
 constexpr int kMaxDevices = 64;
+constexpr int32_t kMaxQueryLen = 32 * 32 * 16;     // the longest sequence the kernels hold (16,384)
 
 struct Scratch {
     int32_t qcount[kMaxSeqs];
@@ -187,9 +195,13 @@ static const LevKernelInfo &kernel_at(int alphabet, int b) {
     return (dna ? kLevWarpDna : kLevWarpProt)[b - 2 * nl];
 }
 
-// Per-device set-up: the scratch address, SM count and kernel occupancies.
+// Per-device set-up: the scratch address, SM count and kernel occupancies,
+// kept for the CUDA context they were taken in.  A context that is torn down
+// and created again (cudaDeviceReset) reloads the module, so the array may
+// move and the kernels' shared-memory attributes are gone: a call that finds
+// a different context on its device than the one recorded redoes the set-up.
 struct DeviceInfo {
-    bool ready = false;
+    unsigned long long ctx_id = 0;   // 0: no set-up yet
     Scratch *scratch = nullptr;
     int sm_count = 0;
     int occ[2][kNB] = {};
@@ -198,15 +210,51 @@ struct DeviceInfo {
 static DeviceInfo g_dev[kMaxDevices];
 static std::mutex g_mu;
 
-static msa_status setup(int dev, int alphabet, DeviceInfo **out) {
+// The driver's current-context calls, reached through the runtime (no link
+// against the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
+
+// Id of the context current on this thread, 0 when there is none.
+static unsigned long long current_ctx_id() {
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Returns a copy of the set-up of device `dev` for `alphabet`, doing it
+// first where needed (the first call on a device, and the first after its
+// context was recreated).  Called with `dev` current.
+static msa_status setup(int dev, int alphabet, DeviceInfo *out) {
     std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_ctx_current) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return MSA_ECUDA;
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    }
     DeviceInfo &d = g_dev[dev];
-    if (!d.ready) {
+    unsigned long long id = current_ctx_id();
+    if (id == 0 || id != d.ctx_id) {
+        // the address of the array in this context (this also makes the
+        // device's primary context current when no context is yet)
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return MSA_ECUDA;
-        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MSA_ECUDA;
-        d.scratch = static_cast<Scratch *>(ptr);
-        d.ready = true;
+        DeviceInfo fresh;
+        if (cudaDeviceGetAttribute(&fresh.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return MSA_ECUDA;
+        fresh.scratch = static_cast<Scratch *>(ptr);
+        fresh.ctx_id = current_ctx_id();
+        if (fresh.ctx_id == 0) return MSA_ECUDA;
+        d = fresh;
     }
     const int nl = alphabet == MSA_DNA ? kLevLaneDnaCount : kLevLaneProtCount;
     const int nw = alphabet == MSA_DNA ? kLevWarpDnaCount : kLevWarpProtCount;
@@ -222,7 +270,7 @@ static msa_status setup(int dev, int alphabet, DeviceInfo **out) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, K.fn, 128, smem) != cudaSuccess) return MSA_ECUDA;
         d.occ[alphabet][b] = std::max(blocks, 1);
     }
-    *out = &d;
+    *out = d;
     return MSA_OK;
 }
 
@@ -239,16 +287,23 @@ extern "C" msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *
     if (P > kMaxPairs || s->n_seqs > kMaxSeqs || s->n_seqs <= 0) return MSA_EINVAL;
     if (!pairs || !d_out || !s->offs || !s->codes || !s->planes) return MSA_EINVAL;
     if (s->alphabet != MSA_DNA && s->alphabet != MSA_PROTEIN) return MSA_EINVAL;
+    if (s->max_len < 0) return MSA_EINVAL;
+    if (s->max_len > kMaxQueryLen) return MSA_EUNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSA_ECUDA;
-    DeviceInfo *D = nullptr;
-    msa_status rc = setup(dev, s->alphabet, &D);
+    DeviceInfo info;
+    msa_status rc = setup(dev, s->alphabet, &info);
     if (rc) return rc;
+    const DeviceInfo *D = &info;
     cudaStream_t st = (cudaStream_t)stream;
     Scratch *S = D->scratch;
     const int32_t n = s->n_seqs;
-    // the scratch keeps the last call's contents: clear what must start at zero
-    if (cudaMemsetAsync(S->qcount, 0, sizeof(int32_t) * 3 * kMaxSeqs, st) != cudaSuccess ||
+    // the scratch keeps the last call's contents: clear what must start at
+    // zero (the per-query counters of this call's n sequences, the bucket
+    // counters) and preset every distance to -1 (pairs no kernel takes)
+    if (cudaMemsetAsync(S->qcount, 0, sizeof(int32_t) * n, st) != cudaSuccess ||
+        cudaMemsetAsync(S->qfill, 0, sizeof(int32_t) * n, st) != cudaSuccess ||
+        cudaMemsetAsync(S->qcursor, 0, sizeof(int32_t) * n, st) != cudaSuccess ||
         cudaMemsetAsync(S->bcount, 0, sizeof(int32_t) * 5 * kNB, st) != cudaSuccess ||
         cudaMemsetAsync(d_out, 0xff, sizeof(int32_t) * P, st) != cudaSuccess)
         return MSA_ECUDA;
@@ -284,8 +339,6 @@ extern "C" msa_status msa_lev_batch_noalloc(const msa_seqset *s, const int32_t *
     a.bsum = S->bsum;
     a.d_out = d_out;
     a.err = S->err;
-    a.one = 1u;
-    a.two = 2u;
     const int Wmax = std::max(1, (s->max_len + 31) / 32);
     for (int b = 0; b < 2 * pl.nlane + pl.nwarp; ++b) {
         const bool is_warp = b >= 2 * pl.nlane;

@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,12 +47,34 @@ struct msa_ctx {
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kSide] = {};
+    // resident blocks per SM of each kernel launched through this context
+    // (its device), keyed by kernel; filled on first use (one host thread at
+    // a time uses a context, so no lock is needed)
+    std::map<const void *, int> occ;
+    bool mlp_smem_set = false;
 };
 
 namespace msa {
 
 msa_status set_error(msa_ctx *ctx, msa_status code, const char *fmt, ...);
 msa_status cuda_check(msa_ctx *ctx, cudaError_t e, const char *what);
+
+// Resident blocks per SM (at least 1) of kernel `fn` launched with `threads`
+// threads and `smem` bytes of dynamic shared memory, on the context's device;
+// cached in the context.
+inline msa_status occupancy(msa_ctx *ctx, const void *fn, int threads, size_t smem, int *out) {
+    auto it = ctx->occ.find(fn);
+    if (it != ctx->occ.end()) {
+        *out = it->second;
+        return MSA_OK;
+    }
+    int blocks = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "occupancy query");
+    *out = blocks > 0 ? blocks : 1;
+    ctx->occ[fn] = *out;
+    return MSA_OK;
+}
 
 // Records a device error (first one wins).
 __device__ __forceinline__ void record_error(int32_t *err, int code, long long d0, long long d1) {
@@ -107,7 +130,8 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
 
 // Bit-parallel NW for the unit cost model (nw_bv.cu), launched by nw_run.
 int64_t nw_bv_slab_bytes(int max_len);
-int nw_bv_occupancy();
+const void *nw_bv_kernel_fn();
+constexpr int kBvThreads = 128;
 cudaError_t nw_bv_launch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
                          int32_t max_len, const int32_t *pairs, int64_t P, int32_t gap, int32_t *score,
                          uint8_t *ops, const int64_t *ops_off, int32_t *ops_len, char *slabs, int64_t slab_bytes,

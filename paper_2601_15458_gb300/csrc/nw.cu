@@ -29,12 +29,6 @@ constexpr int kNwR = 16;                 // rows per lane
 constexpr int kNwTile = 32 * kNwR;       // rows per tile
 constexpr int kNwWarps = 4;              // warps per block
 
-// 0: plain min / compare / select; 1: the two-way min-with-flag instruction
-// (__vibmin_s32), which yields the move preference with the minimum
-#ifndef MSA_NW_VARIANT
-#define MSA_NW_VARIANT 1
-#endif
-
 struct NwArgs {
     const uint8_t *codes;
     const int64_t *offs;
@@ -137,19 +131,12 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
 #pragma unroll
                     for (int r = 0; r < kNwR; ++r) {
                         const int dg = diag + (ac[r] == bj ? match : mismatch);
-#if MSA_NW_VARIANT == 0
-                        const int u = up + gap;
-                        const int lf = H[r] + gap;
-                        const int d = min(dg, min(u, lf));
-                        const uint32_t c = d == dg ? 0u : (d == u ? 1u : 2u);
-#else
                         // two-way minima with their "first argument won" flag:
                         // up <= left keeps up, then diagonal <= that keeps diagonal
                         bool up_wins, diag_wins;
                         const int m1 = __vibmin_s32(up + gap, H[r] + gap, &up_wins);
                         const int d = __vibmin_s32(dg, m1, &diag_wins);
                         const uint32_t c = diag_wins ? 0u : (up_wins ? 1u : 2u);
-#endif
                         code |= c << (2 * r);
                         diag = H[r];
                         H[r] = d;
@@ -438,12 +425,8 @@ msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const in
     if (P == 0) return MSA_OK;
     if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: null pointer");
-    static int occ = 0;
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_affine_kernel, kNwWarps * 32, 0);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "nw affine occupancy");
-        if (occ < 1) occ = 1;
-    }
+    int occ = 1;
+    if (msa_status rc = occupancy(ctx, (const void *)nw_affine_kernel, kNwWarps * 32, 0, &occ)) return rc;
     int32_t *counter = ar.take<int32_t>(64);
     const int64_t slab = nw_affine_slab_bytes(max_len);
     const int64_t avail = counter ? ar.cap - ar.used : 0;
@@ -475,10 +458,6 @@ int64_t nw_slab_bytes(int max_len) {
     return std::max(brow + (tbw + 255) / 256 * 256, nw_bv_slab_bytes(max_len));
 }
 
-#ifndef MSA_NW_BV
-#define MSA_NW_BV 1
-#endif
-
 msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
                   int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
                   int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
@@ -488,16 +467,12 @@ msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *
     if (P == 0) return MSA_OK;
     if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch: null pointer");
-    static int occ = 0, occ_bv = 0;
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_kernel, kNwWarps * 32, 0);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "nw occupancy");
-        if (occ < 1) occ = 1;
-        occ_bv = nw_bv_occupancy();
-    }
+    int occ = 1, occ_bv = 1;
+    if (msa_status rc = occupancy(ctx, (const void *)nw_kernel, kNwWarps * 32, 0, &occ)) return rc;
+    if (msa_status rc = occupancy(ctx, nw_bv_kernel_fn(), kBvThreads, 0, &occ_bv)) return rc;
     // unit costs (match 0, mismatch = gap > 0): the bit-parallel kernel, with
     // the plain DP for the pairs it hands back
-    const bool unit = MSA_NW_BV && match == 0 && mismatch == gap && gap > 0;
+    const bool unit = match == 0 && mismatch == gap && gap > 0;
     int32_t *counter = ar.take<int32_t>(64);
     int32_t *fb_list = unit ? ar.take<int32_t>(P) : nullptr;
     const int64_t slab = nw_slab_bytes(max_len);

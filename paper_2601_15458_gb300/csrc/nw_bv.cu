@@ -37,6 +37,7 @@ constexpr int kBvWpl = 2;                    // words per lane
 constexpr int kBvTileWords = 32 * kBvWpl;    // words per tile
 constexpr int kBvTileRows = 32 * kBvTileWords;
 constexpr int kBvWarps = 4;
+static_assert(kBvWarps * 32 == kBvThreads, "nw_bv_kernel block size");
 constexpr uint32_t kBvFull = 0xffffffffu;
 
 // Two columns per pipeline step: lane l computes columns 2q - 1 and 2q at
@@ -375,10 +376,6 @@ cudaError_t nw_bv_launch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs
     return cudaGetLastError();
 }
 
-int nw_bv_occupancy() {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nw_bv_kernel, kBvWarps * 32, 0) != cudaSuccess) return 1;
-    return occ > 0 ? occ : 1;
-}
+const void *nw_bv_kernel_fn() { return (const void *)nw_bv_kernel; }
 
 }  // namespace msa

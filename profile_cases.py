@@ -1,29 +1,32 @@
 """Small fixed workloads that run one kernel family each, for profiling.
 
-    python -m paper_2601_15458_gb300.cases lev     # lane kernel, 400 x 1,500 DNA all pairs
-    python -m paper_2601_15458_gb300.cases lev_few # slot kernel, 20,000 x 1,500 DNA, 100,000 random pairs
-    python -m paper_2601_15458_gb300.cases tree    # guide tree of 50,000 16S-like DNA sequences
-    python -m paper_2601_15458_gb300.cases nw      # NW fill + traceback, 2,000 pairs of ~1,500
-    python -m paper_2601_15458_gb300.cases band    # certified bands, 100,000 pairs 1,000-10,000
-    python -m paper_2601_15458_gb300.cases band_small  # the same on 20,000 pairs (for ncu captures)
-    python -m paper_2601_15458_gb300.cases pack    # packed loader, 1.1 GB arena
-    python -m paper_2601_15458_gb300.cases mlp     # band network forward + one training step
-    python -m paper_2601_15458_gb300.cases protein # 10,000 x 100 centre distances, 9,999 NW with traceback
-    python -m paper_2601_15458_gb300.cases nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
-    python -m paper_2601_15458_gb300.cases metrics # MSA quality of a 3,000-sequence MSA, 2,000-row sample
+    python profile_cases.py lev     # lane kernel, 400 x 1,500 DNA all pairs
+    python profile_cases.py lev_few # slot kernel, 20,000 x 1,500 DNA, 100,000 random pairs
+    python profile_cases.py tree    # guide tree of 50,000 16S-like DNA sequences
+    python profile_cases.py nw      # NW fill + traceback, 2,000 pairs of ~1,500
+    python profile_cases.py band    # certified bands, 100,000 pairs 1,000-10,000
+    python profile_cases.py band_small  # the same on 20,000 pairs (for ncu captures)
+    python profile_cases.py pack    # packed loader, 1.1 GB arena
+    python profile_cases.py mlp     # band network forward + one training step
+    python profile_cases.py protein # 10,000 x 100 centre distances, 9,999 NW with traceback
+    python profile_cases.py nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
+    python profile_cases.py metrics # MSA quality of a 3,000-sequence MSA, 2,000-row sample
 
 Each case runs its call a few times (the first warms up) and prints one
 line with the call's device time.
 """
 from __future__ import annotations
 
+import os
 import sys
 import time
 
 import numpy as np
 import torch
 
-from . import api, build, learned_band, synth
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+from paper_2601_15458_gb300 import api, build, learned_band, synth
 
 
 def _time(fn, reps=3):

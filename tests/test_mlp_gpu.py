@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import oracle
+from mlp_ties import forward_candidates
 from paper_2601_15458_gb300 import api, synth
 
 pytestmark = pytest.mark.gpu
@@ -71,18 +72,30 @@ def _oracle_params(p):
 
 
 def test_forward_matches_oracle(ctx):
+    """Every output within 1e-3 relative of the oracle.  The kernel sums in
+    fp32 and the oracle in float64, so a hidden value that lies (within the
+    fp32 summation error) on a bf16 rounding boundary may be rounded the
+    other way on the GPU; for such rows the output must match the oracle
+    with that unit rounded either way, each at the same 1e-3 bound."""
     X, _ = _features(ctx)
     model = api.BandModel(ctx, seed=3)
     yh = model.forward(X)
     ctx.check()
-    Xf = X.float().cpu().numpy()
-    ref, _ = oracle.mlp_forward(_oracle_params(model.params()), Xf)
-    got = yh.cpu().numpy()
-    # fp32 accumulation vs float64: a hidden value near a bf16 rounding tie may
-    # land one bf16 step apart, so compare with a tolerance scaled to the outputs
+    Xf = X.float().cpu().numpy().astype(np.float64)
+    op = _oracle_params(model.params())
+    ref, _ = oracle.mlp_forward(op, Xf)
+    got = yh.cpu().numpy().astype(np.float64)
     scale = np.abs(ref).max()
-    assert np.max(np.abs(got - ref)) <= 2e-2 * scale
-    assert np.median(np.abs(got - ref)) <= 1e-3 * scale
+    floor = 0.1 * scale                     # relative error taken against at least 10% of the output range
+    tied_rows = 0
+    for r in range(len(ref)):
+        if abs(got[r] - ref[r]) <= 1e-3 * max(abs(ref[r]), floor):
+            continue
+        cands, ties = forward_candidates(op, Xf[r])
+        tied_rows += ties > 0
+        err = min(abs(got[r] - c) / max(abs(c), floor) for c in cands)
+        assert err <= 1e-3, (r, got[r], ref[r], ties)
+    assert tied_rows <= 0.05 * len(ref)
 
 
 def test_gradients_match_oracle(ctx):
@@ -123,6 +136,30 @@ def test_adam_step_matches_closed_form(ctx):
                                  {k: v.astype(np.float64) for k, v in g.items()}, dict(zero), dict(zero), t=1, lr=1e-3)
     for k in p0:
         np.testing.assert_allclose(p1[k], exp[k], rtol=1e-5, atol=1e-6)
+
+
+def test_adam_five_steps_match_oracle(ctx):
+    """Five consecutive Adam steps on different minibatches, moments and the
+    step count carried on the device, against oracle.adam_step carrying its
+    own moments: catches a kernel that drops m or v, or corrects the bias
+    with the wrong t."""
+    X, y = _features(ctx)
+    model = api.BandModel(ctx, seed=6)
+    yt = torch.from_numpy(y).cuda()
+    p = {k: v.astype(np.float64) for k, v in model.params().items()}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    lr = 2e-3
+    for t in range(1, 6):
+        idx = torch.arange((t - 1) * 256, t * 256, dtype=torch.int32, device="cuda")
+        model.train_step(X, yt, idx, lr=0.0)
+        g = model.read_grad()
+        model.train_step(X, yt, idx, lr=lr)
+        got = model.params()
+        ctx.check()
+        p, m, v = oracle.adam_step(p, {k: x.astype(np.float64) for k, x in g.items()}, m, v, t=t, lr=lr)
+        for k in p:
+            np.testing.assert_allclose(got[k], p[k], rtol=1e-5, atol=1e-6, err_msg=f"step {t}, {k}")
 
 
 def test_band_policy_and_learned_gain(ctx):

@@ -316,6 +316,76 @@ def test_pinball_closed_form():
     np.testing.assert_allclose(dy, [-0.9 / 2, 0.1 / 2])
 
 
+def _one_path(w1=1.0, b1=0.0, w2=1.0, b2=0.0, w3=1.0, b3=0.0):
+    """Parameters whose only live path is x0 -> h1_0 -> h2_0 -> y."""
+    P = dict(W1=np.zeros((256, 128)), b1=np.zeros(128), W2=np.zeros((128, 64)), b2=np.zeros(64),
+             W3=np.zeros((64, 1)), b3=np.array([b3]))
+    P["W1"][0, 0], P["b1"][0], P["W2"][0, 0], P["b2"][0], P["W3"][0, 0] = w1, b1, w2, b2, w3
+    return P
+
+
+@pytest.mark.parametrize("site,x0,kw,expect", [
+    # the input is rounded to bf16: 1 + 2^-9 -> 1, so z1 = 1 - 15/16 = 2^-4
+    # (unrounded: 2^-4 + 2^-9, itself a bf16 value, would come through)
+    ("input", 1 + 2 ** -9, dict(b1=-0.9375), 2 ** -4),
+    # W1, W2 and W3 are rounded to bf16 the same way
+    ("weight1", 1.0, dict(w1=1 + 2 ** -9, b1=-0.9375), 2 ** -4),
+    ("weight2", 1.0, dict(w2=1 + 2 ** -9, b2=-0.9375), 2 ** -4),
+    ("weight3", 1.0, dict(w3=1 + 2 ** -9, b3=-0.9375), 2 ** -4),
+    # h1 = bf16(1 + 2^-8 + 2^-10) = 1 + 2^-7 (above the half step 2^-8);
+    # z2 = h1 - 1 = 2^-7 (unrounded h1 would give 2^-8 + 2^-10, a bf16 value)
+    ("hidden1", 1.0, dict(b1=2 ** -8 + 2 ** -10, b2=-1.0), 2 ** -7),
+    # h2 = bf16(1 + 2^-8 + 2^-10) = 1 + 2^-7, y = h2 - 1
+    ("hidden2", 1.0, dict(b2=2 ** -8 + 2 ** -10, b3=-1.0), 2 ** -7),
+    # ReLU: a negative pre-activation contributes nothing
+    ("relu", 1.0, dict(b1=-2.0, b3=0.25), 0.25),
+])
+def test_mlp_forward_rounding_sites(site, x0, kw, expect):
+    """Each place the forward pass rounds to bf16, shown by a hand-worked
+    one-path network whose output changes if that rounding is left out."""
+    X = np.zeros((1, 256))
+    X[0, 0] = np.float32(x0)
+    y, _ = oracle.mlp_forward(_one_path(**kw), X)
+    assert y[0] == expect
+
+
+def test_forward_tie_enumeration_finds_planted_flip():
+    """The rounding-choice enumeration used by the GPU forward check: a row
+    built to sit exactly on a bf16 boundary yields both outcomes, a row away
+    from every boundary only the oracle's."""
+    from mlp_ties import forward_candidates
+    op = _one_path(b1=2 ** -8, b2=-0.5)   # z1 = 1 + 2^-8: halfway between bf16 values 1 and 1 + 2^-7
+    x = np.zeros(256)
+    x[0] = 1.0
+    cands, ties = forward_candidates(op, x)
+    assert ties == 1 and sorted(cands) == [0.5, 0.5 + 2 ** -7]
+    cands, ties = forward_candidates(_one_path(b1=2 ** -6, b2=-0.5), x)
+    assert ties == 0 and cands == [0.5 + 2 ** -6]
+
+
+def test_adam_second_step_closed_form():
+    # two steps from zero moments: m2 = (1 - b1)(b1 g1 + g2), v2 = (1 - b2)(b2 g1^2 + g2^2),
+    # bias-corrected m2 / (1 - b1^2) = (b1 g1 + g2) / (1 + b1), v2 / (1 - b2^2) = (b2 g1^2 + g2^2) / (1 + b2)
+    b1, b2, lr, eps = 0.9, 0.999, 0.01, 1e-8
+    g1 = np.array([0.5, -2.0, 1e-3, 0.3])
+    g2 = np.array([0.5, 2.0, -1e-3, 0.0])
+    p = {"w": np.zeros(4)}
+    m = {"w": np.zeros(4)}
+    v = {"w": np.zeros(4)}
+    p1, m, v = oracle.adam_step(p, {"w": g1}, m, v, t=1, lr=lr)
+    p2, m, v = oracle.adam_step(p1, {"w": g2}, m, v, t=2, lr=lr)
+    mh = (b1 * g1 + g2) / (1 + b1)
+    vh = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    step1 = -lr * g1 / (np.abs(g1) + eps)
+    np.testing.assert_allclose(p2["w"], step1 - lr * mh / (np.sqrt(vh) + eps), rtol=1e-12, atol=1e-15)
+    # a constant gradient keeps the step at lr (bias correction exact at t = 2)
+    np.testing.assert_allclose(p2["w"][0], -2 * lr * 0.5 / (0.5 + eps), rtol=1e-12)
+    # a reversed gradient: m2 / (1 - b1^2) = -g1 / 19, v2 / (1 - b2^2) = g1^2
+    np.testing.assert_allclose(p2["w"][1] - p1["w"][1], -lr * (2.0 / 19) / (2.0 + eps), rtol=1e-12)
+    np.testing.assert_allclose(m["w"], (1 - b1) * (b1 * g1 + g2), rtol=1e-12)
+    np.testing.assert_allclose(v["w"], (1 - b2) * (b2 * g1 ** 2 + g2 ** 2), rtol=1e-12)
+
+
 def test_adam_first_step_closed_form():
     # from zero moments the bias-corrected first step is -lr * g / (|g| + eps)
     g = {"w": np.array([0.5, -2.0, 1e-3])}
