@@ -25,6 +25,9 @@ computes the plain definition of what the GPU path computes:
 * :func:`partition` -- Alg. 1 ``Partition`` with the readings listed in the
   design notes (medoid sample rule, tie-breaks).
 * :func:`merge_tree` -- the post-order merge of section "Merging".
+* :func:`partition_levels`, :func:`merge_tree_levels` -- the same two with
+  the distances / alignments of one tree level gathered into one batch, for
+  sets too large for the per-pair versions (pinned to them in the tests).
 * :func:`msa_metrics` -- the alignment quality metrics of section
   "Evaluation": percentage of gaps, p-score, distance distortion.
 
@@ -613,6 +616,148 @@ def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1, gap_open=None):
         msa[k] = ([bytes(r) for r in newL] + [bytes(r) for r in newR], ordL + ordR)
     rows, order = msa[0]
     return rows, order, merges
+
+
+def _arena_of(seqs):
+    lens = np.array([len(x) for x in seqs], np.int64)
+    offs = np.zeros(len(seqs) + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    arena = np.frombuffer(b"".join(bytes(x) for x in seqs) + b"\0", np.uint8).copy()
+    return arena, offs
+
+
+def partition_levels(seqs, nthreads=None, max_levels=None):
+    """The tree of :func:`partition`, with the distances of all clusters of
+    one tree level computed together.
+
+    Alg. 1 is applied to every cluster exactly as :func:`partition_step`
+    does (same medoid candidates, sums, poles, split and tie rules), and the
+    nodes are numbered in the same breadth-first order; only the Levenshtein
+    distances of each step are gathered over the clusters of a level and
+    handed to :func:`lev_pairs` as one batch (clusters of one level are
+    disjoint, so no step waits on another cluster's).  Used where the plain
+    per-pair version would take hours (10,000 sequences); tests pin it to
+    :func:`partition` on small sets.  With ``max_levels`` only that many
+    levels are split (``max_levels=1``: one application of Alg. 1 to the
+    whole set, the batched form of :func:`partition_step`).
+    """
+    arena, offs = _arena_of(seqs)
+
+    def batch(pairs):
+        if not pairs:
+            return np.zeros(0, np.int32)
+        return lev_pairs(arena, offs, np.array(pairs, np.int32), nthreads)
+
+    nodes = [dict(members=sorted(range(len(seqs))), center=-1, left=-1, right=-1, parent=-1)]
+    level = [0]
+    depth = 0
+    while level and (max_levels is None or depth < max_levels):
+        depth += 1
+        work = []
+        for q in level:
+            C = nodes[q]["members"]
+            if len(C) == 1:
+                nodes[q]["center"] = C[0]
+            else:
+                work.append(q)
+        # geometric median over the candidates: sums of f over all pairs of S
+        med_pairs, spans = [], []
+        for q in work:
+            S = medoid_candidates(nodes[q]["members"])
+            start = len(med_pairs)
+            med_pairs += [(S[i], S[j]) for i in range(len(S)) for j in range(i + 1, len(S))]
+            spans.append((S, start))
+        dm = batch(med_pairs)
+        center = {}
+        for q, (S, start) in zip(work, spans):
+            sums = {x: 0 for x in S}
+            for t, (x, y) in enumerate(med_pairs[start:start + len(S) * (len(S) - 1) // 2]):
+                sums[x] += int(dm[start + t])
+                sums[y] += int(dm[start + t])
+            center[q] = min((sums[x], x) for x in S)[1]
+
+        def far(frm):
+            pairs = [(frm[q], x) for q in work for x in nodes[q]["members"]]
+            d = batch(pairs)
+            out, o = {}, 0
+            for q in work:
+                C = nodes[q]["members"]
+                out[q] = d[o:o + len(C)]
+                o += len(C)
+            return out
+
+        dc = far(center)
+        pole_l = {q: min((-int(dc[q][i]), x) for i, x in enumerate(nodes[q]["members"]))[1] for q in work}
+        dl = far(pole_l)
+        pole_r = {q: min((-int(dl[q][i]), x) for i, x in enumerate(nodes[q]["members"]))[1] for q in work}
+        dr = far(pole_r)
+        nxt = []
+        for q in level:
+            node = nodes[q]
+            if q not in center:
+                continue
+            node["center"] = center[q]
+            C = node["members"]
+            Lm = [x for i, x in enumerate(C) if dl[q][i] <= dr[q][i]]
+            Rm = [x for i, x in enumerate(C) if dr[q][i] < dl[q][i]]
+            assert Lm and Rm, "de-duplicated input guarantees both children are non-empty"
+            for side, mem in (("left", Lm), ("right", Rm)):
+                node[side] = len(nodes)
+                nxt.append(len(nodes))
+                nodes.append(dict(members=mem, center=-1, left=-1, right=-1, parent=q))
+        level = nxt
+    return nodes
+
+
+def merge_tree_levels(seqs, nodes, match=0, mismatch=1, gap=1, nthreads=None):
+    """The merge of :func:`merge_tree`, with the center alignments of all
+    nodes of one height computed as one :func:`nw_pairs` batch and the MSAs
+    held as 2-D byte arrays.
+
+    A node's height is 1 + the larger of its children's (leaves 0); merges of
+    one height touch disjoint subtrees whose children are all finished, so
+    the result is the post-order result.  Each merge is the step of section
+    "Merging" as :func:`merge_tree` takes it: align the children's center
+    rows (``-`` an ordinary symbol), put an all-gap column into the left
+    rows for every ``I`` and into the right rows for every ``D``, left rows
+    over right rows.  Returns ``(rows, order, merges)`` like
+    :func:`merge_tree`.  Tests pin it to :func:`merge_tree` on small sets.
+    """
+    gapb = ord("-")
+    height = [0] * len(nodes)
+    for k in range(len(nodes) - 1, -1, -1):
+        if nodes[k]["left"] >= 0:
+            height[k] = 1 + max(height[nodes[k]["left"]], height[nodes[k]["right"]])
+    msa = {}
+    for k, nd in enumerate(nodes):
+        if nd["left"] < 0:
+            s = nd["members"][0]
+            msa[k] = (np.frombuffer(bytes(seqs[s]), np.uint8).reshape(1, -1).copy(), [s])
+    merges = {}
+    for h in range(1, max(height) + 1 if nodes else 1):
+        ks = [k for k in range(len(nodes)) if height[k] == h]
+        rows = []
+        for k in ks:
+            for child in (nodes[k]["left"], nodes[k]["right"]):
+                block, order = msa[child]
+                rows.append(block[order.index(nodes[child]["center"])].tobytes())
+        arena, offs = _arena_of(rows)
+        pairs = np.arange(2 * len(ks), dtype=np.int32).reshape(-1, 2)
+        score, ops, ops_off, ops_len = nw_pairs(arena, offs, pairs, match, mismatch, gap, nthreads)
+        for t, k in enumerate(ks):
+            op = ops[ops_off[t]:ops_off[t] + ops_len[t]]
+            merges[k] = (int(score[t]), op.tobytes())
+            bl, ol = msa.pop(nodes[k]["left"])
+            br, orr = msa.pop(nodes[k]["right"])
+            take_l = np.isin(op, (ord("M"), ord("X"), ord("D")))
+            take_r = np.isin(op, (ord("M"), ord("X"), ord("I")))
+            newl = np.full((bl.shape[0], len(op)), gapb, np.uint8)
+            newr = np.full((br.shape[0], len(op)), gapb, np.uint8)
+            newl[:, take_l] = bl
+            newr[:, take_r] = br
+            msa[k] = (np.concatenate([newl, newr]), ol + orr)
+    rows, order = msa[0]
+    return [r.tobytes() for r in rows], order, merges
 
 
 # ---------------------------------------------------------------------------

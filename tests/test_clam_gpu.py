@@ -99,6 +99,29 @@ def test_larger_tree_sampled_nodes(ctx):
     assert not np.any(np.all(rows == ord("-"), axis=0))
 
 
+def test_protein_families_tree_and_merges_full_size(ctx):
+    """The 10,000-protein workload (100 families, 10-40% mutation): Alg. 1
+    over all members and all 9,999 guide-tree merges, against the oracle
+    run end to end on the same sequences (its level-batched partition and
+    merge): every node and centre, every merge cost, and every row of the
+    root MSA -- which fixes each merge's edit script, since a node's columns
+    are the root columns its members' residues occupy."""
+    members, _ = synth.protein_families(seed=3)
+    assert members.n == 10000
+    seqs = members.seqs()
+    sq, tree, width, score, rows = _full(ctx, members)
+    assert tree.n_nodes == 2 * members.n - 1
+    ref_nodes = oracle.partition_levels(seqs)
+    _check_same_tree(_gpu_nodes(tree), ref_nodes)
+    ref_rows, ref_order, merges = oracle.merge_tree_levels(seqs, ref_nodes)
+    assert list(tree.order.cpu().numpy()) == ref_order
+    assert len(merges) == 9999
+    for k, (sc, _) in merges.items():
+        assert score[k] == sc
+    assert width[0] == len(ref_rows[0])
+    assert [r.tobytes() for r in rows] == ref_rows
+
+
 @pytest.mark.parametrize("gamma", [0.2, -0.9])
 def test_banded_partition_same_tree(ctx, gamma):
     """Alg. 1 with every distance batch from the network's band and the

@@ -212,6 +212,29 @@ def test_merge_postconditions():
     assert len(merges) == ds.n - 1
 
 
+@pytest.mark.parametrize("maker", [lambda: synth.SeqSet.from_list([b"A" * k for k in range(1, 8)]),
+                                   lambda: synth.small_dna(seed=1),
+                                   lambda: synth.protein_families(seed=3, n_fam=3, per_fam=30)[0]])
+def test_level_batched_partition_and_merge_equal_plain(maker):
+    """The level-batched oracle (distances and alignments of one tree level
+    gathered into one batch) gives node for node the tree of the per-pair
+    partition and row for row its merge, scripts and scores included."""
+    seqs = maker().seqs()
+    plain = oracle.partition(seqs)
+    assert oracle.partition_levels(seqs, nthreads=3) == plain
+    assert oracle.merge_tree_levels(seqs, plain, nthreads=2) == oracle.merge_tree(seqs, plain)
+
+
+def test_level_batched_single_step_with_sampled_medoid():
+    """max_levels=1 is one application of Alg. 1: on 300 sequences the
+    medoid comes from the 256-member sample, as in partition_step."""
+    seqs = synth.tree_dna(seed=8, n=300, root_len=160).seqs()
+    nodes = oracle.partition_levels(seqs, max_levels=1)
+    c, l, r, L, R = oracle.partition_step(list(range(len(seqs))), oracle._default_dist(seqs))
+    assert len(nodes) == 3 and nodes[0]["center"] == c
+    assert nodes[1]["members"] == L and nodes[2]["members"] == R
+
+
 # ---------------------------------------------------------------------------
 # features and network
 # ---------------------------------------------------------------------------
@@ -347,20 +370,6 @@ def test_mlp_forward_rounding_sites(site, x0, kw, expect):
     X[0, 0] = np.float32(x0)
     y, _ = oracle.mlp_forward(_one_path(**kw), X)
     assert y[0] == expect
-
-
-def test_forward_tie_enumeration_finds_planted_flip():
-    """The rounding-choice enumeration used by the GPU forward check: a row
-    built to sit exactly on a bf16 boundary yields both outcomes, a row away
-    from every boundary only the oracle's."""
-    from mlp_ties import forward_candidates
-    op = _one_path(b1=2 ** -8, b2=-0.5)   # z1 = 1 + 2^-8: halfway between bf16 values 1 and 1 + 2^-7
-    x = np.zeros(256)
-    x[0] = 1.0
-    cands, ties = forward_candidates(op, x)
-    assert ties == 1 and sorted(cands) == [0.5, 0.5 + 2 ** -7]
-    cands, ties = forward_candidates(_one_path(b1=2 ** -6, b2=-0.5), x)
-    assert ties == 0 and cands == [0.5 + 2 ** -6]
 
 
 def test_adam_second_step_closed_form():
