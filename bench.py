@@ -52,8 +52,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (for profiling)")
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band measurement")
     ap.add_argument("--band-pairs", type=int, default=100000)
-    ap.add_argument("--clam", type=int, default=0, metavar="N",
-                    help="also build the guide tree and merge N 16S-like sequences (the 50,000 workload: --clam 50000)")
+    ap.add_argument("--band-oracle-pairs", type=int, default=20000,
+                    help="learned-band pairs checked against the oracle")
+    ap.add_argument("--clam", type=int, default=50000, metavar="N",
+                    help="guide tree and merges of N 16S-like sequences (0 skips)")
+    ap.add_argument("--no-protein", action="store_true", help="skip the 10,000-protein section")
+    ap.add_argument("--merge-checks", type=int, default=1000, help="guide-tree merges checked against the oracle")
     return ap.parse_args()
 
 
@@ -95,7 +99,11 @@ def make_workload(n):
 
 def cpu_oracle_sample(ds, pairs, seconds, seed=7, single=True):
     """Time the oracle on a seeded sample of pairs sized to about `seconds`
-    on all host cores, and (single) on one thread over part of it."""
+    on all host cores, and (single) on one thread over part of it.
+
+    Returns ``(info, cells, seconds, sample_index, oracle_distances)``: the
+    sample's oracle distances are kept so the caller can compare them with
+    the GPU's output for the same pairs."""
     import oracle
     threads = oracle.cpu_threads()
     rng = np.random.default_rng(seed)
@@ -106,15 +114,16 @@ def cpu_oracle_sample(ds, pairs, seconds, seed=7, single=True):
     dt = time.perf_counter() - t0
     per_pair = dt / len(calib)
     k = int(max(threads, min(len(pairs), seconds / max(per_pair, 1e-9))))
-    sample = pairs[rng.choice(len(pairs), size=k, replace=False)]
+    idx = np.sort(rng.choice(len(pairs), size=k, replace=False))
+    sample = pairs[idx]
     t0 = time.perf_counter()
-    oracle.lev_pairs(ds.arena, ds.offs, sample, nthreads=threads)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, sample, nthreads=threads)
     dt = time.perf_counter() - t0
     cells = int((lens[sample[:, 0]].astype(np.int64) * lens[sample[:, 1]]).sum())
     info = dict(value=cells / dt / 1e9, unit="GCUPS", cores=threads, kind="oracle",
                 sample=f"{k} random pairs of the workload ({cells:.3e} cells, {dt:.1f} s)")
     if not single:
-        return info, cells, dt
+        return info, cells, dt, idx, ref
     # the same oracle on one thread, over a sample of about a fifth of the time
     k1 = int(max(1, min(len(pairs), seconds / 5 / max(per_pair * threads, 1e-9))))
     s1 = sample[:k1]
@@ -124,7 +133,14 @@ def cpu_oracle_sample(ds, pairs, seconds, seed=7, single=True):
     cells1 = int((lens[s1[:, 0]].astype(np.int64) * lens[s1[:, 1]]).sum())
     info["single_thread"] = dict(value=cells1 / dt1 / 1e9, unit="GCUPS", cores=1,
                                  sample=f"the first {k1} of those pairs ({cells1:.3e} cells, {dt1:.1f} s)")
-    return info, cells, dt
+    return info, cells, dt, idx, ref
+
+
+def distance_invariants(d, pairs, offs):
+    """Pairs whose distance breaks |m - n| <= d <= max(m, n) (true for any f)."""
+    lens = np.diff(offs)
+    a, b = lens[pairs[:, 0]], lens[pairs[:, 1]]
+    return int(np.sum((d < np.abs(a - b)) | (d > np.maximum(a, b))))
 
 
 class ClockSampler:
@@ -243,15 +259,10 @@ def band_bench(ctx, args, stream):
     k_l1 = torch.maximum(dl, ((l1 + 7) // 8).int())
     d_l1, _ = api.lev_banded_batch(ctx, es, pairs, k_l1)
     ctx.check()
-    mism = (int((d_band != d_full).sum().item()) + int((d_l1 != d_full).sum().item())
-            + int((d_raw != d_full).sum().item()))
-    first = float((k_used.cpu().numpy() < np.maximum(lens[0::2], lens[1::2])).mean())
-    import oracle
-    rng = np.random.default_rng(9)
-    samp = np.sort(rng.choice(P, size=48, replace=False))
-    host_pairs = pairs.cpu().numpy()
-    ref = oracle.lev_pairs(ev.arena, ev.offs, host_pairs[samp])
-    mism += int((ref != d_full.cpu().numpy()[samp]).sum())
+    # every banded result (learned, network alone, L1 bound) against the full DP on all pairs
+    mism_full = dict(learned=int((d_band != d_full).sum().item()), uncalibrated=int((d_raw != d_full).sum().item()),
+                     l1_bound=int((d_l1 != d_full).sum().item()))
+    band_share = float((k_used.cpu().numpy() < np.maximum(lens[0::2], lens[1::2])).mean())
 
     def timed(fn, reps):
         fn()
@@ -272,6 +283,17 @@ def band_bench(ctx, args, stream):
     t_l1 = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_l1, d_l1), reps)
     t_raw = timed(lambda: api.lev_banded_batch(ctx, es, pairs, k_raw, d_raw), reps)
     ctx.check()
+    # the timed outputs against the oracle on a seeded sample of the pairs
+    import oracle
+    rng = np.random.default_rng(9)
+    samp = np.sort(rng.choice(P, size=min(P, args.band_oracle_pairs), replace=False))
+    host_pairs = pairs.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = oracle.lev_pairs(ev.arena, ev.offs, host_pairs[samp])
+    t_oracle = time.perf_counter() - t0
+    mism_oracle = dict(learned=int((ref != d_band.cpu().numpy()[samp]).sum()),
+                       full=int((ref != d_full.cpu().numpy()[samp]).sum()))
+    mism = sum(mism_full.values()) + sum(mism_oracle.values())
     args.band_model = (model, gamma)
     return dict(workload=f"divergent_dna_pairs_{P}_len1000-10000_div1-30pct", pairs=P, cells=cells,
                 pairs_per_s_learned=P / (t_band / 1e3), pairs_per_s_full=P / (t_full / 1e3),
@@ -283,15 +305,111 @@ def band_bench(ctx, args, stream):
                                  k_mean_over_f_uncalibrated=float(
                                      (k_raw.double() / d_full.double().clamp(min=1)).mean().item())),
                 gcups_full=cells / (t_full / 1e3) / 1e9, gcups_equiv_learned=cells / (t_band / 1e3) / 1e9,
-                ms_learned=t_band, ms_full=t_full, mismatches=mism, oracle_sample=len(samp),
-                certified_by_band=first, gamma=gamma, train_pairs=tinfo["pairs"], train_steps=minfo["steps"],
-                val_pinball=minfo["val_loss"], setup_s=setup_s)
+                ms_learned=t_band, ms_full=t_full, mismatches=mism,
+                parity=dict(oracle_pairs=int(len(samp)), oracle_seconds=t_oracle,
+                            mismatches_vs_oracle=mism_oracle, mismatches_vs_full_dp_all_pairs=mism_full),
+                share_certified_by_band=band_share, gamma=gamma, train_pairs=tinfo["pairs"],
+                train_steps=minfo["steps"], val_pinball=minfo["val_loss"], setup_s=setup_s)
+
+
+def _cols_of(tree, order, k, offs, pos_h):
+    """Root-MSA columns of node k: those its members' residues occupy (a
+    node's MSA has no all-gap column, so these are exactly its columns)."""
+    mem = order[tree.lo[k]:tree.hi[k]]
+    parts = [pos_h[offs[s]:offs[s + 1]] for s in mem]
+    return np.unique(np.concatenate(parts)) if parts else np.zeros(0, np.int32)
+
+
+def stepwise_merge_check(ds, tree, pos_h, width, score, nodes, gap=ord("-")):
+    """Each sampled merge redone by the oracle on the same inputs.
+
+    For merge k the two children's centre rows, as gapped rows of the
+    children's MSAs, are read back from the root MSA (positions `pos`),
+    aligned by oracle.nw, and the oracle's cost and edit script are compared
+    with the GPU's cost and with the script the GPU's MSA realises (a column
+    of both children is a diagonal move, one of the left child only D, of
+    the right child only I).  Together with the same check one level down
+    this is an inductive check of the whole merge."""
+    import oracle
+    order = tree.order.cpu().numpy()
+    offs, arena = ds.offs, ds.arena
+    rows, got_ops, bad_width = [], [], 0
+    for k in nodes:
+        L, R = int(tree.left[k]), int(tree.right[k])
+        cl, cr = _cols_of(tree, order, L, offs, pos_h), _cols_of(tree, order, R, offs, pos_h)
+        crow = []
+        for child, cols in ((L, cl), (R, cr)):
+            c = int(tree.center[child])
+            row = np.full(len(cols), gap, np.uint8)
+            row[np.searchsorted(cols, pos_h[offs[c]:offs[c + 1]])] = arena[offs[c]:offs[c + 1]]
+            crow.append(row)
+        u = np.union1d(cl, cr)
+        inl, inr = np.isin(u, cl), np.isin(u, cr)
+        il, ir = np.maximum(np.cumsum(inl) - 1, 0), np.maximum(np.cumsum(inr) - 1, 0)
+        same = crow[0][il] == crow[1][ir]
+        op = np.where(inl & inr, np.where(same, ord("M"), ord("X")), np.where(inl, ord("D"), ord("I")))
+        got_ops.append(op.astype(np.uint8).tobytes())
+        bad_width += int(len(u) != width[k] or len(cl) != width[L] or len(cr) != width[R])
+        rows += [r.tobytes() for r in crow]
+    lens = np.array([len(r) for r in rows], np.int64)
+    roffs = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(lens, out=roffs[1:])
+    rarena = np.frombuffer(b"".join(rows) + b"\0", np.uint8)
+    sc, ops, ooff, oln = oracle.nw_pairs(rarena, roffs, np.arange(len(rows), dtype=np.int32).reshape(-1, 2))
+    bad_score = bad_ops = 0
+    for t, k in enumerate(nodes):
+        bad_score += int(sc[t] != score[k])
+        bad_ops += int(ops[ooff[t]:ooff[t] + oln[t]].tobytes() != got_ops[t])
+    return dict(merges=len(nodes), score_mismatches=bad_score, script_mismatches=bad_ops,
+                width_mismatches=bad_width, cells=int(sum(len(rows[2 * t]) * len(rows[2 * t + 1])
+                                                          for t in range(len(nodes)))))
+
+
+def cluster_checks(seqs, tree, picks):
+    """Alg. 1 redone by the oracle (one batched application) on the GPU
+    tree's clusters `picks`: centre and split must agree."""
+    import oracle
+    order = tree.order.cpu().numpy()
+    bad = 0
+    sizes = []
+    for k in picks:
+        mem = sorted(int(x) for x in order[tree.lo[k]:tree.hi[k]])
+        nodes = oracle.partition_levels([seqs[x] for x in mem], max_levels=1)
+        c = mem[nodes[0]["center"]]
+        L = [mem[i] for i in nodes[1]["members"]]
+        gl = sorted(int(x) for x in order[tree.lo[tree.left[k]]:tree.hi[tree.left[k]]])
+        bad += int(c != int(tree.center[k]) or L != gl)
+        sizes.append(len(mem))
+    return dict(clusters=len(picks), mismatches=bad, sizes_checked=f"{min(sizes)}-{max(sizes)}" if sizes else "",
+                sampled_medoid=int(sum(x > 256 for x in sizes)))
+
+
+def pick_checks(tree, rng, n_merges, n_small=30, n_big=2):
+    """Internal nodes to check: the root plus a seeded sample for merges;
+    the two smallest clusters above 256 members (medoid from the 256-member
+    sample) and a sample of clusters of 2-64 for Alg. 1."""
+    internal = np.nonzero(tree.left[:tree.n_nodes] >= 0)[0]
+    size = tree.hi[:tree.n_nodes] - tree.lo[:tree.n_nodes]
+    merges = [0] + list(rng.choice(internal[1:], min(n_merges, len(internal) - 1), replace=False))
+    big = sorted((int(size[k]), int(k)) for k in internal if size[k] > 256)[:n_big]
+    small = [k for k in internal if 2 <= size[k] <= 64]
+    small = list(rng.choice(small, min(n_small, len(small)), replace=False))
+    return [int(k) for k in merges], [k for _, k in big] + [int(k) for k in small]
+
+
+def rows_match_sequences(rows_h, order, ds, gap=ord("-")):
+    """Every MSA row with its gaps removed is its sequence (one vectorised
+    comparison over all rows)."""
+    flat = rows_h[rows_h != gap]
+    ref = np.concatenate([ds.arena[ds.offs[s]:ds.offs[s + 1]] for s in order])
+    return bool(len(flat) == len(ref) and np.array_equal(flat, ref))
 
 
 def clam_bench(ctx, args):
     """Guide tree (Alg. 1) and bottom-up merges on N 16S-like sequences
-    (lengths 1,400-1,600), with Alg. 1 redone by the oracle on sampled
-    clusters and the MSA rows checked against their sequences."""
+    (lengths 1,400-1,600), learned band on and off; Alg. 1 redone by the
+    oracle on sampled clusters, sampled merges redone by the oracle on the
+    same centre rows, every MSA row checked against its sequence."""
     import torch
     from paper_2601_15458_gb300 import api, synth
     from paper_2601_15458_gb300 import learned_band
@@ -338,20 +456,18 @@ def clam_bench(ctx, args):
     t0 = time.perf_counter()
     met = api.msa_metrics(ctx, sq, tree, rows, sample=min(10000, ds.n), seed=0)
     t_met = time.perf_counter() - t0
-    import oracle
+    # parity (outside every timed region)
+    t0 = time.perf_counter()
     order = tree.order.cpu().numpy()
+    rows_h = rows.cpu().numpy()
+    rows_ok = rows_match_sequences(rows_h, order, ds)
+    no_gap_col = not bool(np.any(np.all(rows_h == ord("-"), axis=0)))
+    del rows_h
     rng = np.random.default_rng(0)
-    seqs = ds.seqs()
-    bad = 0
-    for r in rng.choice(ds.n, 64, replace=False):
-        bad += rows[r].cpu().numpy().tobytes().replace(b"-", b"") != seqs[order[r]]
-    dist = oracle._default_dist(seqs)
-    internal = [k for k in range(tree.n_nodes) if tree.left[k] >= 0 and 2 <= tree.hi[k] - tree.lo[k] <= 24]
-    for k in rng.choice(internal, min(4, len(internal)), replace=False):
-        mem = sorted(int(x) for x in order[tree.lo[k]:tree.hi[k]])
-        c, l, r, L, R = oracle.partition_step(mem, dist)
-        Lg = sorted(int(x) for x in order[tree.lo[tree.left[k]]:tree.hi[tree.left[k]]])
-        bad += int(tree.center[k] != c or Lg != L)
+    merge_nodes, cluster_nodes = pick_checks(tree, rng, args.merge_checks)
+    mcheck = stepwise_merge_check(ds, tree, pos.cpu().numpy(), width, score, merge_nodes)
+    ccheck = cluster_checks(ds.seqs(), tree, cluster_nodes)
+    check_s = time.perf_counter() - t0
     depth = np.zeros(tree.n_nodes, np.int64)
     for k in range(1, tree.n_nodes):
         depth[k] = depth[tree.parent[k]] + 1
@@ -359,6 +475,8 @@ def clam_bench(ctx, args):
     for k in range(tree.n_nodes):
         if tree.left[k] >= 0:
             nw_cells += int(width[tree.left[k]]) * int(width[tree.right[k]])
+    mism = (mcheck["score_mismatches"] + mcheck["script_mismatches"] + mcheck["width_mismatches"]
+            + ccheck["mismatches"] + int(not rows_ok) + int(not no_gap_col) + int(not same_tree))
     return dict(workload=f"gg16s_dna_{ds.n}_len1400-1600", n_seqs=ds.n, partition_s=t_part, merge_s=t_merge,
                 partition_learned_band_s=t_part_b, learned_band_speedup=t_part / t_part_b,
                 learned_band_gamma=gamma, learned_band_same_tree=same_tree,
@@ -367,7 +485,101 @@ def clam_bench(ctx, args):
                 partition_dp_ms=part_dp_ms, merge_dp_ms=merge_dp_ms, launches=part_launches + merge_launches,
                 tree_depth=int(depth.max()), msa_width=int(width[0]), nw_cells=nw_cells,
                 nw_gcups=nw_cells / (merge_dp_ms / 1e3) / 1e9 if merge_dp_ms else None,
-                checks_failed=int(bad), generate_s=gen_s)
+                parity=dict(mismatches=mism, merges_vs_oracle=mcheck, clusters_vs_oracle=ccheck,
+                            all_rows_degap_to_sequences=rows_ok, no_all_gap_column=no_gap_col, seconds=check_s),
+                generate_s=gen_s)
+
+
+def protein_bench(ctx, args, stream):
+    """The 10,000-protein workload: 1,000,000 member-to-family-root distances
+    (one-to-many by root) and the guide tree with its 9,999 merges; oracle
+    checks on a 100,000-pair sample of the distances, on sampled clusters and
+    on 1,000 sampled merges (the tests check every distance, node and row)."""
+    import torch
+    import oracle
+    from paper_2601_15458_gb300 import api, synth
+    members, roots = synth.protein_families(seed=3)
+    allseq = synth.SeqSet.from_list(members.seqs() + roots.seqs(), "protein")
+    nm = members.n
+    pairs_h = np.array([[nm + c, x] for c in range(roots.n) for x in range(nm)], np.int32)
+    lens = np.diff(allseq.offs)
+    cells = int((lens[pairs_h[:, 0]].astype(np.int64) * lens[pairs_h[:, 1]]).sum())
+    sq = api.upload_and_pack(ctx, allseq)
+    pairs = torch.from_numpy(pairs_h).cuda()
+    d = api.lev_batch(ctx, sq, pairs)
+
+    def timed(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_dist = timed(lambda: api.lev_batch(ctx, sq, pairs, d))
+    msq = api.upload_and_pack(ctx, members)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = api.clam_partition(ctx, msq)
+    torch.cuda.synchronize()
+    t_part = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pos, width, score = api.merge_tree(ctx, msq, tree)
+    torch.cuda.synchronize()
+    t_merge = time.perf_counter() - t0
+    rows = api.msa_rows(ctx, msq, tree, pos, int(width[0]))
+    ctx.check()
+    t0 = time.perf_counter()
+    got = d.cpu().numpy()
+    rng = np.random.default_rng(5)
+    samp = np.sort(rng.choice(len(pairs_h), size=100000, replace=False))
+    dmis = int((oracle.lev_pairs(allseq.arena, allseq.offs, pairs_h[samp]) != got[samp]).sum())
+    inv = distance_invariants(got, pairs_h, allseq.offs)
+    rows_ok = rows_match_sequences(rows.cpu().numpy(), tree.order.cpu().numpy(), members)
+    merge_nodes, cluster_nodes = pick_checks(tree, rng, args.merge_checks)
+    mcheck = stepwise_merge_check(members, tree, pos.cpu().numpy(), width, score, merge_nodes)
+    ccheck = cluster_checks(members.seqs(), tree, cluster_nodes)
+    check_s = time.perf_counter() - t0
+    mism = (dmis + inv + mcheck["score_mismatches"] + mcheck["script_mismatches"] + mcheck["width_mismatches"]
+            + ccheck["mismatches"] + int(not rows_ok))
+    return dict(workload="protein_families_10000x100", pairs=len(pairs_h), cells=cells, ms_distances=t_dist,
+                gcups_distances=cells / (t_dist / 1e3) / 1e9, partition_s=t_part, merge_s=t_merge,
+                merges=int(tree.n_nodes - members.n), msa_width=int(width[0]),
+                parity=dict(mismatches=mism, oracle_pairs=len(samp), distance_mismatches=dmis,
+                            invariant_violations=inv, merges_vs_oracle=mcheck, clusters_vs_oracle=ccheck,
+                            all_rows_degap_to_sequences=rows_ok, seconds=check_s))
+
+
+def small_bench(ctx):
+    """The 64-sequence DNA case checked in full: all 2,016 distances, the
+    guide tree node for node and the 63 merges row for row."""
+    import oracle
+    from paper_2601_15458_gb300 import api, synth
+    ds = synth.small_dna(seed=1)
+    seqs = ds.seqs()
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = synth.all_pairs(ds.n)
+    d = api.lev_batch(ctx, sq, pairs).cpu().numpy()
+    tree = api.clam_partition(ctx, sq)
+    pos, width, score = api.merge_tree(ctx, sq, tree)
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0])).cpu().numpy()
+    ctx.check()
+    ref_d = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    ref_nodes = oracle.partition(seqs)
+    ref_rows, ref_order, merges = oracle.merge_tree(seqs, ref_nodes)
+    order = tree.order.cpu().numpy()
+    node_mis = 0
+    for k, nd in enumerate(ref_nodes):
+        node_mis += int(sorted(int(x) for x in order[tree.lo[k]:tree.hi[k]]) != nd["members"]
+                        or int(tree.center[k]) != nd["center"])
+    return dict(workload="small_dna_64x150", pairs=len(pairs), distance_mismatches=int((d != ref_d).sum()),
+                node_mismatches=node_mis + int(tree.n_nodes != len(ref_nodes)),
+                merge_score_mismatches=int(sum(score[k] != sc for k, (sc, _) in merges.items())),
+                row_mismatches=int(sum(r.tobytes() != q for r, q in zip(rows, ref_rows))) + int(list(order) != ref_order))
 
 
 def run_reference(args, rank, world):
@@ -381,7 +593,7 @@ def run_reference(args, rank, world):
     total_t = 0.0
     info = None
     for s in range(args.warmup + args.steps):
-        info, c, dt = cpu_oracle_sample(ds, pairs, per_step, seed=100 + s, single=False)
+        info, c, dt, _, _ = cpu_oracle_sample(ds, pairs, per_step, seed=100 + s, single=False)
         if s >= args.warmup:
             vals.append(info["value"])
             total_cells += c
@@ -456,6 +668,7 @@ def main():
     ctx.prof_enable(False)
     dp_ms, launches = ctx.prof_read(reset=True)
     ctx.check()
+    out_timed = out.cpu().numpy()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     total_ms, dp_ms = max_over_ranks([total_ms, dp_ms], world)
@@ -527,9 +740,20 @@ def main():
     if not args.no_band:
         band = band_bench(ctx, args, stream)
     clam = clam_bench(ctx, args) if args.clam else None
+    protein = None if args.no_protein else protein_bench(ctx, args, stream)
+    small = small_bench(ctx)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _, _ = cpu_oracle_sample(ds, pairs, args.cpu_seconds)
+    parity = None
+    if rank == 0:
+        # the oracle on a seeded sample of the workload: timed as the CPU
+        # baseline (one rank, N = 1) and compared with the timed GPU output
+        secs = args.cpu_seconds if (world == 1 and not args.no_cpu_baseline) else 5.0
+        info, _, _, idx, ref = cpu_oracle_sample(ds, pairs, secs, single=world == 1)
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = info
+        parity = dict(oracle_pairs=int(len(idx)), mismatches=int((out_timed[idx] != ref).sum()),
+                      invariant_violations=distance_invariants(out_timed, pairs, ds.offs),
+                      checked="the distances of the last timed step")
     if rank == 0:
         line = dict(metric="GCUPS", value=value, unit="GCUPS", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
@@ -538,10 +762,11 @@ def main():
                                 pairs_per_s=world * len(pairs) * args.steps / (total_ms / 1e3),
                                 l2="flushed between timed steps (256 MB write)", step="msa_pack + msa_lev_batch",
                                 schedule=dict(api.lev_schedule(ctx), autotuned=not args.no_autotune)),
-                    roofline=roof, cpu_baseline=cpu,
+                    roofline=roof, cpu_baseline=cpu, parity=parity,
                     e2e=dict(value=e2e_value, unit="GCUPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                              output_matches_device=bool(ok)),
                     gpu_launches=launches, dp_kernel_ms_per_step=dp_ms / args.steps, band=band, clam=clam,
+                    protein=protein, small=small,
                     wall_s_timed=t_wall, clocks=clocks)
         print(json.dumps(line), flush=True)
     ctx.close()
