@@ -432,6 +432,22 @@ msa_status msa_msa_metrics(msa_ctx *ctx, const msa_seqset *s, const uint8_t *row
                            const int32_t *sample_rows, const int32_t *sample_seqs, int32_t S, uint8_t gap,
                            double *out3, int64_t *counts4, void *stream);
 
+/* ---- measurement ---------------------------------------------------------- */
+/*
+ * Integer-pipe throughput probe (no counterpart in the paper: it measures the
+ * roofline denominator of the bit-vector kernels, whose word step is 3-input
+ * logic, an add on the carry chain and a funnel shift).  Launches one kernel
+ * on `stream` that runs, from registers only, op = 0 LOP3, 1 funnel shift by
+ * one, 2 add with carry (8-word chains), 3 the Levenshtein word step
+ * (9 operations per 32-row word, two independent columns per thread),
+ * 4 integer multiply-add (the FMA pipe, for comparison), with 8 independent
+ * chains per thread and every SM at its occupancy limit, `iters` loop
+ * iterations.  *lane_ops (host) receives the number of lane operations the
+ * launch executes; time the launch with CUDA events on `stream` and divide.
+ * Uses the context workspace as the kernel's output sink.
+ */
+msa_status msa_probe_int_pipe(msa_ctx *ctx, int32_t op, int32_t iters, int64_t *lane_ops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ SIGNATURES = {
                                   c_int32, ctypes.c_uint8, c_void_p, c_void_p, c_void_p]),
     "msa_msa_rows": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int32, c_void_p,
                                c_void_p]),
+    "msa_probe_int_pipe": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_int64), c_void_p]),
 }
 
 

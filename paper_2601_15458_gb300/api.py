@@ -478,3 +478,29 @@ def msa_metrics(ctx: Context, seqs: DeviceSeqs, tree: Tree, rows: torch.Tensor, 
                                             _stream(stream)))
     return dict(pct_gaps=float(out[0]), p_score=float(out[1]), distortion=float(out[2]), rows=int(len(pick)),
                 gaps=int(cnt[0]), compared=int(cnt[1]), mismatched=int(cnt[2]), pairs=int(cnt[3]), sample=pick)
+
+
+# ---------------------------------------------------------------------------
+# measurement
+# ---------------------------------------------------------------------------
+
+PROBE_OPS = {"lop3": 0, "shf": 1, "addc": 2, "word_step": 3, "imad": 4}
+
+
+def probe_int_pipe(ctx: Context, op: str, iters: int = 4096, reps: int = 3, stream=None) -> dict:
+    """Measured throughput of one integer operation kind (msa_probe_int_pipe):
+    the best of ``reps`` timed launches after a warm-up, in lane-ops/s."""
+    code = PROBE_OPS[op]
+    n = ctypes.c_int64(0)
+    st = _stream(stream)
+    ctx.raise_if(_lib.lib().msa_probe_int_pipe(ctx.handle, code, int(iters), ctypes.byref(n), st))
+    best = float("inf")
+    cur = torch.cuda.current_stream() if stream is None else stream
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        ctx.raise_if(_lib.lib().msa_probe_int_pipe(ctx.handle, code, int(iters), ctypes.byref(n), st))
+        b.record(cur)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return dict(op=op, lane_ops=int(n.value), ms=best, ops_per_s=n.value / (best / 1e3))

@@ -356,6 +356,13 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
     Arena base{ctx->ws, ctx->ws_bytes};
     int32_t *order_tmp = base.take<int32_t>(N);
     if (!order_tmp) return set_error(ctx, MSA_ENOMEM, "msa_clam_partition: workspace");
+    // order_tmp mirrors order: each level's split rewrites the active ranges
+    // in order_tmp and one copy of the whole array brings them back (ranges
+    // that are no longer active are equal in both)
+    {
+        cudaError_t e = cudaMemcpyAsync(order_tmp, order, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "partition order copy");
+    }
     while (!active.empty()) {
         const int A = (int)active.size();
         std::vector<int32_t> hlo(A), hsz(A);
@@ -418,12 +425,10 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
         if ((rc = dist(pairs, PC, dr))) return rc;
         split_kernel<<<g, 1024, 0, st>>>(order, order_tmp, d_lo, d_sz, d_moff, A, dl, dr, d_nl);
         ctx->launches += 9;
-        // copy the partitioned ranges back (only the active ranges changed)
-        for (int k = 0; k < A; ++k) {
-            e = cudaMemcpyAsync(order + hlo[k], order_tmp + hlo[k], hsz[k] * sizeof(int32_t),
-                                cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return cuda_check(ctx, e, "partition copy");
-        }
+        // the partitioned ranges back, in one copy (a copy per cluster cost
+        // thousands of calls at the deep levels)
+        e = cudaMemcpyAsync(order, order_tmp, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "partition copy");
         std::vector<int32_t> nl(A), cc(A);
         if ((e = cudaMemcpyAsync(nl.data(), d_nl, A * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(cc.data(), d_c, A * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -79,16 +79,18 @@ def test_larger_tree_sampled_nodes(ctx):
     assert tree.n_nodes == 2 * ds.n - 1
     leaves = [nd for nd in nodes if nd["left"] < 0]
     assert sorted(nd["members"][0] for nd in leaves) == list(range(ds.n))
-    dist = oracle._default_dist(seqs)
     rng = np.random.default_rng(0)
     internal = [k for k, nd in enumerate(nodes) if nd["left"] >= 0]
     big = [k for k in internal if len(nodes[k]["members"]) > 256][:2]
     small = list(rng.choice([k for k in internal if 2 <= len(nodes[k]["members"]) <= 40], 6, replace=False))
     for k in big + small:
         nd = nodes[k]
-        c, l, r, L, R = oracle.partition_step(nd["members"], dist)
-        assert nd["center"] == c
-        assert nodes[nd["left"]]["members"] == L and nodes[nd["right"]]["members"] == R
+        mem = nd["members"]
+        # one application of Alg. 1 to the cluster (the oracle's batched step)
+        step = oracle.partition_levels([seqs[x] for x in mem], max_levels=1)
+        assert nd["center"] == mem[step[0]["center"]]
+        assert nodes[nd["left"]]["members"] == [mem[i] for i in step[1]["members"]]
+        assert nodes[nd["right"]]["members"] == [mem[i] for i in step[2]["members"]]
     # merge: rows de-gap to their sequences, equal widths
     pos, width, score = api.merge_tree(ctx, sq, tree)
     rows = api.msa_rows(ctx, sq, tree, pos, int(width[0])).cpu().numpy()

@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import oracle
+from mlp_ties import forward_candidates
 from paper_2601_15458_gb300 import api, synth
 
 pytestmark = pytest.mark.gpu
@@ -71,24 +72,29 @@ def _oracle_params(p):
 
 
 def test_forward_matches_oracle(ctx):
-    """Outputs within 1e-3 relative error of the float64 oracle, normwise
-    (max |got - ref| <= 1e-3 max |ref|).  Elementwise (relative to the
-    larger of |ref| and 10% of the output range) the same bound holds for at
-    least 99% of the rows: the kernel sums in fp32, so a hidden value lying
-    within the fp32 summation error of a bf16 rounding boundary may round to
-    the other neighbour and move its row by one bf16 step of that unit's
-    contribution, which the normwise bound still covers."""
+    """Every output within 1e-3 relative error of the float64 oracle
+    (relative to the larger of |ref| and 10% of the output range).  Where a
+    row misses that, a hidden unit sat on a bf16 rounding boundary within
+    the fp32 summation error (the kernel sums in fp32, the oracle in
+    float64): the row must then match, at the same bound, the oracle with
+    that unit rounded to its other neighbour (mlp_ties), and such rows must
+    be rare."""
     X, _ = _features(ctx)
     model = api.BandModel(ctx, seed=3)
     yh = model.forward(X)
     ctx.check()
     Xf = X.float().cpu().numpy().astype(np.float64)
-    ref, _ = oracle.mlp_forward(_oracle_params(model.params()), Xf)
+    op = _oracle_params(model.params())
+    ref, _ = oracle.mlp_forward(op, Xf)
     got = yh.cpu().numpy().astype(np.float64)
-    scale = np.abs(ref).max()
-    assert np.max(np.abs(got - ref)) <= 1e-3 * scale
-    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 0.1 * scale)
-    assert np.mean(rel <= 1e-3) >= 0.99
+    floor = 0.1 * np.abs(ref).max()
+    flipped = 0
+    for r in np.nonzero(np.abs(got - ref) > 1e-3 * np.maximum(np.abs(ref), floor))[0]:
+        cands, ties = forward_candidates(op, Xf[r])
+        err = min(abs(got[r] - c) / max(abs(c), floor) for c in cands)
+        assert err <= 1e-3, (int(r), got[r], ref[r], ties)
+        flipped += 1
+    assert flipped <= 0.02 * len(ref)
 
 
 def test_gradients_match_oracle(ctx):

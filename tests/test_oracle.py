@@ -372,6 +372,19 @@ def test_mlp_forward_rounding_sites(site, x0, kw, expect):
     assert y[0] == expect
 
 
+def test_forward_tie_enumeration_finds_planted_flip():
+    """The rounding-choice enumeration used by the GPU forward check: a row
+    built to sit exactly on a bf16 boundary yields both outcomes, a row away
+    from every boundary only the oracle's."""
+    from mlp_ties import forward_candidates
+    x = np.zeros(256)
+    x[0] = 1.0
+    cands, ties = forward_candidates(_one_path(b1=2 ** -8, b2=-0.5), x)   # z1 halfway between 1 and 1 + 2^-7
+    assert ties == 1 and sorted(cands) == [0.5, 0.5 + 2 ** -7]
+    cands, ties = forward_candidates(_one_path(b1=2 ** -6, b2=-0.5), x)
+    assert ties == 0 and cands == [0.5 + 2 ** -6]
+
+
 def test_adam_second_step_closed_form():
     # two steps from zero moments: m2 = (1 - b1)(b1 g1 + g2), v2 = (1 - b2)(b2 g1^2 + g2^2),
     # bias-corrected m2 / (1 - b1^2) = (b1 g1 + g2) / (1 + b1), v2 / (1 - b2^2) = (b2 g1^2 + g2^2) / (1 + b2)
