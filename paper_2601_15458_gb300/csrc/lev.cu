@@ -123,29 +123,101 @@ __global__ void count_kernel(PairList L, int32_t n, const int64_t *__restrict__ 
     }
 }
 
-// Exclusive scan of n ints by one block of 1024 threads (chunked).
-__global__ void __launch_bounds__(1024) scan_kernel(const int32_t *__restrict__ in, int32_t n,
-                                                    int32_t *__restrict__ out) {
-    __shared__ int32_t part[1024];
-    const int tid = threadIdx.x;
-    const int64_t chunk = (n + 1023) / 1024;
-    const int64_t lo = tid * chunk, hi = min((int64_t)n, lo + chunk);
-    int32_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += in[i];
-    part[tid] = s;
+// Exclusive scan of n ints in tiles of 4,096 (1,024 threads x 4 consecutive
+// values): one kernel sums each tile, a second scans each tile from the sum
+// of the tiles before it.  Loads and stores are coalesced and every tile has
+// its own block, so a scan over hundreds of thousands of queries takes a few
+// microseconds (one block walking the whole array took ~0.2 ms at 200,000).
+constexpr int kScanTile = 4096;
+
+__device__ __forceinline__ int32_t block_sum_1024(int32_t v, int32_t *wsum) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int32_t v = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    int32_t t = threadIdx.x < 32 ? wsum[threadIdx.x] : 0;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
-    int32_t run = tid ? part[tid - 1] : 0;
-    for (int64_t i = lo; i < hi; ++i) {
-        out[i] = run;
-        run += in[i];
+    __syncthreads();
+    if (threadIdx.x == 0) wsum[0] = t;
+    __syncthreads();
+    t = wsum[0];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(1024) tile_sum_kernel(const int32_t *__restrict__ in, int32_t n,
+                                                        int32_t *__restrict__ tsum) {
+    __shared__ int32_t wsum[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int32_t v = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = base + r * 1024 + threadIdx.x;
+        if (i < n) v += in[i];
     }
-    if (tid == 1023) out[n] = part[1023];
+    v = block_sum_1024(v, wsum);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const int32_t *__restrict__ in, int32_t n,
+                                                         const int32_t *__restrict__ tsum,
+                                                         int32_t *__restrict__ out) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t wpre[32];
+    // the sum of the tiles before this one
+    int32_t pre = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += 1024) pre += tsum[t];
+    pre = block_sum_1024(pre, wsum);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * (int64_t)threadIdx.x;
+    int32_t x[4];
+    int32_t own = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        x[r] = base + r < n ? in[base + r] : 0;
+        own += x[r];
+    }
+    // exclusive scan of the per-thread sums across the block
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wpre[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int32_t t = wpre[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wpre[lane] = t;
+    }
+    __syncthreads();
+    int32_t run = pre + (w ? wpre[w - 1] : 0) + inc - own;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (base + r < n) out[base + r] = run;
+        run += x[r];
+    }
+    // the total, once, by the thread that holds the last value
+    if (base < n && base + 4 >= n) out[n] = run;
+    if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+int64_t scan_tiles(int64_t n) { return std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile); }
+
+// out[0..n] = exclusive prefix sums of in[0..n) and the total; tsum holds
+// scan_tiles(n) ints of scratch.
+void exclusive_scan(const int32_t *in, int32_t n, int32_t *out, int32_t *tsum, cudaStream_t st) {
+    const int tiles = (int)scan_tiles(n);
+    tile_sum_kernel<<<tiles, 1024, 0, st>>>(in, n, tsum);
+    tile_scan_kernel<<<tiles, 1024, 0, st>>>(in, n, tsum, out);
 }
 
 __global__ void scatter_kernel(PairList L, int32_t n, const int64_t *__restrict__ offs, int64_t total,
@@ -231,7 +303,7 @@ __global__ void __launch_bounds__(256) one_to_many_pairs_kernel(int32_t query, c
 int64_t lev_workspace(int64_t P, int32_t n) {
     auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
     return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 2 + r(8 * (P + n + 1)) +
-           r(4 * kMaxBuckets) * 5;
+           r(4 * kMaxBuckets) * 5 + r(4 * scan_tiles(n));
 }
 
 static PlanParams plan_params(const Registry &R, const Tune &T, int64_t P, int sm_count) {
@@ -300,7 +372,8 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     int32_t *boff = ar.take<int32_t>(kMaxBuckets);
     int32_t *bcounter = ar.take<int32_t>(kMaxBuckets);
     int32_t *bsum = ar.take<int32_t>(kMaxBuckets);
-    if (!bsum)
+    int32_t *tsum = ar.take<int32_t>(scan_tiles(n));
+    if (!tsum)
         return set_error(ctx, MSA_ENOMEM, "msa_lev_batch: needs %lld workspace bytes, context has %lld",
                          (long long)lev_workspace(P, n), (long long)ctx->ws_bytes);
     // the three per-query arrays are contiguous: one memset
@@ -310,10 +383,10 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
 
     const int gP = grid_for((int)std::min<int64_t>((P + 255) / 256, ctx->sm_count * 8));
     const int gN = grid_for((int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8));
-    ctx->launches += 5;
+    ctx->launches += 6;
     const PairList L{pairs, P, idx, count_dev};
     count_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qcount, ctx->dev_err);
-    scan_kernel<<<1, 1024, 0, st>>>(qcount, n, qstart);
+    exclusive_scan(qcount, n, qstart, tsum, st);
     scatter_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
     const PlanParams pp = plan_params(R, T, P, ctx->sm_count);
     task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, bsum, ctx->dev_err);
@@ -349,7 +422,9 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
             break;
         }
     // the buckets are independent: run them side by side so that small or
-    // uneven buckets do not leave the GPU idle one after another
+    // uneven buckets do not leave the GPU idle one after another (on 16 side
+    // streams for a call of its own; nested in a banded call, on the streams
+    // its band kernels leave free)
     std::vector<int> launch_list;
     for (int b = 0; b < R.count(); ++b) {
         if (b < 2 * R.nlane ? b % R.nlane > lane_last : b - 2 * R.nlane > warp_last) continue;
@@ -362,7 +437,7 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
         ai.bucket = launch_list[i];
         const int grid = grid_for(ctx->sm_count * T.occupancy[s->alphabet][ai.bucket]);
         R.at(ai.bucket).launch(ai, grid, s2);
-    }, side_base, 8);
+    }, side_base, side_base == 0 ? 16 : msa_ctx::kSide - side_base);
     ctx->launches += (int64_t)launch_list.size();
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_batch launch");
     return cuda_check(ctx, cudaGetLastError(), "msa_lev_batch launch");

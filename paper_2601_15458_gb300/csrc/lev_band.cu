@@ -229,8 +229,15 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
             }
             const bool need = !has && more;
             if (__any_sync(kFull, need)) {
-                int i = 0;
-                if (need && gl == 0) i = atomicAdd(counter, 1);
+                // one claim per warp for all its groups that need a pair, so
+                // the queue is handed out in whole warps: claimed one group
+                // at a time, a persistent grid with more groups than pairs
+                // spreads the pairs one per warp and leaves most lanes idle
+                const unsigned leaders = __ballot_sync(kFull, need && gl == 0);
+                int base = 0;
+                if (lane == 0) base = atomicAdd(counter, __popc(leaders));
+                base = __shfl_sync(kFull, base, 0);
+                int i = base + __popc(leaders & ((1u << lane) - 1u));
                 i = __shfl_sync(kFull, i, gbase);
                 if (need) {
                     if (i >= cnt) {
@@ -386,6 +393,8 @@ static const void *kBandFnProt[kBandBuckets] = BAND_FNS(5);
 constexpr int kLenClasses = 64;
 // per round: bcount, boff, bcounter [buckets]; ccount, coff, cfill [buckets x classes]
 constexpr int kBandMeta = 3 * kBandBuckets + 3 * kBandBuckets * kLenClasses;
+static_assert(kBandBuckets * kLenClasses <= 2048, "band_scan_kernel scans two counts per thread");
+static_assert(kBandBuckets <= msa_ctx::kBandSide, "one side stream per band bucket");
 __device__ __forceinline__ int band_len_class(int n) {
     if (n <= 1) return kLenClasses - 1;
     const int lg = 31 - __clz(n);
@@ -446,18 +455,41 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
     }
 }
 
-// Offsets of the buckets and of their length classes in the pair list.
-__global__ void band_scan_kernel(const int32_t *__restrict__ ccount, int32_t *__restrict__ coff,
-                                 int32_t *__restrict__ boff, int32_t nb) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int run = 0;
-    for (int b = 0; b < nb; ++b) {
-        boff[b] = run;
-        for (int c = 0; c < kLenClasses; ++c) {
-            coff[b * kLenClasses + c] = run;
-            run += ccount[b * kLenClasses + c];
-        }
+// Offsets of the buckets and of their length classes in the pair list: an
+// exclusive scan of the bucket-major counts (at most 2,048 of them) by one
+// block, two counts per thread.
+__global__ void __launch_bounds__(1024) band_scan_kernel(const int32_t *__restrict__ ccount,
+                                                         int32_t *__restrict__ coff, int32_t *__restrict__ boff,
+                                                         int32_t nb) {
+    __shared__ int32_t wpre[32];
+    const int total = nb * kLenClasses;
+    const int i0 = 2 * threadIdx.x;
+    const int x0 = i0 < total ? ccount[i0] : 0, x1 = i0 + 1 < total ? ccount[i0 + 1] : 0;
+    const int own = x0 + x1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (lane == 31) wpre[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int t = wpre[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wpre[lane] = t;
+    }
+    __syncthreads();
+    const int run = (w ? wpre[w - 1] : 0) + inc - own;
+    if (i0 < total) coff[i0] = run;
+    if (i0 + 1 < total) coff[i0 + 1] = run + x0;
+    if (i0 < total && i0 % kLenClasses == 0) boff[i0 / kLenClasses] = run;
+    if (i0 + 1 < total && (i0 + 1) % kLenClasses == 0) boff[(i0 + 1) / kLenClasses] = run + x0;
 }
 
 __global__ void band_append_kernel(const int32_t *__restrict__ cur, const int32_t *cur_count,
@@ -549,7 +581,7 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
         band_plan_kernel<0><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
                                                             k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
                                                             nb, ctx->dev_err);
-        band_scan_kernel<<<1, 32, 0, st>>>(ccount, coff, boff, nb);
+        band_scan_kernel<<<1, 1024, 0, st>>>(ccount, coff, boff, nb);
         band_plan_kernel<1><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
                                                             k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
                                                             nb, ctx->dev_err);
@@ -562,7 +594,7 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
                 BandArgs ab = a;
                 ab.bucket = b;
                 launch[b](ab, ctx->sm_count * occ[b], s2);
-            }, 0, 8, /*join=*/r != 0);
+            }, 0, msa_ctx::kBandSide, /*join=*/r != 0);
             ctx->launches += last + 1;
             if (e != cudaSuccess) return cuda_check(ctx, e, "band launch");
             if (r == 0) {
@@ -570,8 +602,9 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
                                                                        k_used_out);
                 ++ctx->launches;
                 Arena tmp = ar;
-                if ((rc = lev_run(ctx, s, pairs, P, d_out, st, full_list, counts + 2, &tmp, 8))) return rc;
-                if ((e = join_side(ctx, st, 0, std::min(last + 1, 8))) != cudaSuccess)
+                if ((rc = lev_run(ctx, s, pairs, P, d_out, st, full_list, counts + 2, &tmp, msa_ctx::kBandSide)))
+                    return rc;
+                if ((e = join_side(ctx, st, 0, std::min(last + 1, msa_ctx::kBandSide))) != cudaSuccess)
                     return cuda_check(ctx, e, "band join");
             }
         }

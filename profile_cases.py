@@ -8,7 +8,7 @@
     python profile_cases.py band_small  # the same on 20,000 pairs (for ncu captures)
     python profile_cases.py pack    # packed loader, 1.1 GB arena
     python profile_cases.py mlp     # band network forward + one training step
-    python profile_cases.py protein # 10,000 x 100 centre distances, 9,999 NW with traceback
+    python profile_cases.py protein # 10,000 x 100 centre distances; guide tree and 9,999 merges of the 10,000
     python profile_cases.py nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
     python profile_cases.py metrics # MSA quality of a 3,000-sequence MSA, 2,000-row sample
 
@@ -159,23 +159,25 @@ def case_protein(ctx):
     sq = api.upload_and_pack(ctx, allseq)
     lens = np.diff(allseq.offs).astype(np.int64)
     cen = np.array([[nm + c, x] for c in range(roots.n) for x in range(nm)], np.int32)
-    fam = members.extra["family"]
-    aln = np.array([[x, nm + int(fam[x])] for x in range(nm - 1)], np.int32)
     cen_d = torch.from_numpy(cen).cuda()
-    aln_d = torch.from_numpy(aln).cuda()
     out = torch.empty(len(cen), dtype=torch.int32, device="cuda")
     t_lev = _time(lambda: api.lev_batch(ctx, sq, cen_d, out))
-    bs = api.ByteSeqs.from_device_seqs(sq)
-    cap = torch.from_numpy(lens[aln[:, 0]] + lens[aln[:, 1]]).cuda()
-    off = torch.zeros(len(aln) + 1, dtype=torch.int64, device="cuda")
-    torch.cumsum(cap, 0, out=off[1:])
-    ops = torch.empty(int(off[-1].item()), dtype=torch.uint8, device="cuda")
-    t_nw = _time(lambda: api.nw_align_batch(ctx, bs, aln_d, ops_off=off, ops=ops))
     c_lev = int((lens[cen[:, 0]] * lens[cen[:, 1]]).sum())
-    c_nw = int((lens[aln[:, 0]] * lens[aln[:, 1]]).sum())
     print(f"centre distances: {len(cen)} pairs, {t_lev:.3f} ms, {c_lev / t_lev / 1e9:.1f} TCUPS")
-    print(f"NW with traceback: {len(aln)} pairs, {t_nw:.3f} ms, {c_nw / t_nw / 1e9:.2f} TCUPS")
-    return t_lev + t_nw
+    # Alg. 1 over the 10,000 members and the 9,999 guide-tree merges
+    msq = api.upload_and_pack(ctx, members)
+    api.clam_partition(ctx, msq)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = api.clam_partition(ctx, msq)
+    torch.cuda.synchronize()
+    t_tree = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    pos, width, score = api.merge_tree(ctx, msq, tree)
+    torch.cuda.synchronize()
+    t_merge = (time.perf_counter() - t0) * 1e3
+    print(f"guide tree: {t_tree:.1f} ms; 9,999 merges with traceback: {t_merge:.1f} ms, MSA width {int(width[0])}")
+    return t_lev + t_tree + t_merge
 
 
 CASES = dict(lev=case_lev, lev_few=case_lev_few, tree=case_tree, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
