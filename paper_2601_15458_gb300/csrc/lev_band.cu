@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "carry_chain.cuh"
 #include "lev_kernels.cuh"
@@ -50,6 +51,17 @@ __constant__ int kBandG[kBandBuckets] = BAND_G_LIST;
 __constant__ int kBandWPL[kBandBuckets] = BAND_WPL_LIST;
 static const int kBandGHost[kBandBuckets] = BAND_G_LIST;
 static const int kBandWPLHost[kBandBuckets] = BAND_WPL_LIST;
+// One-lane buckets (DNA): a pair in a single lane, its band held as a window
+// of W 32-row words in registers (band_lane_kernel), for bands up to
+// 32 W - 63 rows.  Indices kBandBuckets .. kBandAll - 1 after the group
+// buckets.
+constexpr int kLaneBuckets = 8;
+constexpr int kBandAll = kBandBuckets + kLaneBuckets;
+#define BAND_LANE_W_LIST {4, 8, 12, 16, 24, 32, 40, 48}
+__constant__ int kLaneW[kLaneBuckets] = BAND_LANE_W_LIST;
+static const int kLaneWHost[kLaneBuckets] = BAND_LANE_W_LIST;
+// band rows a W-word window covers at every column of a 32-column phase
+__host__ __device__ constexpr int lane_capacity(int W) { return 32 * W - 63; }
 // a band whose rows per column (k + H) exceed this share of the column goes
 // to the full bit-vector DP, whose kernels need no band bookkeeping
 constexpr float kBandMaxShare = 0.75f;
@@ -57,6 +69,9 @@ constexpr float kBandMaxShare = 0.75f;
 // the last one go to the full DP)
 constexpr int kBandRounds = 3;
 constexpr int kBandThreads = 128;
+// dynamic shared memory of a one-lane block: each thread's window planes, W uint2
+constexpr size_t lane_band_smem(int W) { return (size_t)W * kBandThreads * 8; }
+static_assert(lane_band_smem(48) <= 48 * 1024, "one-lane buckets fit the default shared-memory limit");
 
 struct BandArgs {
     const uint32_t *planes;
@@ -360,6 +375,199 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
     }
 }
 
+// One-lane banded kernel (DNA): each lane holds a whole pair.  The band of
+// column j spans rows [j - dhi, j - dlo]; the lane keeps a window of W
+// 32-row words (Pv and Mv in registers, the query's two bit planes of the
+// window's rows in shared memory) that moves down one word at a time, only
+// at 32-column phase boundaries, so that it covers every band row of the
+// next 32 columns (32 W >= k + 63).  The row just above the window is taken
+// to grow by +1 per column (the upper bound D[i][j] <= D[i][j-1] + 1, the
+// same boundary as row 0, whose value T is carried along), and a word
+// entering at the bottom starts at "+1 on every row" (D[i][j] <= D[i-1][j] +
+// 1); every computed value is then an upper bound of D, and exact on every
+// cell whose optimal paths stay in the window, so the certificate of the
+// group kernel applies unchanged.  All lanes of a warp start pairs only at
+// phase boundaries, so the window moves (or not) for every lane at the same
+// iteration.
+
+// One column over the window, in chunks of up to 8 words on the carry chain
+// (as in the lane kernel), the match masks formed from the two planes:
+// Eq = ~((P0 ^ m0) | (P1 ^ m1)) for the column's code bits m0, m1 (0 or ~0).
+// The row above the window adds +1 (Ph in = 1, carry in = 0).
+template <int W, int K0 = 0>
+__device__ __forceinline__ void lane_band_column(const uint2 *sP, uint32_t m0, uint32_t m1, uint32_t (&Pv)[W],
+                                                 uint32_t (&Mv)[W], uint32_t cy = 0u, uint32_t php = 1u << 31) {
+    if constexpr (K0 < W) {
+        constexpr int L = W - K0 < 8 ? W - K0 : 8;
+        uint32_t eq[L], u[L], pv[L], sm[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const uint2 pl = sP[(K0 + i) * kBandThreads];
+            eq[i] = ~((pl.x ^ m0) | (pl.y ^ m1));
+            pv[i] = Pv[K0 + i];
+            u[i] = eq[i] & pv[i];
+        }
+        cy = CarryChainIn<L>::add(sm, u, pv, cy);
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const uint32_t mhs = sm[i] ^ u[i] ^ pv[i];
+            const uint32_t ph = Mv[K0 + i] | ~(sm[i] | pv[i] | eq[i]);
+            const uint32_t phs = __funnelshift_l(php, ph, 1);
+            php = ph;
+            const uint32_t xv = eq[i] | Mv[K0 + i];
+            Pv[K0 + i] = mhs | ~(xv | phs);
+            Mv[K0 + i] = phs & xv;
+        }
+        lane_band_column<W, K0 + L>(sP, m0, m1, Pv, Mv, cy, php);
+    }
+}
+
+// the target's 2-bit codes at arena positions pos .. pos + 31, as two planes
+__device__ __forceinline__ void lane_target_bits(const uint32_t *__restrict__ planes, int64_t pos, uint32_t &t0,
+                                                 uint32_t &t1) {
+    const int64_t wi = pos >> 5;
+    const int r = (int)(pos & 31);
+    t0 = __funnelshift_r(__ldg(planes + 2 * wi), __ldg(planes + 2 * wi + 2), r);
+    t1 = __funnelshift_r(__ldg(planes + 2 * wi + 1), __ldg(planes + 2 * wi + 3), r);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
+    extern __shared__ uint2 sPlanes[];
+    uint2 *sP = sPlanes + threadIdx.x;        // word w of this lane's window at sP[w * kBandThreads]
+    const int lane = threadIdx.x & 31;
+    const int cnt = a.bcount[a.bucket];
+    const int32_t *list = a.blist + a.boff[a.bucket];
+    int32_t *counter = a.bcounter + a.bucket;
+    uint32_t Pv[W], Mv[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        Pv[w] = kFull;
+        Mv[w] = 0u;
+    }
+    int p = -1, m = 0, n = 0, k = 0, dhi = 0, j = 0, w0 = 0, T = 0;
+    int64_t qa = 0, ta = 0;
+    bool has = false, more = true, start = false;
+    uint32_t t0 = 0u, t1 = 0u, nt0 = 0u, nt1 = 0u;
+    uint2 nb = make_uint2(0u, 0u);
+    while (true) {
+        // ---- phase boundary -------------------------------------------
+        // a lane whose pair has reached column n applies the certificate;
+        // a failed band that still fits the window restarts at once
+        if (has && j == n) {
+            int d = T;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int rem = m - 32 * (w0 + w);
+                const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                d += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
+            }
+            const int k2 = min(d, 2 * k + 1);
+            if (d <= k) {
+                a.d_out[p] = d;
+                a.k_used[p] = k;
+                has = false;
+            } else if (k2 <= lane_capacity(W) && k2 < m) {
+                k = k2;
+                start = true;
+            } else {
+                a.k_cur[p] = k2;
+                a.next_list[atomicAdd(a.next_count, 1)] = p;
+                has = false;
+            }
+        }
+        // lanes without a pair take the next ones (one claim per warp)
+        const bool need = !has && more;
+        if (__any_sync(kFull, need)) {
+            const unsigned who = __ballot_sync(kFull, need);
+            int base = 0;
+            if (lane == 0) base = atomicAdd(counter, __popc(who));
+            base = __shfl_sync(kFull, base, 0);
+            if (need) {
+                const int i = base + __popc(who & ((1u << lane) - 1u));
+                if (i >= cnt) {
+                    more = false;
+                } else {
+                    p = list[i];
+                    const int q = a.pairs[2 * p], r = a.pairs[2 * p + 1];
+                    int64_t qb = a.offs[q + 1], tb = a.offs[r + 1];
+                    qa = a.offs[q];
+                    ta = a.offs[r];
+                    if (qb - qa < tb - ta) {     // longer sequence on the rows
+                        int64_t y = qa; qa = ta; ta = y;
+                        y = qb; qb = tb; tb = y;
+                    }
+                    m = (int)(qb - qa);
+                    n = (int)(tb - ta);
+                    k = min(max(a.k_cur[p], m - n), m);
+                    has = true;
+                    start = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, has)) break;
+        if (start) {
+            // (re)start the pair at column 0: window at row 1, rows +1
+            start = false;
+            dhi = (n - m + k) >> 1;
+            j = 0;
+            w0 = 0;
+            T = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                Pv[w] = kFull;
+                Mv[w] = 0u;
+                uint32_t pl[2], mask;
+                query_planes<2>(a.planes, qa, m, w, pl, mask);
+                sP[w * kBandThreads] = make_uint2(pl[0], pl[1]);
+            }
+            uint32_t pl[2], mask;
+            query_planes<2>(a.planes, qa, m, W, pl, mask);
+            nb = make_uint2(pl[0], pl[1]);
+            lane_target_bits(a.planes, ta, nt0, nt1);
+        } else if (has) {
+            // the window moves down a word when the band's top row passes it:
+            // w0 = floor((j - dhi) / 32) for the columns j + 1 .. j + 32
+            const int w0n = j - dhi < 0 ? 0 : (j - dhi) >> 5;
+            if (w0n > w0) {
+                T += __popc(Pv[0]) - __popc(Mv[0]);
+#pragma unroll
+                for (int w = 0; w + 1 < W; ++w) {
+                    Pv[w] = Pv[w + 1];
+                    Mv[w] = Mv[w + 1];
+                    sP[w * kBandThreads] = sP[(w + 1) * kBandThreads];
+                }
+                Pv[W - 1] = kFull;
+                Mv[W - 1] = 0u;
+                sP[(W - 1) * kBandThreads] = nb;
+                w0 = w0n;
+                uint32_t pl[2], mask;
+                query_planes<2>(a.planes, qa, m, w0 + W, pl, mask);
+                nb = make_uint2(pl[0], pl[1]);
+            }
+        }
+        // the target's codes for this phase, and a prefetch of the next
+        t0 = nt0;
+        t1 = nt1;
+        if (has && j + 32 < n) lane_target_bits(a.planes, ta + j + 32, nt0, nt1);
+        // ---- 32 columns ------------------------------------------------
+        const int cols = has ? min(32, n - j) : 0;
+#pragma unroll 1
+        for (int c = 0; c < 32; ++c) {
+            if (c < cols) lane_band_column<W>(sP, 0u - (t0 & 1u), 0u - (t1 & 1u), Pv, Mv);
+            t0 >>= 1;
+            t1 >>= 1;
+        }
+        j += cols;
+        T += cols;
+    }
+}
+
+template <int W>
+void launch_band_lane(const BandArgs &a, int grid, cudaStream_t st) {
+    band_lane_kernel<W><<<grid, kBandThreads, lane_band_smem(W), st>>>(a);
+}
+
 using BandLauncher = void (*)(const BandArgs &, int, cudaStream_t);
 
 template <int G, int WPL, int B>
@@ -386,15 +594,23 @@ static const BandLauncher kBandDna[kBandBuckets] = BAND_TABLE(2);
 static const BandLauncher kBandProt[kBandBuckets] = BAND_TABLE(5);
 static const void *kBandFnDna[kBandBuckets] = BAND_FNS(2);
 static const void *kBandFnProt[kBandBuckets] = BAND_FNS(5);
+static const BandLauncher kBandLane[kLaneBuckets] = {launch_band_lane<4>, launch_band_lane<8>, launch_band_lane<12>,
+                                                     launch_band_lane<16>, launch_band_lane<24>, launch_band_lane<32>,
+                                                     launch_band_lane<40>, launch_band_lane<48>};
+static const void *kBandLaneFn[kLaneBuckets] = {
+    (const void *)band_lane_kernel<4>,  (const void *)band_lane_kernel<8>,  (const void *)band_lane_kernel<12>,
+    (const void *)band_lane_kernel<16>, (const void *)band_lane_kernel<24>, (const void *)band_lane_kernel<32>,
+    (const void *)band_lane_kernel<40>, (const void *)band_lane_kernel<48>};
 
 // Pairs of a bucket are ordered longest first (by half-octave classes of
 // the column count), so that the long pairs start early and the short ones
 // fill the end of the persistent launch.
 constexpr int kLenClasses = 64;
-// per round: bcount, boff, bcounter [buckets]; ccount, coff, cfill [buckets x classes]
-constexpr int kBandMeta = 3 * kBandBuckets + 3 * kBandBuckets * kLenClasses;
-static_assert(kBandBuckets * kLenClasses <= 2048, "band_scan_kernel scans two counts per thread");
-static_assert(kBandBuckets <= msa_ctx::kBandSide, "one side stream per band bucket");
+// per round: bcount, boff, bcounter [buckets]; ccount, coff, cfill [buckets x classes], over the
+// group buckets and then the one-lane buckets
+constexpr int kBandMeta = 3 * kBandAll + 3 * kBandAll * kLenClasses;
+static_assert(kBandAll * kLenClasses <= 2048, "band_scan_kernel scans two counts per thread");
+static_assert(kBandAll <= msa_ctx::kBandSide, "one side stream per band bucket");
 __device__ __forceinline__ int band_len_class(int n) {
     if (n <= 1) return kLenClasses - 1;
     const int lg = 31 - __clz(n);
@@ -413,7 +629,7 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
                                                         int32_t *__restrict__ ccount, int32_t *__restrict__ cfill,
                                                         const int32_t *__restrict__ coff, int32_t *__restrict__ blist,
                                                         int32_t *__restrict__ full_list, int32_t *full_count, int32_t nb,
-                                                        int32_t *err) {
+                                                        bool lane_ok, int32_t *err) {
     const int64_t N = cur ? (int64_t)*cur_count : P;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int p = cur ? cur[i] : (int)i;
@@ -434,12 +650,23 @@ __global__ void __launch_bounds__(256) band_plan_kernel(const int32_t *__restric
         const int k = min(max(k_cur[p], dl), m);
         int b = -1;
         if (ly > 0 && lx > 0) {
-            for (int c = 0; c < nb; ++c)
-                if (band_capacity(kBandG[c], kBandWPL[c]) >= k) {
-                    b = c;
-                    break;
-                }
-            if (b >= 0 && (float)(k + 32 * kBandWPL[b]) > kBandMaxShare * (float)m) b = -1;
+            // DNA bands that a one-lane window holds go to the one-lane
+            // kernel, wider ones to the first group bucket that holds them
+            if (lane_ok && k <= lane_capacity(kLaneW[kLaneBuckets - 1])) {
+                for (int c = 0; c < kLaneBuckets; ++c)
+                    if (lane_capacity(kLaneW[c]) >= k) {
+                        b = kBandBuckets + c;
+                        break;
+                    }
+                if ((float)(k + 63) > kBandMaxShare * (float)m) b = -1;
+            } else {
+                for (int c = 0; c < nb; ++c)
+                    if (band_capacity(kBandG[c], kBandWPL[c]) >= k) {
+                        b = c;
+                        break;
+                    }
+                if (b >= 0 && (float)(k + 32 * kBandWPL[b]) > kBandMaxShare * (float)m) b = -1;
+            }
         }
         if (b < 0) {
             if (PASS == 0) full_list[atomicAdd(full_count, 1)] = p;
@@ -541,9 +768,9 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
     if (!full_list2 || ar.cap - ar.used < lev_workspace(P, s->n_seqs))
         return set_error(ctx, MSA_ENOMEM, "msa_lev_banded_batch: needs %lld workspace bytes, context has %lld",
                          (long long)msa_lev_banded_workspace_bytes(P, s->n_seqs), (long long)ctx->ws_bytes);
-    int32_t *bcount = meta, *boff = meta + kBandBuckets, *bcounter = meta + 2 * kBandBuckets;
-    int32_t *ccount = meta + 3 * kBandBuckets, *coff = ccount + kBandBuckets * kLenClasses,
-            *cfill = coff + kBandBuckets * kLenClasses;
+    int32_t *bcount = meta, *boff = meta + kBandAll, *bcounter = meta + 2 * kBandAll;
+    int32_t *ccount = meta + 3 * kBandAll, *coff = ccount + kBandAll * kLenClasses,
+            *cfill = coff + kBandAll * kLenClasses;
     cudaError_t e = cudaMemcpyAsync(k_cur, k0, P * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 4 * sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "msa_lev_banded_batch setup");
@@ -555,9 +782,13 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
         const int c1 = band_capacity(kBandGHost[b], kBandWPLHost[b]);
         if (c1 <= c0) return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table not increasing at %d", b);
     }
-    int occ[kBandBuckets];
-    for (int b = 0; b < nb; ++b)
-        if ((rc = occupancy(ctx, fns[b], kBandThreads, 0, &occ[b]))) return rc;
+    const bool lane_ok = s->alphabet == MSA_DNA;
+    int occ[kBandAll];
+    for (int b = 0; b < kBandAll; ++b)
+        if (b < nb || lane_ok)
+            if ((rc = occupancy(ctx, b < nb ? fns[b] : kBandLaneFn[b - nb], kBandThreads,
+                                b < nb ? 0 : lane_band_smem(kLaneWHost[b - nb]), &occ[b])))
+                return rc;
     // buckets beyond the first that holds a band as wide as the longest
     // sequence of this set are never used
     int last = nb - 1;
@@ -566,6 +797,15 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
             last = b;
             break;
         }
+    // the launches of a round: the one-lane buckets (DNA), then the group buckets
+    std::vector<int> buckets;
+    if (lane_ok)
+        for (int c = 0; c < kLaneBuckets; ++c) {
+            buckets.push_back(nb + c);
+            if (lane_capacity(kLaneWHost[c]) >= s->max_len) break;
+        }
+    for (int b = 0; b <= last; ++b) buckets.push_back(b);
+    const int nl = (int)buckets.size();
     const int g = (int)std::min<int64_t>((P + 255) / 256, ctx->sm_count * 8);
     int32_t *cur = nullptr, *cur_count = nullptr;
     for (int r = 0; r < kBandRounds; ++r) {
@@ -580,22 +820,23 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
         int32_t *fcount = counts + (r == 0 ? 2 : 3);
         band_plan_kernel<0><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
                                                             k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
-                                                            nb, ctx->dev_err);
-        band_scan_kernel<<<1, 1024, 0, st>>>(ccount, coff, boff, nb);
+                                                            nb, lane_ok, ctx->dev_err);
+        band_scan_kernel<<<1, 1024, 0, st>>>(ccount, coff, boff, kBandAll);
         band_plan_kernel<1><<<std::max(g, 1), 256, 0, st>>>(pairs, P, cur, cur_count, s->offs, s->n_seqs, s->total,
                                                             k_cur, bcount, ccount, cfill, coff, blist, flist, fcount,
-                                                            nb, ctx->dev_err);
+                                                            nb, lane_ok, ctx->dev_err);
         ctx->launches += 3;
         BandArgs a{s->planes, s->codes, s->offs, pairs, blist, boff, bcount, bcounter, k_cur, d_out, k_used_out,
                    nxt, nxt_count, 0};
         {
             ProfScope prof(ctx, st);
-            e = run_concurrent(ctx, st, last + 1, [&](int b, cudaStream_t s2) {
+            e = run_concurrent(ctx, st, nl, [&](int i, cudaStream_t s2) {
                 BandArgs ab = a;
-                ab.bucket = b;
-                launch[b](ab, ctx->sm_count * occ[b], s2);
+                ab.bucket = buckets[i];
+                const int b = buckets[i];
+                (b < nb ? launch[b] : kBandLane[b - nb])(ab, ctx->sm_count * occ[b], s2);
             }, 0, msa_ctx::kBandSide, /*join=*/r != 0);
-            ctx->launches += last + 1;
+            ctx->launches += nl;
             if (e != cudaSuccess) return cuda_check(ctx, e, "band launch");
             if (r == 0) {
                 band_full_kused_kernel<<<std::max(g, 1), 256, 0, st>>>(pairs, s->offs, full_list, counts + 2,
@@ -604,7 +845,7 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
                 Arena tmp = ar;
                 if ((rc = lev_run(ctx, s, pairs, P, d_out, st, full_list, counts + 2, &tmp, msa_ctx::kBandSide)))
                     return rc;
-                if ((e = join_side(ctx, st, 0, std::min(last + 1, msa_ctx::kBandSide))) != cudaSuccess)
+                if ((e = join_side(ctx, st, 0, std::min(nl, msa_ctx::kBandSide))) != cudaSuccess)
                     return cuda_check(ctx, e, "band join");
             }
         }

@@ -43,10 +43,10 @@ struct msa_ctx {
     double prof_ms = 0.0;
     // side streams for running independent bucket kernels concurrently
     // (fork / join through events, so stream capture still works)
-    static constexpr int kSide = 32;
+    static constexpr int kSide = 40;
     // streams [0, kBandSide) take the band buckets of a banded call (one
     // bucket each), the rest the full-DP batch running beside them
-    static constexpr int kBandSide = 24;
+    static constexpr int kBandSide = 32;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kSide] = {};

@@ -76,3 +76,40 @@ def test_band_protein(ctx):
         d, _ = api.lev_banded_batch(ctx, sq, pairs, np.full(len(pairs), k0, np.int32))
         ctx.check()
         np.testing.assert_array_equal(d.cpu().numpy(), ref)
+
+
+LANE_CAPACITIES = [32 * w - 63 for w in (4, 8, 12, 16, 24, 32, 40, 48)]
+
+
+def test_band_one_lane_windows(ctx):
+    """DNA bands up to 1,473 rows run one pair per lane with a window of
+    32-row words that moves down a word at 32-column boundaries: bands at
+    and around every window size, column counts on and off those boundaries,
+    rows far longer than columns, and bands started too narrow (retried in
+    the lane when the retry band still fits the window, else in a later
+    round) are all exact."""
+    rng = np.random.default_rng(21)
+    rows = []
+    for L, div in ((32, 0.2), (64, 0.1), (95, 0.3), (640, 0.05), (1000, 0.3), (1024, 0.15), (1500, 0.25),
+                   (2500, 0.12), (3000, 0.3), (4000, 0.08)):
+        a = rng.choice(list(b"ACGT"), size=L).astype(np.uint8)
+        b = a.copy()
+        nsub = int(div * L)
+        b[rng.integers(0, L, nsub)] = rng.choice(list(b"ACGT"), size=nsub).astype(np.uint8)
+        cut = rng.integers(0, max(1, L // 3))
+        b = np.concatenate([b[:L // 2], b[L // 2 + cut:]])      # rows longer than columns
+        rows += [a.tobytes(), b.tobytes()]
+    ds = synth.SeqSet.from_list(rows)
+    pairs = np.array([[2 * i, 2 * i + 1] for i in range(len(rows) // 2)], np.int32)
+    ref = oracle.lev_pairs(ds.arena, ds.offs, pairs)
+    sq = api.upload_and_pack(ctx, ds)
+    lens = np.diff(ds.offs)
+    dl = np.abs(lens[pairs[:, 0]] - lens[pairs[:, 1]])
+    starts = [np.full(len(pairs), c + e, np.int32) for c in LANE_CAPACITIES for e in (-1, 0, 1)]
+    starts += [np.maximum(ref // 2, 0).astype(np.int32), np.maximum(ref - 3, 0).astype(np.int32),
+               (ref + dl).astype(np.int32)]
+    for k0 in starts:
+        d, k_used = api.lev_banded_batch(ctx, sq, pairs, k0)
+        ctx.check()
+        np.testing.assert_array_equal(d.cpu().numpy(), ref)
+        assert np.all(k_used.cpu().numpy() >= ref)
