@@ -69,9 +69,9 @@ constexpr float kBandMaxShare = 0.75f;
 // the last one go to the full DP)
 constexpr int kBandRounds = 3;
 constexpr int kBandThreads = 128;
-// dynamic shared memory of a one-lane block: each thread's window planes, W uint2
-constexpr size_t lane_band_smem(int W) { return (size_t)W * kBandThreads * 8; }
-static_assert(lane_band_smem(48) <= 48 * 1024, "one-lane buckets fit the default shared-memory limit");
+// dynamic shared memory of a one-lane block: each thread's match masks of
+// its window rows, 4 symbols x W words
+constexpr size_t lane_band_smem(int W) { return (size_t)W * 4 * kBandThreads * 4; }
 
 struct BandArgs {
     const uint32_t *planes;
@@ -117,6 +117,16 @@ constexpr uint32_t kBandTopBits = 0x55555555u & ((1u << (2 * kBandCps)) - 1u);
 // block b must have finished it before block b + G needs it
 __host__ __device__ constexpr int band_capacity(int G, int WPL) { return (G - 1) * 32 * WPL - 2 * kBandCps; }
 
+// The 4 code bytes at p .. p + 3, from the two aligned words that hold them
+// (bytes past a sequence's end come from the next sequence or the arena's
+// padding of at least 32 bytes; they only feed columns past n, never read).
+__device__ __forceinline__ uint32_t load_codes4(const uint8_t *p) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~uintptr_t(3));
+    return __funnelshift_r(__ldg(w), __ldg(w + 1), (int)(a & 3) * 8);
+}
+static_assert(kBandCps == 4, "a chunk's codes are one packed word");
+
 // Takes block bk of the current pair: its live chunks [qs, qe] (columns
 // widened to whole chunks), the last live column of the block above (0 for
 // the top block) and its chunk, fresh +1 vertical deltas, the query's match
@@ -125,7 +135,7 @@ template <int WPL, int B>
 __device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m, int n, const uint32_t *planes,
                                                  int64_t qa, const uint8_t *tc, int &qs, int &qe, int &jep, int &qep,
                                                  uint32_t (&Pv)[WPL], uint32_t (&Mv)[WPL], BandEq<WPL, B> &E,
-                                                 uint32_t *sPeq, int (&c_next)[kBandCps]) {
+                                                 uint32_t *sPeq, uint32_t &cw_next) {
     constexpr int H = 32 * WPL;
     const int js = max(1, bk * H + 1 + dlo);
     const int je = min(n, bk * H + H + dhi);
@@ -153,9 +163,7 @@ __device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m
             for (int q = 0; q < B; ++q) E.pl[w][q] = pl[q];
         }
     }
-    const int j0 = (qs - 1) * kBandCps;
-#pragma unroll
-    for (int c = 0; c < kBandCps; ++c) c_next[c] = j0 + c < n ? __ldg(tc + j0 + c) : 0;
+    cw_next = load_codes4(tc + (qs - 1) * kBandCps);
 }
 
 template <int G, int WPL, int B>
@@ -195,9 +203,7 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
     // the block above and its chunk, T, the lane's share of D[m][n] and the
     // word sent down
     int bk = 0, qs = 1, qe = 0, jep = 0, qep = 0, Tb = 0, acc = 0;
-    int c_next[CPS];
-#pragma unroll
-    for (int c = 0; c < CPS; ++c) c_next[c] = 0;
+    uint32_t cw_next = 0u;   // the codes of the block's next chunk, one byte per column
     uint32_t out = 0u;
     bool fin = false;
     while (true) {
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                         bk = gl;
                         if (bk <= bm)
                             band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv, Mv,
-                                                     E, sPeq, c_next);
+                                                     E, sPeq, cw_next);
                     } else {
                         if (gl == 0) {
                             a.k_cur[p] = k2;
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                             bk = gl;
                             if (bk <= bm)
                                 band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv,
-                                                         Mv, E, sPeq, c_next);
+                                                         Mv, E, sPeq, cw_next);
                             has = true;
                         }
                     }
@@ -304,14 +310,9 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
             if (bk <= bm) {
                 if (q == qep) Tb = (int)(in >> (2 * CPS));    // the block above leaves after this chunk
                 if (q >= qs && q <= qe) {
-                    int cc[CPS];
-#pragma unroll
-                    for (int c = 0; c < CPS; ++c) cc[c] = c_next[c];
+                    const uint32_t cw = cw_next;
                     const int j0 = (q - 1) * CPS;              // columns j0 + 1 .. j0 + CPS
-                    if (q < qe) {
-#pragma unroll
-                        for (int c = 0; c < CPS; ++c) c_next[c] = j0 + CPS + c < n ? __ldg(tc + j0 + CPS + c) : 0;
-                    }
+                    if (q < qe) cw_next = load_codes4(tc + j0 + CPS);
                     // the block above leaves at a chunk end, so a chunk is
                     // either all below it or all on top (row above: +1 per
                     // column, Ph = 1, carry 0 for every column)
@@ -322,17 +323,18 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                     uint32_t o = 0u;
 #pragma unroll
                     for (int c = 0; c < CPS; ++c) {
-                        // columns past n (in the last chunk) run on symbol 0
-                        // and are never read
+                        // columns past n (in the last chunk) run on whatever
+                        // bytes follow and are never read
+                        const uint32_t cc = (cw >> (8 * c)) & 0xffu;
                         uint32_t eq[WPL];
                         if constexpr (kShared) {
-                            const uint32_t *row = sPeq + (cc[c] & 3) * WPL * kBandThreads;
+                            const uint32_t *row = sPeq + (cc & 3) * WPL * kBandThreads;
 #pragma unroll
                             for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
                         } else {
                             uint32_t x[B];
 #pragma unroll
-                            for (int b = 0; b < B; ++b) x[b] = ((cc[c] >> b) & 1) ? 0u : kFull;
+                            for (int b = 0; b < B; ++b) x[b] = ((cc >> b) & 1) ? 0u : kFull;
 #pragma unroll
                             for (int w = 0; w < WPL; ++w) {
                                 uint32_t e = E.pl[w][0] ^ x[0];
@@ -341,9 +343,12 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                                 eq[w] = e;
                             }
                         }
-                        uint32_t ph_out, mh_out;
-                        bv_column<WPL>(eq, Pv, Mv, (inb >> (2 * c)) & 1u, (inb >> (2 * c + 1)) & 1u, ph_out, mh_out);
-                        o |= (ph_out | (mh_out << 1)) << (2 * c);
+                        // the Ph bit of the row above goes in as bit 31 of php,
+                        // its carry as any nonzero value; the block's bottom
+                        // bits are packed into o on the multiply-add pipe
+                        uint32_t php_out, mh_out;
+                        bv_column_raw<WPL>(eq, Pv, Mv, inb << (31 - 2 * c), inb & (2u << (2 * c)), php_out, mh_out);
+                        o = mad_u32(mh_out, 2u << (2 * c), mad_u32(php_out >> 31, 1u << (2 * c), o));
                         if (last && j0 + 1 + c == n) {
                             // this block's share of D[m][n]: its rows <= m (and T if on top)
                             int part = top ? Tb : 0;
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                         bk += G;
                         if (bk <= bm)
                             band_block_setup<WPL, B>(bk, dlo, dhi, m, n, a.planes, qa, tc, qs, qe, jep, qep, Pv, Mv,
-                                                     E, sPeq, c_next);
+                                                     E, sPeq, cw_next);
                     }
                 }
             }
@@ -391,19 +396,18 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
 // iteration.
 
 // One column over the window, in chunks of up to 8 words on the carry chain
-// (as in the lane kernel), the match masks formed from the two planes:
-// Eq = ~((P0 ^ m0) | (P1 ^ m1)) for the column's code bits m0, m1 (0 or ~0).
-// The row above the window adds +1 (Ph in = 1, carry in = 0).
+// (as in the lane kernel), the match masks of the column's symbol read from
+// shared memory (sEq: word w of the window at sEq[4 w kBandThreads]).  The
+// row above the window adds +1 (Ph in = 1, carry in = 0).
 template <int W, int K0 = 0>
-__device__ __forceinline__ void lane_band_column(const uint2 *sP, uint32_t m0, uint32_t m1, uint32_t (&Pv)[W],
-                                                 uint32_t (&Mv)[W], uint32_t cy = 0u, uint32_t php = 1u << 31) {
+__device__ __forceinline__ void lane_band_column(const uint32_t *sEq, uint32_t (&Pv)[W], uint32_t (&Mv)[W],
+                                                 uint32_t cy = 0u, uint32_t php = 1u << 31) {
     if constexpr (K0 < W) {
         constexpr int L = W - K0 < 8 ? W - K0 : 8;
         uint32_t eq[L], u[L], pv[L], sm[L];
 #pragma unroll
         for (int i = 0; i < L; ++i) {
-            const uint2 pl = sP[(K0 + i) * kBandThreads];
-            eq[i] = ~((pl.x ^ m0) | (pl.y ^ m1));
+            eq[i] = sEq[(K0 + i) * 4 * kBandThreads];
             pv[i] = Pv[K0 + i];
             u[i] = eq[i] & pv[i];
         }
@@ -418,7 +422,7 @@ __device__ __forceinline__ void lane_band_column(const uint2 *sP, uint32_t m0, u
             Pv[K0 + i] = mhs | ~(xv | phs);
             Mv[K0 + i] = phs & xv;
         }
-        lane_band_column<W, K0 + L>(sP, m0, m1, Pv, Mv, cy, php);
+        lane_band_column<W, K0 + L>(sEq, Pv, Mv, cy, php);
     }
 }
 
@@ -433,8 +437,11 @@ __device__ __forceinline__ void lane_target_bits(const uint32_t *__restrict__ pl
 
 template <int W>
 __global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
-    extern __shared__ uint2 sPlanes[];
-    uint2 *sP = sPlanes + threadIdx.x;        // word w of this lane's window at sP[w * kBandThreads]
+    extern __shared__ uint32_t sMasks[];
+    // the match mask of symbol c for word w of this lane's window at
+    // sM[(4 w + c) kBandThreads] (thread-minor: conflict-free for any mix of
+    // symbols across the warp)
+    uint32_t *sM = sMasks + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int cnt = a.bcount[a.bucket];
     const int32_t *list = a.blist + a.boff[a.bucket];
@@ -449,7 +456,8 @@ __global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
     int64_t qa = 0, ta = 0;
     bool has = false, more = true, start = false;
     uint32_t t0 = 0u, t1 = 0u, nt0 = 0u, nt1 = 0u;
-    uint2 nb = make_uint2(0u, 0u);
+    uint2 nb = make_uint2(0u, 0u);     // planes and row mask of the word that enters at the next move
+    uint32_t nbm = 0u;
     while (true) {
         // ---- phase boundary -------------------------------------------
         // a lane whose pair has reached column n applies the certificate;
@@ -519,11 +527,13 @@ __global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
                 Mv[w] = 0u;
                 uint32_t pl[2], mask;
                 query_planes<2>(a.planes, qa, m, w, pl, mask);
-                sP[w * kBandThreads] = make_uint2(pl[0], pl[1]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sM[(4 * w + c) * kBandThreads] = match_mask<2, 4>(pl, mask, c);
             }
             uint32_t pl[2], mask;
             query_planes<2>(a.planes, qa, m, W, pl, mask);
             nb = make_uint2(pl[0], pl[1]);
+            nbm = mask;
             lane_target_bits(a.planes, ta, nt0, nt1);
         } else if (has) {
             // the window moves down a word when the band's top row passes it:
@@ -535,15 +545,21 @@ __global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
                 for (int w = 0; w + 1 < W; ++w) {
                     Pv[w] = Pv[w + 1];
                     Mv[w] = Mv[w + 1];
-                    sP[w * kBandThreads] = sP[(w + 1) * kBandThreads];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sM[(4 * w + c) * kBandThreads] = sM[(4 * w + 4 + c) * kBandThreads];
                 }
                 Pv[W - 1] = kFull;
                 Mv[W - 1] = 0u;
-                sP[(W - 1) * kBandThreads] = nb;
+                {
+                    const uint32_t pl[2] = {nb.x, nb.y};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sM[(4 * (W - 1) + c) * kBandThreads] = match_mask<2, 4>(pl, nbm, c);
+                }
                 w0 = w0n;
                 uint32_t pl[2], mask;
                 query_planes<2>(a.planes, qa, m, w0 + W, pl, mask);
                 nb = make_uint2(pl[0], pl[1]);
+                nbm = mask;
             }
         }
         // the target's codes for this phase, and a prefetch of the next
@@ -554,7 +570,7 @@ __global__ void __launch_bounds__(kBandThreads) band_lane_kernel(BandArgs a) {
         const int cols = has ? min(32, n - j) : 0;
 #pragma unroll 1
         for (int c = 0; c < 32; ++c) {
-            if (c < cols) lane_band_column<W>(sP, 0u - (t0 & 1u), 0u - (t1 & 1u), Pv, Mv);
+            if (c < cols) lane_band_column<W>(sM + (int)((t0 & 1u) | ((t1 & 1u) << 1)) * kBandThreads, Pv, Mv);
             t0 >>= 1;
             t1 >>= 1;
         }
@@ -783,6 +799,14 @@ msa_status lev_banded_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pair
         if (c1 <= c0) return set_error(ctx, MSA_EUNSUPPORTED, "band bucket table not increasing at %d", b);
     }
     const bool lane_ok = s->alphabet == MSA_DNA;
+    if (lane_ok && !ctx->band_lane_smem_set) {
+        for (int c = 0; c < kLaneBuckets; ++c)
+            if (lane_band_smem(kLaneWHost[c]) > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(kBandLaneFn[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)lane_band_smem(kLaneWHost[c]))) != cudaSuccess)
+                return cuda_check(ctx, e, "band lane shared memory");
+        ctx->band_lane_smem_set = true;
+    }
     int occ[kBandAll];
     for (int b = 0; b < kBandAll; ++b)
         if (b < nb || lane_ok)

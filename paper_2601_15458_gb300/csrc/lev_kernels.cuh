@@ -207,6 +207,42 @@ __device__ __forceinline__ void bv_column(const uint32_t (&eq)[N], uint32_t (&Pv
     ph_out = php >> 31;
 }
 
+// bv_column with the boundary bits in place: the Ph bit of the row above is
+// bit 31 of php_in, the carry into the first row is 1 iff cin != 0; on return
+// bit 31 of php_out is the last row's Ph bit and cout its carry (Mh bit).
+template <int N>
+__device__ __forceinline__ void bv_column_raw(const uint32_t (&eq)[N], uint32_t (&Pv)[N], uint32_t (&Mv)[N],
+                                              uint32_t php_in, uint32_t cin, uint32_t &php_out, uint32_t &cout) {
+    uint32_t u[N], sum[N], pv[N];
+#pragma unroll
+    for (int w = 0; w < N; ++w) {
+        pv[w] = Pv[w];
+        u[w] = eq[w] & pv[w];
+    }
+    cout = chain_add_all<N>(sum, u, pv, cin);
+    uint32_t php = php_in;
+#pragma unroll
+    for (int w = 0; w < N; ++w) {
+        const uint32_t mhs = sum[w] ^ u[w] ^ pv[w];
+        const uint32_t ph = Mv[w] | ~(sum[w] | pv[w] | eq[w]);
+        const uint32_t phs = __funnelshift_l(php, ph, 1);
+        php = ph;
+        const uint32_t xv = eq[w] | Mv[w];
+        Pv[w] = mhs | ~(xv | phs);
+        Mv[w] = phs & xv;
+    }
+    php_out = php;
+}
+
+// d = a * b + c on the integer multiply-add pipe (used for bit packing that
+// would otherwise take shifts and ORs on the logic pipe; b a power of two and
+// a * b disjoint from c)
+__device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);

@@ -55,6 +55,7 @@ struct msa_ctx {
     // a time uses a context, so no lock is needed)
     std::map<const void *, int> occ;
     bool mlp_smem_set = false;
+    bool band_lane_smem_set = false;
 };
 
 namespace msa {
