@@ -166,6 +166,40 @@ __device__ __forceinline__ void band_block_setup(int bk, int dlo, int dhi, int m
     cw_next = load_codes4(tc + (qs - 1) * kBandCps);
 }
 
+// Column c of a block's chunk: the match masks of the column's code (from
+// shared memory for DNA, from the bit planes in registers otherwise), the
+// column step with the row-above bits of inb, and the block's bottom bits
+// packed into o.
+template <int WPL, int B>
+__device__ __forceinline__ void band_chunk_column(int c, uint32_t cw, uint32_t inb, const uint32_t *sPeq,
+                                                  const BandEq<WPL, B> &E, uint32_t (&Pv)[WPL], uint32_t (&Mv)[WPL],
+                                                  uint32_t &o) {
+    const uint32_t cc = (cw >> (8 * c)) & 0xffu;
+    uint32_t eq[WPL];
+    if constexpr (BandEq<WPL, B>::kShared) {
+        const uint32_t *row = sPeq + (cc & 3) * WPL * kBandThreads;
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
+    } else {
+        uint32_t x[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) x[b] = ((cc >> b) & 1) ? 0u : kFull;
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) {
+            uint32_t e = E.pl[w][0] ^ x[0];
+#pragma unroll
+            for (int b = 1; b < B; ++b) e &= E.pl[w][b] ^ x[b];
+            eq[w] = e;
+        }
+    }
+    // the Ph bit of the row above goes in as bit 31 of php, its carry as any
+    // nonzero value; the block's bottom bits are packed into o on the
+    // multiply-add pipe
+    uint32_t php_out, mh_out;
+    bv_column_raw<WPL>(eq, Pv, Mv, inb << (31 - 2 * c), inb & (2u << (2 * c)), php_out, mh_out);
+    o = mad_u32(mh_out, 2u << (2 * c), mad_u32(php_out >> 31, 1u << (2 * c), o));
+}
+
 template <int G, int WPL, int B>
 __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "group size");
@@ -321,44 +355,26 @@ __global__ void __launch_bounds__(kBandThreads) band_pipe_kernel(BandArgs a) {
                     if (top) Tb += min(CPS, n - j0);
                     const bool last = j0 + CPS >= n;          // the chunk holds column n
                     uint32_t o = 0u;
+                    if (!last) {
 #pragma unroll
-                    for (int c = 0; c < CPS; ++c) {
-                        // columns past n (in the last chunk) run on whatever
-                        // bytes follow and are never read
-                        const uint32_t cc = (cw >> (8 * c)) & 0xffu;
-                        uint32_t eq[WPL];
-                        if constexpr (kShared) {
-                            const uint32_t *row = sPeq + (cc & 3) * WPL * kBandThreads;
+                        for (int c = 0; c < CPS; ++c) band_chunk_column<WPL, B>(c, cw, inb, sPeq, E, Pv, Mv, o);
+                    } else {
+                        // the chunk holding column n: columns past n run on
+                        // whatever bytes follow and are never read
 #pragma unroll
-                            for (int w = 0; w < WPL; ++w) eq[w] = row[w * kBandThreads];
-                        } else {
-                            uint32_t x[B];
+                        for (int c = 0; c < CPS; ++c) {
+                            band_chunk_column<WPL, B>(c, cw, inb, sPeq, E, Pv, Mv, o);
+                            if (j0 + 1 + c == n) {
+                                // this block's share of D[m][n]: its rows <= m (and T if on top)
+                                int part = top ? Tb : 0;
 #pragma unroll
-                            for (int b = 0; b < B; ++b) x[b] = ((cc >> b) & 1) ? 0u : kFull;
-#pragma unroll
-                            for (int w = 0; w < WPL; ++w) {
-                                uint32_t e = E.pl[w][0] ^ x[0];
-#pragma unroll
-                                for (int b = 1; b < B; ++b) e &= E.pl[w][b] ^ x[b];
-                                eq[w] = e;
+                                for (int w = 0; w < WPL; ++w) {
+                                    const int rem = m - 32 * (bk * WPL + w);
+                                    const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+                                    part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
+                                }
+                                acc += part;
                             }
-                        }
-                        // the Ph bit of the row above goes in as bit 31 of php,
-                        // its carry as any nonzero value; the block's bottom
-                        // bits are packed into o on the multiply-add pipe
-                        uint32_t php_out, mh_out;
-                        bv_column_raw<WPL>(eq, Pv, Mv, inb << (31 - 2 * c), inb & (2u << (2 * c)), php_out, mh_out);
-                        o = mad_u32(mh_out, 2u << (2 * c), mad_u32(php_out >> 31, 1u << (2 * c), o));
-                        if (last && j0 + 1 + c == n) {
-                            // this block's share of D[m][n]: its rows <= m (and T if on top)
-                            int part = top ? Tb : 0;
-#pragma unroll
-                            for (int w = 0; w < WPL; ++w) {
-                                const int rem = m - 32 * (bk * WPL + w);
-                                const uint32_t mk = rem >= 32 ? kFull : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-                                part += __popc(Pv[w] & mk) - __popc(Mv[w] & mk);
-                            }
-                            acc += part;
                         }
                     }
                     out = o;
