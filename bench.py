@@ -212,7 +212,7 @@ def peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, sm_max_mhz=2070.0), "fallback"
 
 
-HELD_OUT_PAIRS = 20000   # per held-out set (calibration; margin timing)
+HELD_OUT_PAIRS = 20000   # held-out pairs that fit the calibration
 
 
 def band_bench(ctx, args, stream):
@@ -226,13 +226,14 @@ def band_bench(ctx, args, stream):
     del X, y
     # calibration and band margin come from held-out pairs of two other
     # seeds, never from the evaluation pairs
-    def held_out(seed):
-        val = synth.divergent_pairs(seed=seed, n_pairs=HELD_OUT_PAIRS)
+    def held_out(seed, n_pairs):
+        val = synth.divergent_pairs(seed=seed, n_pairs=n_pairs)
         vs = api.upload_and_pack(ctx, val)
         vp = torch.from_numpy(np.stack([np.arange(0, val.n, 2), np.arange(1, val.n, 2)], 1).astype(np.int32))
         return vs, api.kmer_profile(ctx, vs), vp.cuda()
 
-    cal_set, gam_set = held_out(41), held_out(42)
+    # the margin is timed on a held-out batch of the evaluation batch's size
+    cal_set, gam_set = held_out(41, HELD_OUT_PAIRS), held_out(42, args.band_pairs)
     gamma_raw, _ = learned_band.pick_gamma(ctx, model, *gam_set)
     cal_tau, gamma, _ = learned_band.pick_band(ctx, model, cal_set, gam_set)
     setup_s = time.perf_counter() - t0
@@ -300,7 +301,8 @@ def band_bench(ctx, args, stream):
                 pairs_per_s_l1_bound=P / (t_l1 / 1e3), speedup_learned_vs_full=t_full / t_band,
                 speedup_learned_vs_l1_bound=t_l1 / t_band,
                 speedup_uncalibrated_vs_full=t_full / t_raw,
-                calibration=dict(tau=cal_tau, pairs=HELD_OUT_PAIRS, gamma_uncalibrated=gamma_raw,
+                calibration=dict(tau=cal_tau, pairs=HELD_OUT_PAIRS, margin_timing_pairs=args.band_pairs,
+                                 gamma_uncalibrated=gamma_raw,
                                  k_mean_over_f=float((k.double() / d_full.double().clamp(min=1)).mean().item()),
                                  k_mean_over_f_uncalibrated=float(
                                      (k_raw.double() / d_full.double().clamp(min=1)).mean().item())),

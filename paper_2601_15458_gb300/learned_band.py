@@ -113,9 +113,10 @@ def calibrate(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof
 
 
 def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, prof: torch.Tensor,
-               pairs: torch.Tensor, candidates=(-0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 2):
+               pairs: torch.Tensor, candidates=(-0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.2, 0.35), margin: int = 8, reps: int = 3):
     """The band margin gamma with the fastest certified banded run on a
-    validation batch (timed with CUDA events; all candidates are exact)."""
+    validation batch (median of ``reps`` runs timed with CUDA events; all
+    candidates are exact)."""
     best, best_t = candidates[0], float("inf")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for g in candidates:
@@ -128,20 +129,23 @@ def pick_gamma(ctx: api.Context, model: api.BandModel, seqs: api.DeviceSeqs, pro
             ev1.record()
             ev1.synchronize()
             ts.append(ev0.elapsed_time(ev1))
-        t = min(ts)
+        t = float(np.median(ts))
         if t < best_t:
             best, best_t = g, t
     return best, best_t
 
 
 def pick_band(ctx: api.Context, model: api.BandModel, cal_set, gamma_set, taus=(0.95, 0.99, 1.0),
-              candidates=(-0.1, -0.05, 0.0, 0.05, 0.1, 0.15, 0.2, 0.35), margin: int = 8):
+              candidates=(-0.05, -0.025, 0.0, 0.025, 0.05, 0.1, 0.15, 0.25), margin: int = 8):
     """Calibration quantile tau and margin gamma together: for each tau the
     calibration is fitted on ``cal_set`` and gamma picked by timing on
-    ``gamma_set`` (each a ``(seqs, prof, pairs)`` of held-out pairs, large
-    enough to fill the GPU, or the timing favours wide bands); the model is
-    left calibrated with the best tau.  Returns ``(tau, gamma, ms)``; tau
-    None is the network without calibration, when that is fastest."""
+    ``gamma_set`` (each a ``(seqs, prof, pairs)`` of held-out pairs; the
+    timing set should be as large as the batches the band is for: a failed
+    band's retry runs after the first pass, and a long pair's retry is a
+    fixed latency that weighs more, and favours wider bands, in a smaller
+    batch); the model is left calibrated with the best tau.  Returns
+    ``(tau, gamma, ms)``; tau None is the network without calibration, when
+    that is fastest."""
     best = (None, *pick_gamma(ctx, model, *gamma_set, candidates=candidates, margin=margin))
     for tau in taus:
         calibrate(ctx, model, *cal_set, tau=tau)
