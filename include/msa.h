@@ -344,6 +344,21 @@ msa_status msa_nw_align_batch_affine(msa_ctx *ctx, const uint8_t *codes, const i
                                      int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off,
                                      int32_t *ops_len_out, void *stream);
 
+/*
+ * The affine alignment with a substitution table: a diagonal move costs
+ * sub[nsym * a_i + b_j] (device int32 [nsym][nsym], row-major by code,
+ * nsym <= 32, entries may be negative) instead of match / mismatch; the
+ * paper's protein merges use BLOSUM62 (section "Implementation"), as costs
+ * -score.  'M' / 'X' still mark identical / different codes.  A pair with a
+ * code >= nsym is reported as MSA_EDATA by msa_ctx_check and left unwritten.
+ * Gaps, traceback, arguments and outputs as in msa_nw_align_batch_affine.
+ */
+msa_status msa_nw_align_batch_affine_sub(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                         int64_t total, int32_t max_len, const int32_t *pairs, int64_t P,
+                                         const int32_t *sub, int32_t nsym, int32_t gap_open, int32_t gap_ext,
+                                         int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off,
+                                         int32_t *ops_len_out, void *stream);
+
 /* ---- A11: guide tree by Alg. 1 (Partition) ------------------------------ */
 /*
  * Builds the binary cluster tree of Alg. 1 (section "Clustering") over the
@@ -406,6 +421,14 @@ msa_status msa_merge_tree_affine(msa_ctx *ctx, const msa_seqset *s, const int32_
                                  const int32_t *right, int32_t n_nodes, int32_t match, int32_t mismatch,
                                  int32_t gap_open, int32_t gap_ext, int32_t *pos, int32_t *width, int32_t *score,
                                  void *stream);
+/* The same merge with a substitution table for the centre alignments
+ * (msa_nw_align_batch_affine_sub's model); the table must cover the gap code
+ * of the centre rows (nsym >= 5 for DNA, 21 for protein). */
+msa_status msa_merge_tree_affine_sub(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                                     const int32_t *hi, const int32_t *center, const int32_t *left,
+                                     const int32_t *right, int32_t n_nodes, const int32_t *sub, int32_t nsym,
+                                     int32_t gap_open, int32_t gap_ext, int32_t *pos, int32_t *width, int32_t *score,
+                                     void *stream);
 /* Writes the MSA rows (ASCII, '-' for gaps) in `order`: row r (W bytes at
  * rows + r*W, device) is sequence order[r]; W = width of the root. */
 msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,

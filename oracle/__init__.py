@@ -12,7 +12,8 @@ computes the plain definition of what the GPU path computes:
   step 2) as a minimum-cost DP with a flat cost model and the traceback
   preference diagonal > up > left (``oracle.c``).
 * :func:`nw_affine` -- the same with affine gap costs (Gotoh), the cost model
-  of the paper's experiments (flat substitution costs here).
+  of the paper's experiments, with flat substitution costs or a table
+  (:func:`blosum62_costs`: BLOSUM62, which the paper names for proteins).
 * :func:`brute_alignments` -- every alignment of two short strings, used to
   pin the functions above.
 * :func:`kmer_counts`, :func:`pair_feature` -- 4-mer count profiles and the
@@ -79,6 +80,9 @@ def _load():
             L.oracle_nw_affine.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            i32p, u8p, i64p]
+            L.oracle_nw_affine_sub.restype = ctypes.c_int32
+            L.oracle_nw_affine_sub.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, i32p,
+                                               ctypes.c_int32, ctypes.c_int32, i32p, u8p, i64p]
             L.oracle_lev_pairs.restype = ctypes.c_int32
             L.oracle_lev_pairs.argtypes = [u8p, i64p, i32p, ctypes.c_int64, i32p, ctypes.c_int32]
             L.oracle_nw_pairs.restype = ctypes.c_int32
@@ -135,18 +139,30 @@ def nw(a, b, match: int = 0, mismatch: int = 1, gap: int = 1):
     return int(score.value), bytes(ops[: L.value])
 
 
-def nw_affine(a, b, match: int = 0, mismatch: int = 1, gap_open: int = 10, gap_ext: int = 1):
+def nw_affine(a, b, match: int = 0, mismatch: int = 1, gap_open: int = 10, gap_ext: int = 1, sub=None):
     """Needleman-Wunsch with affine gap costs (the paper's merges use affine
     gaps, open = 10 x extend; section "Implementation"): a run of L gap
     positions costs ``gap_open + L * gap_ext``.  Gotoh's three matrices and
     the traceback of ``oracle.c`` (diagonal, then up, then left; a gap run
     closes where opening it attains, else it extends), which with
-    ``gap_open = 0`` is :func:`nw`'s traceback.  Returns ``(score, ops)``.
+    ``gap_open = 0`` is :func:`nw`'s traceback.  With ``sub`` (a 256 x 256
+    integer array over byte values) a substitution costs ``sub[a_i, b_j]``
+    instead of match / mismatch (``M`` / ``X`` still label identity).
+    Returns ``(score, ops)``.
     """
     A, B = _as_u8(a), _as_u8(b)
     ops = np.zeros(len(A) + len(B) + 1, dtype=np.uint8)
     score = ctypes.c_int32(0)
     L = ctypes.c_int64(0)
+    if sub is not None:
+        T = np.ascontiguousarray(sub, dtype=np.int32)
+        assert T.shape == (256, 256)
+        rc = _load().oracle_nw_affine_sub(_ptr(A, ctypes.c_uint8), len(A), _ptr(B, ctypes.c_uint8), len(B),
+                                          _ptr(T, ctypes.c_int32), gap_open, gap_ext, ctypes.byref(score),
+                                          _ptr(ops, ctypes.c_uint8), ctypes.byref(L))
+        if rc != 0:
+            raise MemoryError("oracle_nw_affine_sub: allocation failed")
+        return int(score.value), ops[:L.value].tobytes()
     rc = _load().oracle_nw_affine(_ptr(A, ctypes.c_uint8), len(A), _ptr(B, ctypes.c_uint8), len(B),
                                   match, mismatch, gap_open, gap_ext, ctypes.byref(score),
                                   _ptr(ops, ctypes.c_uint8), ctypes.byref(L))
@@ -155,16 +171,17 @@ def nw_affine(a, b, match: int = 0, mismatch: int = 1, gap_open: int = 10, gap_e
     return int(score.value), ops[:L.value].tobytes()
 
 
-def rescore_affine(a, b, ops, match=0, mismatch=1, gap_open=10, gap_ext=1):
-    """Cost of an alignment under affine gaps: substitutions plus, for every
-    maximal run of D (or of I) of length L, gap_open + L * gap_ext."""
+def rescore_affine(a, b, ops, match=0, mismatch=1, gap_open=10, gap_ext=1, sub=None):
+    """Cost of an alignment under affine gaps: substitutions (match /
+    mismatch, or ``sub[a_i, b_j]``) plus, for every maximal run of D (or of
+    I) of length L, gap_open + L * gap_ext."""
     a, b = bytes(a), bytes(b)
     i = j = 0
     cost = 0
     prev = None
     for op in bytes(ops):
         if op in (ord("M"), ord("X")):
-            cost += match if a[i] == b[j] else mismatch
+            cost += int(sub[a[i], b[j]]) if sub is not None else (match if a[i] == b[j] else mismatch)
             i += 1
             j += 1
         elif op == ord("D"):
@@ -481,6 +498,32 @@ def band_policy(yhat, la, lb, gamma: float, margin: int, knots=None) -> np.ndarr
 
 
 # ---------------------------------------------------------------------------
+# BLOSUM62 costs for protein merges
+# ---------------------------------------------------------------------------
+
+def blosum62_scores() -> dict:
+    """BLOSUM62 (Henikoff & Henikoff 1992) as {(x, y): score} over the 20
+    residue letters, read from ``blosum62.txt``."""
+    rows = [ln.split() for ln in open(os.path.join(_HERE, "blosum62.txt")) if ln.strip() and not ln.startswith("#")]
+    cols = rows[0]
+    return {(r[0], c): int(v) for r in rows[1:] for c, v in zip(cols, r[1:])}
+
+
+def blosum62_costs(gap: int = ord("-")) -> np.ndarray:
+    """256 x 256 cost table over byte values for minimising NW: cost = -score
+    for two residues; the gap symbol of a gapped centre row is read as
+    BLOSUM62's stop row '*' (score -4 against any residue, 1 against itself,
+    so cost 4 and -1); other bytes cost 0 (never used)."""
+    T = np.zeros((256, 256), np.int32)
+    for (x, y), v in blosum62_scores().items():
+        T[ord(x), ord(y)] = -v
+    for x in "ARNDCQEGHILKMFPSTWYV":
+        T[ord(x), gap] = T[gap, ord(x)] = 4
+    T[gap, gap] = -1
+    return T
+
+
+# ---------------------------------------------------------------------------
 # Alg. 1 Partition and the post-order merge
 # ---------------------------------------------------------------------------
 
@@ -559,11 +602,12 @@ def partition(seqs, dist=None):
     return nodes
 
 
-def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1, gap_open=None):
+def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1, gap_open=None, sub=None):
     """Post-order merge of section "Merging" over the tree from :func:`partition`.
 
     With ``gap_open`` the centers are aligned by :func:`nw_affine` (a run of L
-    gaps costs ``gap_open + L * gap``) instead of :func:`nw`.
+    gaps costs ``gap_open + L * gap``) instead of :func:`nw`, and with ``sub``
+    too, substitutions cost ``sub[x, y]`` (e.g. :func:`blosum62_costs`).
 
     A leaf is the one-row MSA of its sequence.  At an internal node the two
     children's centers, as gapped rows of the children's MSAs, are aligned by
@@ -591,7 +635,7 @@ def merge_tree(seqs, nodes, match=0, mismatch=1, gap=1, gap_open=None):
         if gap_open is None:
             score, ops = nw(center_row(L), center_row(R), match, mismatch, gap)
         else:
-            score, ops = nw_affine(center_row(L), center_row(R), match, mismatch, gap_open, gap)
+            score, ops = nw_affine(center_row(L), center_row(R), match, mismatch, gap_open, gap, sub=sub)
         merges[k] = (score, ops)
         rowsL, ordL = msa.pop(L)
         rowsR, ordR = msa.pop(R)

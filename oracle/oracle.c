@@ -44,6 +44,10 @@
  *                 open = 0 this is the linear traceback exactly.  Row 0 forces
  *                 'I', column 0 forces 'D'.
  *
+ *  oracle_nw_affine_sub -- oracle_nw_affine with c(a_i, b_j) read from a
+ *                 substitution table over byte values (BLOSUM62 costs for
+ *                 the paper's protein merges, section "Implementation").
+ *
  *  oracle_lev_pairs / oracle_nw_pairs -- the same functions mapped over a
  *                 list of pairs, threads split the pair list only; each
  *                 pair's DP is the plain single-threaded one above.
@@ -75,10 +79,36 @@ int32_t oracle_lev(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n)
     return d;
 }
 
+/* The substitution cost c(x, y): sub[256 x + y] when a table is given,
+ * else match / mismatch by byte equality. */
+static inline int32_t subst_cost(const int32_t *sub, int32_t match, int32_t mismatch, uint8_t x, uint8_t y)
+{
+    return sub ? sub[256 * (int)x + (int)y] : (x == y ? match : mismatch);
+}
+
+static int32_t nw_affine_core(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, const int32_t *sub,
+                              int32_t match, int32_t mismatch, int32_t open, int32_t ext,
+                              int32_t *score, uint8_t *ops, int64_t *ops_len);
+
 /* Returns 0 on success, -1 on allocation failure.  ops must hold m + n bytes. */
 int32_t oracle_nw_affine(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                          int32_t match, int32_t mismatch, int32_t open, int32_t ext,
                          int32_t *score, uint8_t *ops, int64_t *ops_len)
+{
+    return nw_affine_core(a, m, b, n, NULL, match, mismatch, open, ext, score, ops, ops_len);
+}
+
+/* The same with a substitution table: c(a_i, b_j) = sub[256 a_i + b_j]
+ * (a 256 x 256 table over byte values); 'M' / 'X' still label identity. */
+int32_t oracle_nw_affine_sub(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, const int32_t *sub,
+                             int32_t open, int32_t ext, int32_t *score, uint8_t *ops, int64_t *ops_len)
+{
+    return nw_affine_core(a, m, b, n, sub, 0, 0, open, ext, score, ops, ops_len);
+}
+
+static int32_t nw_affine_core(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, const int32_t *sub,
+                              int32_t match, int32_t mismatch, int32_t open, int32_t ext,
+                              int32_t *score, uint8_t *ops, int64_t *ops_len)
 {
     const int32_t INF = 1 << 29;
     const int64_t cols = n + 1;
@@ -103,7 +133,7 @@ int32_t oracle_nw_affine(const uint8_t *a, int64_t m, const uint8_t *b, int64_t 
             const int64_t x = i * cols + j, up = (i - 1) * cols + j, lf = i * cols + j - 1;
             F[x] = min2(F[up] + ext, H[up] + open + ext);
             E[x] = min2(E[lf] + ext, H[lf] + open + ext);
-            const int32_t c = (a[i - 1] == b[j - 1]) ? match : mismatch;
+            const int32_t c = subst_cost(sub, match, mismatch, a[i - 1], b[j - 1]);
             H[x] = min2(H[(i - 1) * cols + j - 1] + c, min2(F[x], E[x]));
         }
     }
@@ -116,7 +146,7 @@ int32_t oracle_nw_affine(const uint8_t *a, int64_t m, const uint8_t *b, int64_t 
         if (j == 0) { ops[k++] = 'D'; --i; continue; }
         const int64_t x = i * cols + j;
         if (state == 0) {
-            const int32_t c = (a[i - 1] == b[j - 1]) ? match : mismatch;
+            const int32_t c = subst_cost(sub, match, mismatch, a[i - 1], b[j - 1]);
             if (H[x] == H[(i - 1) * cols + j - 1] + c) {
                 ops[k++] = (a[i - 1] == b[j - 1]) ? 'M' : 'X';
                 --i; --j;

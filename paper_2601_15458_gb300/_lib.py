@@ -87,6 +87,12 @@ SIGNATURES = {
     "msa_msa_rows": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_int32, c_void_p,
                                c_void_p]),
     "msa_probe_int_pipe": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_int64), c_void_p]),
+    "msa_nw_align_batch_affine_sub": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p,
+                                                c_int64, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                                c_void_p, c_void_p, c_void_p]),
+    "msa_merge_tree_affine_sub": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_int32,
+                                            c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 

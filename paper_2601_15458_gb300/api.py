@@ -212,15 +212,18 @@ class ByteSeqs:
 
 
 def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_off: torch.Tensor | None = None,
-                   stream=None, gap_open: int | None = None, ops: torch.Tensor | None = None):
+                   stream=None, gap_open: int | None = None, ops: torch.Tensor | None = None,
+                   sub: torch.Tensor | None = None):
     """A5/A6: NW score, edit script (forward order, bytes M/X/D/I) per pair.
 
     Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64, ops_len[P] int32)``.
     ``seqs`` is a :class:`ByteSeqs` or a packed :class:`DeviceSeqs` (its byte codes).
     With ``gap_open`` the gap costs are affine: a run of L gaps costs
-    ``gap_open + L * gap`` (msa_nw_align_batch_affine).  A caller that passes
-    both ``ops_off`` and an ``ops`` buffer of ``ops_off[-1]`` bytes makes the
-    call without a host synchronisation.
+    ``gap_open + L * gap`` (msa_nw_align_batch_affine); with ``sub`` as well
+    (device int32 [nsym, nsym] costs by code, e.g. :func:`blosum62_table`) a
+    substitution costs ``sub[a, b]`` (msa_nw_align_batch_affine_sub).  A
+    caller that passes both ``ops_off`` and an ``ops`` buffer of
+    ``ops_off[-1]`` bytes makes the call without a host synchronisation.
     """
     if isinstance(seqs, DeviceSeqs):
         seqs = ByteSeqs.from_device_seqs(seqs)
@@ -241,11 +244,24 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
         ctx.raise_if(_lib.lib().msa_nw_align_batch(ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total,
                                                    seqs.max_len, _ptr(pairs), P, match, mismatch, gap, _ptr(score),
                                                    _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
-    else:
+    elif sub is None:
         ctx.raise_if(_lib.lib().msa_nw_align_batch_affine(
             ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, match,
             mismatch, gap_open, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    else:
+        sub = sub.to(device=dev, dtype=torch.int32).contiguous()
+        ctx.raise_if(_lib.lib().msa_nw_align_batch_affine_sub(
+            ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P,
+            _ptr(sub), int(sub.shape[0]), gap_open, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len),
+            _stream(stream)))
     return score, ops, ops_off, ops_len
+
+
+def blosum62_table(device="cuda") -> torch.Tensor:
+    """BLOSUM62 as costs (-score) over the protein codes 0..19 and the gap
+    code 20 of gapped centre rows: int32 [21, 21] (see ``substitution``)."""
+    from . import substitution
+    return torch.tensor(substitution.blosum62_costs_by_code(), dtype=torch.int32, device=device)
 
 
 def lev_schedule(ctx: Context, lane_min_targets: int = -1, slot_min_targets: int = -1, lane_per_task: int = -1,
@@ -433,11 +449,13 @@ def clam_partition(ctx: Context, seqs: DeviceSeqs, band: "BandModel | None" = No
 
 
 def merge_tree(ctx: Context, seqs: DeviceSeqs, tree: Tree, match=0, mismatch=1, gap=1, stream=None,
-               gap_open: int | None = None):
+               gap_open: int | None = None, sub: torch.Tensor | None = None):
     """A12: bottom-up merge; returns ``(pos tensor, width[n_nodes], score[n_nodes])``.
 
     With ``gap_open`` the center alignments use affine gaps (a run of L gaps
-    costs ``gap_open + L * gap``; msa_merge_tree_affine)."""
+    costs ``gap_open + L * gap``; msa_merge_tree_affine), and with ``sub``
+    (device int32 [nsym, nsym] covering the gap code) substitutions cost
+    ``sub[a, b]`` (msa_merge_tree_affine_sub)."""
     pos = torch.empty(max(seqs.total, 1), dtype=torch.int32, device="cuda")
     width = np.zeros(max(tree.n_nodes, 1), np.int32)
     score = np.zeros(max(tree.n_nodes, 1), np.int32)
@@ -446,8 +464,12 @@ def merge_tree(ctx: Context, seqs: DeviceSeqs, tree: Tree, match=0, mismatch=1, 
     outs = (_ptr(pos), _np_ptr(width), _np_ptr(score), _stream(stream))
     if gap_open is None:
         ctx.raise_if(_lib.lib().msa_merge_tree(ctx.handle, *tr, gap, *outs))
-    else:
+    elif sub is None:
         ctx.raise_if(_lib.lib().msa_merge_tree_affine(ctx.handle, *tr, gap_open, gap, *outs))
+    else:
+        sub = sub.to(device="cuda", dtype=torch.int32).contiguous()
+        ctx.raise_if(_lib.lib().msa_merge_tree_affine_sub(ctx.handle, *tr[:-2], _ptr(sub), int(sub.shape[0]),
+                                                           gap_open, gap, *outs))
     return pos, width[: tree.n_nodes], score[: tree.n_nodes]
 
 

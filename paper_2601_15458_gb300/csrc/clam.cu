@@ -501,7 +501,8 @@ msa_status msa_clam_partition_banded(msa_ctx *ctx, const msa_seqset *s, const vo
 static msa_status merge_tree_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
                                  const int32_t *hi, const int32_t *center, const int32_t *left, const int32_t *right,
                                  int32_t n_nodes, int32_t match, int32_t mismatch, int32_t gap, int32_t gap_open,
-                                 int32_t *pos, int32_t *width, int32_t *score, void *stream) {
+                                 int32_t *pos, int32_t *width, int32_t *score, void *stream,
+                                 const int32_t *sub = nullptr, int32_t nsym = 0) {
     if (!ctx || !s) return MSA_EINVAL;
     if (!order || !lo || !hi || !center || !left || !right || !pos || !width || !score)
         return set_error(ctx, MSA_EINVAL, "msa_merge_tree: null pointer");
@@ -603,7 +604,7 @@ static msa_status merge_tree_run(msa_ctx *ctx, const msa_seqset *s, const int32_
         rc = gap_open < 0 ? nw_run(ctx, ar, rows, d_roff, 2 * M, roff[2 * M], maxw, d_pairs, M, match, mismatch, gap,
                                    d_score, ops, d_ooff, d_len, st)
                           : nw_affine_run(ctx, ar, rows, d_roff, 2 * M, roff[2 * M], maxw, d_pairs, M, match,
-                                          mismatch, gap_open, gap, d_score, ops, d_ooff, d_len, st);
+                                          mismatch, gap_open, gap, d_score, ops, d_ooff, d_len, st, sub, nsym);
         if (rc) return rc;
         column_maps_kernel<<<(M + 127) / 128, 128, 0, st>>>(ops, d_ooff, d_len, d_roff, M, maps);
         const int64_t members = seg_start[2 * M];
@@ -642,6 +643,19 @@ msa_status msa_merge_tree_affine(msa_ctx *ctx, const msa_seqset *s, const int32_
     if (ctx && gap_open < 0) return set_error(ctx, MSA_EINVAL, "msa_merge_tree_affine: gap_open < 0");
     return merge_tree_run(ctx, s, order, lo, hi, center, left, right, n_nodes, match, mismatch, gap_ext, gap_open,
                           pos, width, score, stream);
+}
+
+msa_status msa_merge_tree_affine_sub(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *lo,
+                                     const int32_t *hi, const int32_t *center, const int32_t *left,
+                                     const int32_t *right, int32_t n_nodes, const int32_t *sub, int32_t nsym,
+                                     int32_t gap_open, int32_t gap_ext, int32_t *pos, int32_t *width, int32_t *score,
+                                     void *stream) {
+    if (ctx && gap_open < 0) return set_error(ctx, MSA_EINVAL, "msa_merge_tree_affine_sub: gap_open < 0");
+    if (ctx && !sub) return set_error(ctx, MSA_EINVAL, "msa_merge_tree_affine_sub: null table");
+    if (ctx && s && nsym < (s->alphabet == MSA_DNA ? 5 : 21))
+        return set_error(ctx, MSA_EINVAL, "msa_merge_tree_affine_sub: the table must cover the gap code");
+    return merge_tree_run(ctx, s, order, lo, hi, center, left, right, n_nodes, 0, 0, gap_ext, gap_open, pos, width,
+                          score, stream, sub, nsym);
 }
 
 msa_status msa_msa_rows(msa_ctx *ctx, const msa_seqset *s, const int32_t *order, const int32_t *pos, int32_t W,

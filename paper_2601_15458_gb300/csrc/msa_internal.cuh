@@ -140,10 +140,13 @@ cudaError_t nw_bv_launch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs
                          int32_t max_len, const int32_t *pairs, int64_t P, int32_t gap, int32_t *score,
                          uint8_t *ops, const int64_t *ops_off, int32_t *ops_len, char *slabs, int64_t slab_bytes,
                          int64_t warps, int32_t *counter, int32_t *fb_list, int32_t *fb_count, cudaStream_t st);
+// With sub (device int32 [nsym][nsym], nsym <= 32) a substitution costs
+// sub[a][b] by code instead of match / mismatch.
 msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
                          int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t match,
                          int32_t mismatch, int32_t open, int32_t ext, int32_t *score_out, uint8_t *ops_out,
-                         const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st);
+                         const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st, const int32_t *sub = nullptr,
+                         int32_t nsym = 0);
 msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
                   int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
                   int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,

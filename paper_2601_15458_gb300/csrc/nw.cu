@@ -48,7 +48,14 @@ struct NwArgs {
     const int32_t *plist;   // optional pair ids (count at *pcount); all pairs when null
     const int32_t *pcount;
     int32_t *err;
+    const int32_t *sub;     // optional substitution costs [nsym][nsym] by code (affine kernel)
+    int32_t nsym;
 };
+
+// substitution table in shared memory: stride kSubStride > kSubMax so that the
+// rows a warp reads fall on different banks
+constexpr int kSubMax = 32;
+constexpr int kSubStride = 33;
 
 __device__ __forceinline__ int64_t nw_tb_words(int max_len) {
     return (int64_t)((max_len + kNwTile - 1) / kNwTile) * 32 * max_len;
@@ -229,9 +236,16 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_kernel(NwArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int32_t kNwInf = 1 << 29;
 
+template <bool kSub>
 __global__ void __launch_bounds__(kNwWarps * 32) nw_affine_kernel(NwArgs a, int32_t open, int32_t ext) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    __shared__ int32_t sSub[kSub ? kSubMax * kSubStride : 1];
+    if constexpr (kSub) {
+        for (int i = threadIdx.x; i < a.nsym * a.nsym; i += blockDim.x)
+            sSub[(i / a.nsym) * kSubStride + i % a.nsym] = a.sub[i];
+        __syncthreads();
+    }
     const int gw = blockIdx.x * kNwWarps + (threadIdx.x >> 5);
     char *slab = a.slabs + (int64_t)gw * a.slab_bytes;
     int32_t *bH = reinterpret_cast<int32_t *>(slab);
@@ -269,6 +283,16 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_affine_kernel(NwArgs a, int3
             continue;
         }
         uint8_t *ops = a.ops + o0;
+        if constexpr (kSub) {
+            // every code must index the table
+            bool bad = false;
+            for (int k = lane; k < m; k += 32) bad |= A[k] >= a.nsym;
+            for (int k = lane; k < n; k += 32) bad |= Bq[k] >= a.nsym;
+            if (__any_sync(FULL, bad)) {
+                if (lane == 0) record_error(a.err, kErrSymbol, p, a.nsym);
+                continue;
+            }
+        }
         if (m == 0 || n == 0) {
             for (int k = lane; k < m + n; k += 32) ops[k] = m == 0 ? 'I' : 'D';
             if (lane == 0) {
@@ -316,7 +340,9 @@ __global__ void __launch_bounds__(kNwWarps * 32) nw_affine_kernel(NwArgs a, int3
                         const int Fn = min(fx, fo);
                         const int ex = E[r] + ext, eo = H[r] + oe;
                         const int En = min(ex, eo);
-                        const int dg = diag + (ac[r] == bj ? match : mismatch);
+                        // rows past m (ac = -1) read any entry: never used
+                        const int dg = diag + (kSub ? sSub[(ac[r] & (kSubMax - 1)) * kSubStride + bj]
+                                                    : (ac[r] == bj ? match : mismatch));
                         const int Hn = min(dg, min(Fn, En));
                         const uint32_t hs = dg == Hn ? 0u : (Fn == Hn ? 1u : 2u);
                         const uint32_t code = hs | ((uint32_t)(fo <= fx) << 2) | ((uint32_t)(eo <= ex) << 3);
@@ -417,7 +443,10 @@ int64_t nw_affine_slab_bytes(int max_len) {
 msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
                          int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t match,
                          int32_t mismatch, int32_t open, int32_t ext, int32_t *score_out, uint8_t *ops_out,
-                         const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st) {
+                         const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st, const int32_t *sub,
+                         int32_t nsym) {
+    if (sub && (nsym < 1 || nsym > kSubMax))
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine_sub: table size %d outside 1..%d", nsym, kSubMax);
     if (P < 0 || P >= (int64_t(1) << 31) || n_seqs < 0 || max_len < 0 || total < 0)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: negative or oversized count");
     if (open < 0 || ext < 1)
@@ -425,8 +454,9 @@ msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const in
     if (P == 0) return MSA_OK;
     if (!codes || !offs || !pairs || !score_out || !ops_out || !ops_off || !ops_len_out)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine: null pointer");
+    const void *fn = sub ? (const void *)nw_affine_kernel<true> : (const void *)nw_affine_kernel<false>;
     int occ = 1;
-    if (msa_status rc = occupancy(ctx, (const void *)nw_affine_kernel, kNwWarps * 32, 0, &occ)) return rc;
+    if (msa_status rc = occupancy(ctx, fn, kNwWarps * 32, 0, &occ)) return rc;
     int32_t *counter = ar.take<int32_t>(64);
     const int64_t slab = nw_affine_slab_bytes(max_len);
     const int64_t avail = counter ? ar.cap - ar.used : 0;
@@ -441,9 +471,12 @@ msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const in
     cudaError_t e = cudaMemsetAsync(counter, 0, 4, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "nw memset");
     NwArgs a{codes, offs, n_seqs, total, pairs, P, match, mismatch, 0, score_out, ops_out, ops_off,
-             ops_len_out, slabs, slab, max_len, counter, nullptr, nullptr, ctx->dev_err};
+             ops_len_out, slabs, slab, max_len, counter, nullptr, nullptr, ctx->dev_err, sub, nsym};
     ProfScope prof(ctx, st);
-    nw_affine_kernel<<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a, open, ext);
+    if (sub)
+        nw_affine_kernel<true><<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a, open, ext);
+    else
+        nw_affine_kernel<false><<<(int)(warps / kNwWarps), kNwWarps * 32, 0, st>>>(a, open, ext);
     ++ctx->launches;
     return cuda_check(ctx, cudaGetLastError(), "nw affine launch");
 }
@@ -523,6 +556,18 @@ msa_status msa_nw_align_batch_affine(msa_ctx *ctx, const uint8_t *codes, const i
     Arena ar{ctx->ws, ctx->ws_bytes};
     return nw_affine_run(ctx, ar, codes, offs, n_seqs, total, max_len, pairs, P, match, mismatch, gap_open, gap_ext,
                          score_out, ops_out, ops_off, ops_len_out, (cudaStream_t)stream);
+}
+
+msa_status msa_nw_align_batch_affine_sub(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                         int64_t total, int32_t max_len, const int32_t *pairs, int64_t P,
+                                         const int32_t *sub, int32_t nsym, int32_t gap_open, int32_t gap_ext,
+                                         int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off,
+                                         int32_t *ops_len_out, void *stream) {
+    if (!ctx) return MSA_EINVAL;
+    if (!sub) return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_affine_sub: null table");
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    return nw_affine_run(ctx, ar, codes, offs, n_seqs, total, max_len, pairs, P, 0, 0, gap_open, gap_ext, score_out,
+                         ops_out, ops_off, ops_len_out, (cudaStream_t)stream, sub, nsym);
 }
 
 msa_status msa_nw_align_batch(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,

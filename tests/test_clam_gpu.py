@@ -204,3 +204,23 @@ def test_affine_merge_matches_oracle(ctx, maker):
     assert [r.tobytes() for r in rows] == ref_rows
     for k, (sc, _) in merges.items():
         assert score[k] == sc
+
+
+def test_blosum62_merge_matches_oracle(ctx):
+    """The paper's protein setting (section "Implementation"): merges with
+    BLOSUM62 substitution costs and affine gaps (open 10, extend 1), the gap
+    of a centre row read as BLOSUM62's '*'; identical MSA rows and per-merge
+    costs to the oracle's post-order merge."""
+    ds = synth.protein_families(seed=3, n_fam=3, per_fam=30)[0]
+    seqs = ds.seqs()
+    sq = api.upload_and_pack(ctx, ds)
+    tree = api.clam_partition(ctx, sq)
+    pos, width, score = api.merge_tree(ctx, sq, tree, gap=1, gap_open=10, sub=api.blosum62_table())
+    rows = api.msa_rows(ctx, sq, tree, pos, int(width[0])).cpu().numpy()
+    ctx.check()
+    ref_nodes = oracle.partition(seqs)
+    ref_rows, ref_order, merges = oracle.merge_tree(seqs, ref_nodes, gap=1, gap_open=10, sub=oracle.blosum62_costs())
+    assert list(tree.order.cpu().numpy()) == ref_order
+    assert [r.tobytes() for r in rows] == ref_rows
+    for k, (sc, _) in merges.items():
+        assert score[k] == sc

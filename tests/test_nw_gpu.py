@@ -177,3 +177,68 @@ def test_affine_protein_and_linear_reduction(ctx):
     np.testing.assert_array_equal(s0.cpu().numpy(), s1.cpu().numpy())
     np.testing.assert_array_equal(l0.cpu().numpy(), l1.cpu().numpy())
     np.testing.assert_array_equal(o0.cpu().numpy(), o1.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# substitution tables (BLOSUM62 for proteins, section "Implementation")
+# ---------------------------------------------------------------------------
+
+def _ascii_table(T_code, letters, gap=ord("-")):
+    """The same costs as a 256 x 256 table over the oracle's ASCII bytes."""
+    T = np.zeros((256, 256), np.int32)
+    syms = list(letters) + [chr(gap)]
+    for i, x in enumerate(syms):
+        for j, y in enumerate(syms):
+            T[ord(x), ord(y)] = T_code[i][j]
+    return T
+
+
+def test_affine_blosum62_protein_pairs(ctx):
+    """BLOSUM62 costs with affine gaps (open 10, extend 1) on protein pairs:
+    scores and scripts identical to the oracle's."""
+    from paper_2601_15458_gb300 import substitution
+    members, roots = synth.protein_families(seed=3, n_fam=4, per_fam=15)
+    rows = members.seqs() + roots.seqs()
+    ds = synth.SeqSet.from_list(rows, "protein")
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = np.array([[members.n + f, f * 15 + k] for f in range(4) for k in range(15)] + [[0, 1], [5, 5], [7, 40]],
+                     np.int32)
+    score, ops, off, ln = api.nw_align_batch(ctx, sq, pairs, gap=1, gap_open=10, sub=api.blosum62_table())
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    assert oracle.blosum62_costs()[ord("W"), ord("W")] == -11
+    T = _ascii_table(substitution.blosum62_costs_by_code(), substitution.PROTEIN_ORDER)
+    np.testing.assert_array_equal(T, oracle.blosum62_costs())
+    for p, (a, b) in enumerate(pairs):
+        rs, rops = oracle.nw_affine(rows[a], rows[b], 0, 0, 10, 1, sub=T)
+        assert score[p] == rs
+        assert ops[off[p]:off[p] + ln[p]].tobytes() == rops
+
+
+def test_affine_random_table_dna_with_gaps(ctx):
+    """A random table over DNA codes and the gap code (some costs negative),
+    on gapped rows: identical to the oracle."""
+    rng = np.random.default_rng(31)
+    T5 = rng.integers(-3, 6, (5, 5)).astype(np.int32)
+    rows = [rng.choice(list(b"ACGT-"), size=int(rng.integers(0, 300))).astype(np.uint8).tobytes() for _ in range(40)]
+    codes = [bytes(b"ACGT-".index(c) for c in r) for r in rows]
+    bs = api.ByteSeqs.from_list(codes)
+    pairs = np.array([[i, (i * 7 + 3) % 40] for i in range(40)], np.int32)
+    score, ops, off, ln = api.nw_align_batch(ctx, bs, pairs, gap=2, gap_open=3,
+                                             sub=torch.from_numpy(T5).cuda())
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    T = _ascii_table(T5.tolist(), "ACGT")
+    for p, (a, b) in enumerate(pairs):
+        rs, rops = oracle.nw_affine(rows[a], rows[b], 0, 0, 3, 2, sub=T)
+        assert score[p] == rs
+        assert ops[off[p]:off[p] + ln[p]].tobytes() == rops
+
+
+def test_affine_table_rejects_codes_outside(ctx):
+    bs = api.ByteSeqs.from_list([bytes([0, 1, 2]), bytes([0, 7, 1])])
+    api.nw_align_batch(ctx, bs, np.array([[0, 1]], np.int32), gap=1, gap_open=2,
+                       sub=torch.zeros((5, 5), dtype=torch.int32, device="cuda"))
+    with pytest.raises(api.MsaError) as e:
+        ctx.check()
+    assert e.value.code == 6

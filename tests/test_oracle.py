@@ -506,6 +506,61 @@ def test_nw_affine_closed_forms():
     assert oracle.nw_affine(b"", b"ACG", 0, 1, 10, 1) == (13, b"III")
 
 
+def test_nw_affine_substitution_table_bruteforce():
+    """With a substitution table the DP score is the minimum over every
+    alignment rescored with that table, and its own script rescores to it
+    (random integer tables, some entries negative like BLOSUM62 costs)."""
+    rng = np.random.default_rng(52)
+    for trial in range(12):
+        T = np.zeros((256, 256), np.int32)
+        letters = list(b"ACG-")
+        for x in letters:
+            for y in letters:
+                T[x, y] = int(rng.integers(-4, 6))
+        go, ge = int(rng.integers(0, 6)), int(rng.integers(1, 4))
+        for _ in range(20):
+            a = rng.choice(letters, size=int(rng.integers(0, 6))).astype(np.uint8).tobytes()
+            b = rng.choice(letters, size=int(rng.integers(0, 6))).astype(np.uint8).tobytes()
+            best = min(oracle.rescore_affine(a, b, ops, 0, 0, go, ge, sub=T) for ops in oracle.brute_alignments(a, b))
+            score, ops = oracle.nw_affine(a, b, 0, 0, go, ge, sub=T)
+            assert score == best
+            assert oracle.rescore_affine(a, b, ops, 0, 0, go, ge, sub=T) == score
+
+
+def test_nw_affine_flat_table_is_the_flat_model():
+    rng = np.random.default_rng(53)
+    T = np.full((256, 256), 3, np.int32)
+    np.fill_diagonal(T, -1)
+    for _ in range(30):
+        a, b = _rand_dna(rng, int(rng.integers(0, 30))), _rand_dna(rng, int(rng.integers(0, 30)))
+        assert oracle.nw_affine(a, b, -1, 3, 4, 1, sub=T) == oracle.nw_affine(a, b, -1, 3, 4, 1)
+
+
+def test_blosum62_table():
+    """Properties of the BLOSUM62 transcription: symmetric, the published
+    diagonal, off-diagonal scores in [-4, 3] and below both residues' own
+    scores; and the library's copy (its own transcription, in its code
+    order) holds the same scores."""
+    S = oracle.blosum62_scores()
+    aa = "ARNDCQEGHILKMFPSTWYV"
+    diag = dict(A=4, R=5, N=6, D=6, C=9, Q=5, E=5, G=6, H=8, I=4, L=4, K=5, M=5, F=6, P=7, S=4, T=5, W=11, Y=7, V=4)
+    assert {x: S[(x, x)] for x in aa} == diag
+    for x in aa:
+        for y in aa:
+            assert S[(x, y)] == S[(y, x)]
+            if x != y:
+                assert -4 <= S[(x, y)] <= 3 and S[(x, y)] < min(S[(x, x)], S[(y, y)])
+    from paper_2601_15458_gb300 import substitution
+    lib = substitution.blosum62_costs_by_code()
+    order = substitution.PROTEIN_ORDER
+    for i, x in enumerate(order):
+        for j, y in enumerate(order):
+            assert lib[i][j] == -S[(x, y)]
+    T = oracle.blosum62_costs()
+    g = len(order)
+    assert lib[g][g] == T[ord("-"), ord("-")] and all(lib[g][i] == T[ord("-"), ord(x)] for i, x in enumerate(order))
+
+
 # ---------------------------------------------------------------------------
 # band policy and calibration
 # ---------------------------------------------------------------------------
