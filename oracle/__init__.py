@@ -16,6 +16,8 @@ computes the plain definition of what the GPU path computes:
   (:func:`blosum62_costs`: BLOSUM62, which the paper names for proteins).
 * :func:`brute_alignments` -- every alignment of two short strings, used to
   pin the functions above.
+* :func:`nw_anchored` -- NW split at unique k-mer anchors (the paper's
+  future work for long pairs; this project's definition).
 * :func:`kmer_counts`, :func:`pair_feature` -- 4-mer count profiles and the
   pair feature of the learned band proposer (no counterpart in the paper; the
   definition is this project's).
@@ -495,6 +497,97 @@ def band_policy(yhat, la, lb, gamma: float, margin: int, knots=None) -> np.ndarr
     mx = np.maximum(la, lb).astype(np.float32)
     kf = np.ceil(((np.float32(1) + np.float32(gamma)) * c).astype(np.float32) * mx).astype(np.int64)
     return np.maximum(np.abs(np.asarray(la, np.int64) - lb), kf + margin)
+
+
+# ---------------------------------------------------------------------------
+# k-mer anchored splitting of long alignments (the paper's future work for
+# length scaling, section "Conclusion"; the definition below is this
+# project's, the paper gives none)
+# ---------------------------------------------------------------------------
+
+def kmer_anchors(a, b, k):
+    """Anchors of a pair: every (i, j) where the k-mer a[i:i+k] occurs
+    exactly once in a, exactly once in b, and b[j:j+k] is that k-mer; sorted
+    by i."""
+    a, b = bytes(a), bytes(b)
+    ca, cb, pa, pb = {}, {}, {}, {}
+    for i in range(len(a) - k + 1):
+        w = a[i:i + k]
+        ca[w] = ca.get(w, 0) + 1
+        pa[w] = i
+    for j in range(len(b) - k + 1):
+        w = b[j:j + k]
+        cb[w] = cb.get(w, 0) + 1
+        pb[w] = j
+    return sorted((pa[w], pb[w]) for w in ca if ca[w] == 1 and cb.get(w, 0) == 1)
+
+
+def anchor_chain(anchors):
+    """The longest chain of anchors increasing in both i and j, by patience
+    sorting over the anchors in i order: each anchor replaces the first
+    chain tail whose j is >= its own (binary search) and links to the tail
+    before it; the chain is read back from the last tail."""
+    tails, tail_idx, prev = [], [], [-1] * len(anchors)
+    for t, (_, j) in enumerate(anchors):
+        lo, hi = 0, len(tails)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if tails[mid] < j:
+                lo = mid + 1
+            else:
+                hi = mid
+        if lo == len(tails):
+            tails.append(j)
+            tail_idx.append(t)
+        else:
+            tails[lo] = j
+            tail_idx[lo] = t
+        prev[t] = tail_idx[lo - 1] if lo > 0 else -1
+    chain = []
+    t = tail_idx[-1] if tail_idx else -1
+    while t >= 0:
+        chain.append(anchors[t])
+        t = prev[t]
+    return chain[::-1]
+
+
+def anchor_blocks(chain, k):
+    """Matched blocks from a chain, left to right: an anchor on the current
+    block's diagonal that starts inside or right after it extends the block
+    to its own end; an anchor that starts at or after the block's end in both
+    sequences starts a new block; any other anchor is dropped.  Returns
+    (start_a, start_b, length) per block."""
+    blocks = []
+    for i, j in chain:
+        if blocks:
+            sa, sb, ln = blocks[-1]
+            if j - i == sb - sa and i <= sa + ln:
+                blocks[-1] = (sa, sb, max(ln, i + k - sa))
+                continue
+            if i < sa + ln or j < sb + ln:
+                continue
+        blocks.append((i, j, k))
+    return blocks
+
+
+def nw_anchored(a, b, k=12, match=0, mismatch=1, gap=1):
+    """Needleman-Wunsch split at k-mer anchors: the blocks of
+    :func:`anchor_blocks` (over :func:`anchor_chain` of
+    :func:`kmer_anchors`) are aligned as runs of matches, the segments
+    between them (and before the first, after the last) by :func:`nw`.
+    Returns ``(score, ops)``; the score is an upper bound of the optimal NW
+    cost, equal to it whenever an optimal alignment passes through every
+    block.  Without anchors this is :func:`nw`."""
+    a, b = bytes(a), bytes(b)
+    blocks = anchor_blocks(anchor_chain(kmer_anchors(a, b, k)), k)
+    score, ops = 0, bytearray()
+    ia = ib = 0
+    for sa, sb, ln in blocks + [(len(a), len(b), 0)]:
+        sc, op = nw(a[ia:sa], b[ib:sb], match, mismatch, gap)
+        score += sc + ln * match
+        ops += op + b"M" * ln
+        ia, ib = sa + ln, sb + ln
+    return score, bytes(ops)
 
 
 # ---------------------------------------------------------------------------

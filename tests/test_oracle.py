@@ -621,3 +621,86 @@ def test_calibrated_policy_reductions():
     np.testing.assert_allclose(oracle.band_calibrated(knots, mid), (knots[:-1] + knots[1:]) / 2, rtol=1e-6)
     # outputs above 1 use the last knot
     assert oracle.band_calibrated(knots, np.array([1.7], np.float32))[0] == knots[32]
+
+
+# ---------------------------------------------------------------------------
+# k-mer anchored NW (long pairs)
+# ---------------------------------------------------------------------------
+
+def test_kmer_anchors_definition():
+    """Anchors are exactly the k-mers seen once in each sequence, counted
+    with overlaps, at their positions."""
+    rng = np.random.default_rng(61)
+    for _ in range(30):
+        a, b = _rand_dna(rng, int(rng.integers(0, 60))), _rand_dna(rng, int(rng.integers(0, 60)))
+        k = int(rng.integers(2, 5))
+        ref = []
+        for i in range(len(a) - k + 1):
+            w = a[i:i + k]
+            ia = [t for t in range(len(a) - k + 1) if a[t:t + k] == w]
+            jb = [t for t in range(len(b) - k + 1) if b[t:t + k] == w]
+            if len(ia) == 1 and len(jb) == 1:
+                ref.append((i, jb[0]))
+        assert oracle.kmer_anchors(a, b, k) == ref
+
+
+def test_anchor_chain_is_a_longest_increasing_chain():
+    rng = np.random.default_rng(62)
+    for _ in range(40):
+        n = int(rng.integers(0, 9))
+        anchors = sorted({(int(x), int(y)) for x, y in rng.integers(0, 12, (n, 2))})
+        anchors = [(i, j) for t, (i, j) in enumerate(anchors) if t == 0 or i != anchors[t - 1][0]]
+        chain = oracle.anchor_chain(anchors)
+        assert all(p in anchors for p in chain)
+        assert all(chain[t][0] < chain[t + 1][0] and chain[t][1] < chain[t + 1][1] for t in range(len(chain) - 1))
+        best = 0
+        for mask in range(1 << len(anchors)):
+            sub = [anchors[t] for t in range(len(anchors)) if mask >> t & 1]
+            if all(sub[t][1] < sub[t + 1][1] for t in range(len(sub) - 1)):
+                best = max(best, len(sub))
+        assert len(chain) == best
+
+
+def test_nw_anchored_properties():
+    """The split alignment is a valid alignment whose cost it reports, never
+    below the optimum, equal to it for identical or anchor-free pairs, and
+    its blocks are exact matches in order."""
+    rng = np.random.default_rng(63)
+    for _ in range(25):
+        L = int(rng.integers(50, 600))
+        a = _rand_dna(rng, L)
+        b = bytearray(a)
+        for _ in range(int(rng.integers(0, L // 10 + 1))):
+            p = int(rng.integers(0, len(b)))
+            b[p] = b"ACGT"[int(rng.integers(0, 4))]
+        if rng.random() < 0.5 and len(b) > 20:
+            del b[5:8]
+        b = bytes(b)
+        score, ops = oracle.nw_anchored(a, b, k=8)
+        assert oracle.rescore(a, b, ops)[0] == score
+        assert score >= oracle.nw(a, b)[0]
+        blocks = oracle.anchor_blocks(oracle.anchor_chain(oracle.kmer_anchors(a, b, 8)), 8)
+        for t, (sa, sb, ln) in enumerate(blocks):
+            assert a[sa:sa + ln] == b[sb:sb + ln]
+            if t:
+                pa, pb, pl = blocks[t - 1]
+                assert sa >= pa + pl and sb >= pb + pl
+    a = _rand_dna(rng, 300)
+    assert oracle.nw_anchored(a, a, k=8) == (0, b"M" * 300)
+    # unrelated sequences over disjoint alphabets: no anchors, plain NW
+    x, y = b"AC" * 40, b"GT" * 30
+    assert oracle.nw_anchored(x, y, k=4) == oracle.nw(x, y)
+
+
+def test_nw_anchored_hand_worked_split():
+    # a = ACAGGGCCCTTT, b = AAGGGCCCTTAT.  The 6-mers seen once in each:
+    # AGGGCC (2, 1), GGGCCC (3, 2), GGCCCT (4, 3), GCCCTT (5, 4), all on one
+    # diagonal, so one block a[2:11] = b[1:10] (9 matches).  Left of it:
+    # nw(AC, A) = 1 as M then D; right of it: nw(T, AT) = 1 as I then M.
+    a = b"ACAGGGCCCTTT"
+    b = b"AAGGGCCCTTAT"
+    assert oracle.kmer_anchors(a, b, 6) == [(2, 1), (3, 2), (4, 3), (5, 4)]
+    assert oracle.anchor_blocks(oracle.anchor_chain(oracle.kmer_anchors(a, b, 6)), 6) == [(2, 1, 9)]
+    assert oracle.nw(b"AC", b"A") == (1, b"MD")
+    assert oracle.nw(b"T", b"AT") == (1, b"IM")
+    assert oracle.nw_anchored(a, b, k=6) == (2, b"MD" + b"M" * 9 + b"IM")
