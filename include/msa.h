@@ -359,6 +359,37 @@ msa_status msa_nw_align_batch_affine_sub(msa_ctx *ctx, const uint8_t *codes, con
                                          int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off,
                                          int32_t *ops_len_out, void *stream);
 
+/* ---- NW split at k-mer anchors (section "Discussion and Future Work") ---- */
+/*
+ * The paper names splitting long alignments at k-mer anchors as a way to
+ * scale to longer sequences without fixing a method; this library's method:
+ *   anchors: every (i, j) where the k-mer a[i .. i+k) occurs exactly once in
+ *     a and exactly once in b and b[j .. j+k) is that k-mer;
+ *   chain: the longest chain of anchors increasing in i and j, by patience
+ *     sorting over the anchors in i order (an anchor replaces the first tail
+ *     whose j is >= its own and links to the tail before it);
+ *   blocks, along the chain: an anchor on the current block's diagonal that
+ *     starts inside it or right after it extends the block to its own end,
+ *     one that starts at or after the block's end in both sequences starts a
+ *     new block, any other is dropped;
+ *   each block is aligned as a run of matches ('M', cost match per column),
+ *     every segment between blocks (and before the first, after the last) by
+ *     msa_nw_align_batch with the same costs; scripts and costs are joined.
+ * The cost is an upper bound of the NW optimum (equal to it when an optimal
+ * alignment passes through every block); without anchors it is the NW
+ * result.  k in 1..256; k-mers are compared as bytes (any byte values).
+ * Sequences, pairs and outputs as in msa_nw_align_batch (a bad pair is
+ * reported by msa_ctx_check as there and its outputs are left unwritten).
+ * The workspace holds a hash table of 2^ceil(log2(2 max_len)) 20-byte slots
+ * and 16 max_len bytes per resident pair block, then the segments.
+ * Synchronous: the host reads the segment count, bytes and longest segment
+ * once per call, then the segment alignments run as one msa_nw_align_batch.
+ */
+msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                       int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t k,
+                                       int32_t match, int32_t mismatch, int32_t gap, int32_t *score_out,
+                                       uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out, void *stream);
+
 /* ---- A11: guide tree by Alg. 1 (Partition) ------------------------------ */
 /*
  * Builds the binary cluster tree of Alg. 1 (section "Clustering") over the

@@ -501,7 +501,7 @@ def band_policy(yhat, la, lb, gamma: float, margin: int, knots=None) -> np.ndarr
 
 # ---------------------------------------------------------------------------
 # k-mer anchored splitting of long alignments (the paper's future work for
-# length scaling, section "Conclusion"; the definition below is this
+# length scaling, section "Discussion and Future Work"; the definition below is this
 # project's, the paper gives none)
 # ---------------------------------------------------------------------------
 

@@ -257,6 +257,32 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
     return score, ops, ops_off, ops_len
 
 
+def nw_align_batch_anchored(ctx: Context, seqs, pairs, k=12, match=0, mismatch=1, gap=1,
+                            ops_off: torch.Tensor | None = None, stream=None):
+    """NW split at unique k-mer anchors (msa_nw_align_batch_anchored):
+    runs of matches along the chained anchors, NW on the segments between
+    them.  Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64,
+    ops_len[P] int32)`` like :func:`nw_align_batch`."""
+    if isinstance(seqs, DeviceSeqs):
+        seqs = ByteSeqs.from_device_seqs(seqs)
+    pairs = _pairs_tensor(pairs)
+    P = pairs.shape[0]
+    dev = pairs.device
+    if ops_off is None:
+        lens = seqs.offs[1:] - seqs.offs[:-1]
+        cap = lens[pairs[:, 0].long()] + lens[pairs[:, 1].long()]
+        ops_off = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(cap, 0, out=ops_off[1:])
+    cap_total = int(ops_off[-1].item()) if P else 0
+    ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
+    score = torch.empty(P, dtype=torch.int32, device=dev)
+    ops_len = torch.empty(P, dtype=torch.int32, device=dev)
+    ctx.raise_if(_lib.lib().msa_nw_align_batch_anchored(
+        ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, k, match,
+        mismatch, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    return score, ops, ops_off, ops_len
+
+
 def blosum62_table(device="cuda") -> torch.Tensor:
     """BLOSUM62 as costs (-score) over the protein codes 0..19 and the gap
     code 20 of gapped centre rows: int32 [21, 21] (see ``substitution``)."""

@@ -130,12 +130,13 @@ __global__ void count_kernel(PairList L, int32_t n, const int64_t *__restrict__ 
 // microseconds (one block walking the whole array took ~0.2 ms at 200,000).
 constexpr int kScanTile = 4096;
 
-__device__ __forceinline__ int32_t block_sum_1024(int32_t v, int32_t *wsum) {
+template <class T>
+__device__ __forceinline__ T block_sum_1024(T v, T *wsum) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
-    int32_t t = threadIdx.x < 32 ? wsum[threadIdx.x] : 0;
+    T t = threadIdx.x < 32 ? wsum[threadIdx.x] : T(0);
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -148,11 +149,11 @@ __device__ __forceinline__ int32_t block_sum_1024(int32_t v, int32_t *wsum) {
     return t;
 }
 
-__global__ void __launch_bounds__(1024) tile_sum_kernel(const int32_t *__restrict__ in, int32_t n,
-                                                        int32_t *__restrict__ tsum) {
-    __shared__ int32_t wsum[32];
+template <class T>
+__global__ void __launch_bounds__(1024) tile_sum_kernel(const T *__restrict__ in, int32_t n, T *__restrict__ tsum) {
+    __shared__ T wsum[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int32_t v = 0;
+    T v = 0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int64_t i = base + r * 1024 + threadIdx.x;
@@ -162,18 +163,18 @@ __global__ void __launch_bounds__(1024) tile_sum_kernel(const int32_t *__restric
     if (threadIdx.x == 0) tsum[blockIdx.x] = v;
 }
 
-__global__ void __launch_bounds__(1024) tile_scan_kernel(const int32_t *__restrict__ in, int32_t n,
-                                                         const int32_t *__restrict__ tsum,
-                                                         int32_t *__restrict__ out) {
-    __shared__ int32_t wsum[32];
-    __shared__ int32_t wpre[32];
+template <class T>
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const T *__restrict__ in, int32_t n, const T *__restrict__ tsum,
+                                                         T *__restrict__ out) {
+    __shared__ T wsum[32];
+    __shared__ T wpre[32];
     // the sum of the tiles before this one
-    int32_t pre = 0;
+    T pre = 0;
     for (int t = threadIdx.x; t < (int)blockIdx.x; t += 1024) pre += tsum[t];
     pre = block_sum_1024(pre, wsum);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * (int64_t)threadIdx.x;
-    int32_t x[4];
-    int32_t own = 0;
+    T x[4];
+    T own = 0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         x[r] = base + r < n ? in[base + r] : 0;
@@ -181,25 +182,25 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int32_t *__restri
     }
     // exclusive scan of the per-thread sums across the block
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t inc = own;
+    T inc = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        const T y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) wpre[w] = inc;
     __syncthreads();
     if (w == 0) {
-        int32_t t = wpre[lane];
+        T t = wpre[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            const T y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
         wpre[lane] = t;
     }
     __syncthreads();
-    int32_t run = pre + (w ? wpre[w - 1] : 0) + inc - own;
+    T run = pre + (w ? wpre[w - 1] : T(0)) + inc - own;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         if (base + r < n) out[base + r] = run;
@@ -216,8 +217,14 @@ int64_t scan_tiles(int64_t n) { return std::max<int64_t>(1, (n + kScanTile - 1) 
 // scan_tiles(n) ints of scratch.
 void exclusive_scan(const int32_t *in, int32_t n, int32_t *out, int32_t *tsum, cudaStream_t st) {
     const int tiles = (int)scan_tiles(n);
-    tile_sum_kernel<<<tiles, 1024, 0, st>>>(in, n, tsum);
-    tile_scan_kernel<<<tiles, 1024, 0, st>>>(in, n, tsum, out);
+    tile_sum_kernel<int32_t><<<tiles, 1024, 0, st>>>(in, n, tsum);
+    tile_scan_kernel<int32_t><<<tiles, 1024, 0, st>>>(in, n, tsum, out);
+}
+
+void exclusive_scan64(const int64_t *in, int32_t n, int64_t *out, int64_t *tsum, cudaStream_t st) {
+    const int tiles = (int)scan_tiles(n);
+    tile_sum_kernel<int64_t><<<tiles, 1024, 0, st>>>(in, n, tsum);
+    tile_scan_kernel<int64_t><<<tiles, 1024, 0, st>>>(in, n, tsum, out);
 }
 
 __global__ void scatter_kernel(PairList L, int32_t n, const int64_t *__restrict__ offs, int64_t total,

@@ -147,6 +147,11 @@ msa_status nw_affine_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const in
                          int32_t mismatch, int32_t open, int32_t ext, int32_t *score_out, uint8_t *ops_out,
                          const int64_t *ops_off, int32_t *ops_len_out, cudaStream_t st, const int32_t *sub = nullptr,
                          int32_t nsym = 0);
+// out[0..n] = exclusive prefix sums of in[0..n) and the total (tile scan,
+// two launches); tsum: scan_tiles(n) values of scratch.
+int64_t scan_tiles(int64_t n);
+void exclusive_scan(const int32_t *in, int32_t n, int32_t *out, int32_t *tsum, cudaStream_t st);
+void exclusive_scan64(const int64_t *in, int32_t n, int64_t *out, int64_t *tsum, cudaStream_t st);
 msa_status nw_run(msa_ctx *ctx, Arena &ar, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
                   int32_t max_len, const int32_t *pairs, int64_t P, int32_t match, int32_t mismatch, int32_t gap,
                   int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,

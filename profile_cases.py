@@ -11,6 +11,7 @@
     python profile_cases.py protein # 10,000 x 100 centre distances; guide tree and 9,999 merges of the 10,000
     python profile_cases.py nw_affine # NW with affine gaps (open 10, extend 1), 2,000 pairs
     python profile_cases.py metrics # MSA quality of a 3,000-sequence MSA, 2,000-row sample
+    python profile_cases.py nw_long # 512 pairs of 6,000-10,000: plain NW against NW split at k-mer anchors
 
 Each case runs its call a few times (the first warms up) and prints one
 line with the call's device time.
@@ -180,8 +181,34 @@ def case_protein(ctx):
     return t_lev + t_tree + t_merge
 
 
+def case_nw_long(ctx):
+    """512 DNA pairs of 6,000-10,000 at 1-10 % divergence: plain NW against
+    NW split at unique 12-mer anchors, in a 64 GB workspace (the plain
+    traceback needs about max_len^2 bits per pair in flight)."""
+    big = api.Context(0, workspace_bytes=64 << 30)
+    ds = synth.divergent_pairs(seed=44, n_pairs=512, len_lo=6000, len_hi=10000, div_lo=0.01, div_hi=0.10)
+    sq = api.upload_and_pack(big, ds)
+    pairs = torch.from_numpy(np.stack([np.arange(0, ds.n, 2), np.arange(1, ds.n, 2)], 1).astype(np.int32)).cuda()
+    off = _nw_offsets(sq, pairs)
+    ops = torch.empty(int(off[-1].item()), dtype=torch.uint8, device="cuda")
+    t_plain = _time(lambda: api.nw_align_batch(big, sq, pairs, ops_off=off, ops=ops))
+    opt = api.nw_align_batch(big, sq, pairs, ops_off=off, ops=ops)[0].cpu()
+    res = {}
+    for k in (12, 16):
+        t = _time(lambda: api.nw_align_batch_anchored(big, sq, pairs, k, ops_off=off))
+        sc = api.nw_align_batch_anchored(big, sq, pairs, k, ops_off=off)[0].cpu()
+        big.check()
+        res[k] = (t, float((sc == opt).float().mean()), float(((sc - opt).float() / opt.clamp(min=1).float()).max()))
+    print(f"plain NW {t_plain:.2f} ms; " + "; ".join(
+        f"anchored k={k}: {t:.2f} ms ({t_plain / t:.1f}x), optimal on {100 * eq:.1f} % of pairs, worst excess "
+        f"{100 * ex:.2f} %" for k, (t, eq, ex) in res.items()))
+    big.close()
+    return res[12][0]
+
+
 CASES = dict(lev=case_lev, lev_few=case_lev_few, tree=case_tree, nw=case_nw, band=case_band, band_small=case_band_small, pack=case_pack, mlp=case_mlp,
-             protein=case_protein, nw_affine=case_nw_affine, metrics=case_metrics)
+             protein=case_protein, nw_affine=case_nw_affine, metrics=case_metrics,
+             nw_long=case_nw_long)
 
 
 def main(argv):
