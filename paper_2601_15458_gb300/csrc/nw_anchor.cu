@@ -21,9 +21,10 @@
 // Device steps: anchor_chain_kernel (one block per pair: a hash table of
 // a's k-mers with occurrence counts in both sequences, the anchors marked by
 // their i, the chain and the blocks by one thread), scans of the segment
-// counts and bytes, one read-back of the two totals, seg_build_kernel (the
-// segments' bytes into an arena of their own), nw_run on the segments, and
-// assemble_kernel (one warp per pair joins the scripts and adds the costs).
+// counts and bytes, one read-back of the two totals and the longest segment,
+// seg_build_kernel (the segments' bytes into an arena of their own, one warp
+// per segment), nw_run on the segments, and assemble_kernel (a block scan of
+// the segments' script lengths places them; the costs are added up).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,7 +58,7 @@ struct AnchorArgs {
     int32_t tbits;            // log2 of the table size (>= 2 max_len entries)
     char *slabs;              // per-block scratch
     int64_t slab_bytes;
-    int3 *blocks;             // [P][bcap]: start in a, start in b, length
+    int4 *blocks;             // [P][bcap]: start in a, start in b, length, matched before
     int32_t bcap;
     int32_t *nblocks;         // [P]
     int32_t *seg_count;       // [P] segments (blocks + 1)
@@ -81,14 +82,22 @@ __device__ __forceinline__ bool same_kmer(const uint8_t *x, const uint8_t *y, in
 }
 
 __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs a) {
-    __shared__ int32_t s_pair;
+    // chunks of the per-position arrays staged by the whole block, so the
+    // serial chain passes of thread 0 read shared memory, not global
+    constexpr int kChunk = 2048;
+    __shared__ int32_t s_a[kChunk], s_b[kChunk];
+    __shared__ int32_t s_pair, s_len, s_last, s_want;
     char *slab = a.slabs + (int64_t)blockIdx.x * a.slab_bytes;
     const int64_t tsize = int64_t(1) << a.tbits;
     KmerSlot *table = reinterpret_cast<KmerSlot *>(slab);
+    // per position of a: its anchor's j (-1: none) and its chain level;
+    // the patience tails; the chain (positions in a, in b)
+    const int64_t L4 = ((int64_t)a.max_len + 3) & ~int64_t(3);
     int32_t *aj = reinterpret_cast<int32_t *>(slab + tsize * sizeof(KmerSlot));
-    int32_t *tails = aj + a.max_len;
-    int32_t *tidx = tails + a.max_len;
-    int32_t *prev = tidx + a.max_len;
+    int32_t *level = aj + L4;
+    int32_t *tails = level + L4;
+    int32_t *cj = tails + L4;
+    int32_t *ci = tails;          // written over the tails once they are done
     const int k = a.k;
     while (true) {
         if (threadIdx.x == 0) s_pair = atomicAdd(a.counter, 1);
@@ -153,54 +162,125 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
         for (int64_t t = threadIdx.x; t < (int64_t(1) << tb); t += blockDim.x)
             if (table[t].ca == 1 && table[t].cb == 1) aj[table[t].pa] = table[t].pb;
         __syncthreads();
-        // chain and blocks: one thread
-        if (threadIdx.x == 0) {
-            int len = 0;
-            for (int i = 0; i < m; ++i) {
-                const int j = aj[i];
-                if (j < 0) continue;
-                int lo = 0, hi = len;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (tails[mid] < j) lo = mid + 1;
-                    else hi = mid;
-                }
-                tails[lo] = j;
-                tidx[lo] = i;
-                prev[i] = lo > 0 ? tidx[lo - 1] : -1;
-                if (lo == len) ++len;
-            }
-            // the chain back to front into tails[] as anchor i's (front first)
-            int c = len;
-            for (int i = len ? tidx[len - 1] : -1; i >= 0; i = prev[i]) tails[--c] = i;
-            int3 *bl = a.blocks + (int64_t)p * a.bcap;
-            int nb = 0;
-            int64_t matched = 0;
-            for (int t = 0; t < len; ++t) {
-                const int i = tails[t], j = aj[i];
-                if (nb) {
-                    int3 &cur = bl[nb - 1];
-                    if (j - i == cur.y - cur.x && i <= cur.x + cur.z) {
-                        const int nl = max(cur.z, i + k - cur.x);
-                        matched += nl - cur.z;
-                        cur.z = nl;
-                        continue;
+        // chain and blocks: one thread, over chunks the block stages.
+        // Patience sorting in a's order; an anchor past the last tail (most
+        // of them when the pair is related) extends the longest chain
+        // without a search.  level[i] = the chain length ending at anchor i,
+        // minus one.
+        int len = 0, last_j = -1, last_i = -1;
+        for (int c0 = 0; c0 < m; c0 += kChunk) {
+            const int cn = min(kChunk, m - c0);
+            for (int t = threadIdx.x; t < cn; t += blockDim.x) s_a[t] = aj[c0 + t];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int t = 0; t < cn; ++t) {
+                    const int j = s_a[t];
+                    if (j < 0) continue;
+                    int lo = len;
+                    if (j < last_j) {            // first tail >= j lies in [0, len - 1]
+                        int lo2 = 0, hi = len - 1;
+                        while (lo2 < hi) {
+                            const int mid = (lo2 + hi) >> 1;
+                            if (tails[mid] < j) lo2 = mid + 1;
+                            else hi = mid;
+                        }
+                        lo = lo2;
                     }
-                    if (i < cur.x + cur.z || j < cur.y + cur.z) continue;
+                    tails[lo] = j;
+                    s_b[t] = lo;
+                    if (lo == len) ++len;
+                    if (lo == len - 1) {
+                        last_j = j;
+                        last_i = c0 + t;
+                    }
                 }
-                if (nb == a.bcap) {          // cannot happen for blocks of >= k residues in a
-                    record_error(a.err, kErrCapacity, p, nb);
-                    break;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < cn; t += blockDim.x)
+                if (s_a[t] >= 0) level[c0 + t] = s_b[t];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_len = len;
+            s_last = last_i;
+            s_want = len - 1;
+        }
+        __syncthreads();
+        len = s_len;
+        last_i = s_last;
+        // the chain, back to front: the anchor that set the last tail, then
+        // before each chain anchor the nearest anchor one level lower (the
+        // one whose tail it linked to when it was placed)
+        int c = len, want = len - 1;
+        for (int hi = last_i + 1; hi > 0 && s_want >= 0; hi -= kChunk) {
+            const int lo = max(0, hi - kChunk), cn = hi - lo;
+            for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+                s_a[t] = aj[lo + t];
+                s_b[t] = level[lo + t];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int t = cn - 1; t >= 0 && want >= 0; --t) {
+                    const int j = s_a[t];
+                    if (j >= 0 && s_b[t] == want) {
+                        --c;
+                        ci[c] = lo + t;
+                        cj[c] = j;
+                        --want;
+                    }
                 }
-                bl[nb++] = make_int3(i, j, k);
-                matched += k;
+                s_want = want;
             }
-            int ia = 0, ib = 0, longest = 0;
-            for (int t = 0; t <= nb; ++t) {
-                const int sa = t < nb ? bl[t].x : m, sb = t < nb ? bl[t].y : n;
-                longest = max(longest, max(sa - ia, sb - ib));
-                if (t < nb) ia = sa + bl[t].z, ib = sb + bl[t].z;
+            __syncthreads();
+        }
+        // blocks along the chain, the open one in thread 0's registers; each
+        // block records the matched length before it (for segment offsets)
+        int4 *bl = a.blocks + (int64_t)p * a.bcap;
+        int nb = 0, bx = -1, by = 0, bz = 0, ia = 0, ib = 0, longest = 0;
+        int64_t matched = 0;
+        bool full = false;
+        auto close_block = [&]() {
+            if (nb == a.bcap) {                  // cannot happen: blocks are >= k residues of a apart
+                full = true;
+                return;
             }
+            bl[nb++] = make_int4(bx, by, bz, (int)(matched - bz));
+            longest = max(longest, max(bx - ia, by - ib));
+            ia = bx + bz;
+            ib = by + bz;
+        };
+        for (int c0 = 0; c0 < len; c0 += kChunk) {
+            const int cn = min(kChunk, len - c0);
+            for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+                s_a[t] = ci[c0 + t];
+                s_b[t] = cj[c0 + t];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int t = 0; t < cn && !full; ++t) {
+                    const int i = s_a[t], j = s_b[t];
+                    if (bx >= 0) {
+                        if (j - i == by - bx && i <= bx + bz) {
+                            const int nl = max(bz, i + k - bx);
+                            matched += nl - bz;
+                            bz = nl;
+                            continue;
+                        }
+                        if (i < bx + bz || j < by + bz) continue;
+                        close_block();
+                    }
+                    bx = i;
+                    by = j;
+                    bz = k;
+                    matched += k;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (bx >= 0 && !full) close_block();
+            if (full) record_error(a.err, kErrCapacity, p, nb);
+            longest = max(longest, max(m - ia, n - ib));
             atomicMax(a.counter + 1, longest);
             a.nblocks[p] = nb;
             a.seg_count[p] = nb + 1;
@@ -210,77 +290,146 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
     }
 }
 
+// Exclusive scan of one value per thread over the block (kAnchorThreads);
+// returns the thread's prefix and leaves the block total in *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kAnchorThreads / 32; ++w) {
+            const int t = warp_sums[w];
+            warp_sums[w] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return warp_sums[wid] + incl - v;
+}
+
+// Segment s of a pair runs from the end of block s - 1 (or the start) to the
+// start of block s (or the end) in both sequences; blocks[.].w is the
+// matched length before the block, so the bytes of the pair's earlier
+// segments are (start in a + start in b - 2 x matched before).
+struct SegSpan {
+    int ia, ib, sa, sb, cum;
+};
+
+__device__ __forceinline__ SegSpan seg_span(const int4 *bl, int nb, int s, int m, int n) {
+    SegSpan r{0, 0, m, n, 0};
+    if (s > 0) {
+        const int4 b = bl[s - 1];
+        r.ia = b.x + b.z;
+        r.ib = b.y + b.z;
+        r.cum = b.w + b.z;
+    }
+    if (s < nb) {
+        const int4 b = bl[s];
+        r.sa = b.x;
+        r.sb = b.y;
+    }
+    return r;
+}
+
 // Writes the segments of every pair: their bytes into the segment arena
 // (a-part then b-part), the pseudo-sequence offsets and the pseudo pairs.
+// One block per pair, one warp per segment.
 __global__ void __launch_bounds__(kAnchorThreads) seg_build_kernel(
     const uint8_t *__restrict__ codes, const int64_t *__restrict__ offs, const int32_t *__restrict__ pairs, int32_t P,
-    const int3 *__restrict__ blocks, int32_t bcap, const int32_t *__restrict__ nblocks,
+    const int4 *__restrict__ blocks, int32_t bcap, const int32_t *__restrict__ nblocks,
     const int32_t *__restrict__ seg_start, const int64_t *__restrict__ byte_start, uint8_t *__restrict__ seg_codes,
     int64_t *__restrict__ seg_offs, int32_t *__restrict__ seg_pairs) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int p = blockIdx.x; p < P; p += gridDim.x) {
-        const int nb = nblocks[p];
         if (seg_start[p + 1] == seg_start[p]) continue;   // a rejected pair
+        const int nb = nblocks[p];
         const int64_t xa = offs[pairs[2 * p]], ya = offs[pairs[2 * p + 1]];
         const int m = (int)(offs[pairs[2 * p] + 1] - xa), n = (int)(offs[pairs[2 * p + 1] + 1] - ya);
-        const int3 *bl = blocks + (int64_t)p * bcap;
-        int ia = 0, ib = 0;
-        int64_t w = byte_start[p];
-        for (int s = 0; s <= nb; ++s) {
-            const int sa = s < nb ? bl[s].x : m, sb = s < nb ? bl[s].y : n;
-            const int g = seg_start[p] + s;
-            const int la = sa - ia, lb = sb - ib;
-            for (int t = threadIdx.x; t < la; t += blockDim.x) seg_codes[w + t] = codes[xa + ia + t];
-            for (int t = threadIdx.x; t < lb; t += blockDim.x) seg_codes[w + la + t] = codes[ya + ib + t];
-            if (threadIdx.x == 0) {
+        const int4 *bl = blocks + (int64_t)p * bcap;
+        const int g0 = seg_start[p];
+        const int64_t w0 = byte_start[p];
+        for (int sg = wid; sg <= nb; sg += kAnchorThreads / 32) {
+            const SegSpan sp = seg_span(bl, nb, sg, m, n);
+            const int la = sp.sa - sp.ia, lb = sp.sb - sp.ib;
+            const int64_t w = w0 + sp.ia + sp.ib - 2 * (int64_t)sp.cum;
+            for (int t = lane; t < la; t += 32) seg_codes[w + t] = codes[xa + sp.ia + t];
+            for (int t = lane; t < lb; t += 32) seg_codes[w + la + t] = codes[ya + sp.ib + t];
+            if (lane == 0) {
+                const int g = g0 + sg;
                 seg_offs[2 * g] = w;
                 seg_offs[2 * g + 1] = w + la;
                 seg_offs[2 * g + 2] = w + la + lb;
                 seg_pairs[2 * g] = 2 * g;
                 seg_pairs[2 * g + 1] = 2 * g + 1;
             }
-            w += la + lb;
-            if (s < nb) {
-                ia = sa + bl[s].z;
-                ib = sb + bl[s].z;
-            }
         }
     }
 }
 
-// One warp per pair: the segments' scripts with each block's run of matches
-// between them, and the total cost.
-__global__ void assemble_kernel(int32_t P, const int3 *__restrict__ blocks, int32_t bcap,
-                                const int32_t *__restrict__ nblocks, const int32_t *__restrict__ seg_start,
-                                const int32_t *__restrict__ seg_score, const uint8_t *__restrict__ seg_ops,
-                                const int64_t *__restrict__ seg_ops_off, const int32_t *__restrict__ seg_ops_len,
-                                int32_t match, int32_t *__restrict__ score_out, uint8_t *__restrict__ ops_out,
-                                const int64_t *__restrict__ ops_off, int32_t *__restrict__ ops_len_out) {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+// Joins the segments' scripts with each block's run of matches between
+// them and adds up the cost.  One block per pair: a block scan of the
+// segments' script lengths places each segment, then one warp per segment
+// copies its script and the block after it.
+__global__ void __launch_bounds__(kAnchorThreads) assemble_kernel(
+    int32_t P, const int4 *__restrict__ blocks, int32_t bcap, const int32_t *__restrict__ nblocks,
+    const int32_t *__restrict__ seg_start, const int32_t *__restrict__ seg_score, const uint8_t *__restrict__ seg_ops,
+    const int64_t *__restrict__ seg_ops_off, const int32_t *__restrict__ seg_ops_len, int32_t match,
+    int32_t *__restrict__ score_out, uint8_t *__restrict__ ops_out, const int64_t *__restrict__ ops_off,
+    int32_t *__restrict__ ops_len_out) {
+    __shared__ int warp_sums[kAnchorThreads / 32];
+    __shared__ int s_total, s_score;
+    __shared__ int64_t s_pos[kAnchorThreads];
+    __shared__ int s_len[kAnchorThreads];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int p = blockIdx.x; p < P; p += gridDim.x) {
         if (seg_start[p + 1] == seg_start[p]) continue;   // a rejected pair (error recorded)
         const int nb = nblocks[p];
-        const int3 *bl = blocks + (int64_t)p * bcap;
-        int64_t w = ops_off[p];
-        int score = 0;
-        for (int s = 0; s <= nb; ++s) {
-            const int g = seg_start[p] + s;
-            const int L = seg_ops_len[g];
-            const uint8_t *src = seg_ops + seg_ops_off[g];
-            for (int t = lane; t < L; t += 32) ops_out[w + t] = src[t];
-            w += L;
-            score += seg_score[g];
-            if (s < nb) {
-                const int z = bl[s].z;
-                for (int t = lane; t < z; t += 32) ops_out[w + t] = 'M';
-                w += z;
-                score += z * match;
+        const int4 *bl = blocks + (int64_t)p * bcap;
+        const int g0 = seg_start[p];
+        const int64_t base = ops_off[p];
+        if (threadIdx.x == 0) s_score = 0;
+        int64_t carry = 0;                                  // script bytes of earlier chunks
+        for (int s0 = 0; s0 <= nb; s0 += kAnchorThreads) {
+            const int sg = s0 + threadIdx.x;
+            const bool live = sg <= nb;
+            const int L = live ? seg_ops_len[g0 + sg] : 0;
+            const int excl = block_exclusive_scan(L, warp_sums, &s_total);
+            if (live) {
+                const int cum = sg > 0 ? bl[sg - 1].w + bl[sg - 1].z : 0;
+                s_pos[threadIdx.x] = base + carry + excl + cum;
+                s_len[threadIdx.x] = L;
+                atomicAdd(&s_score, seg_score[g0 + sg]);
             }
+            __syncthreads();
+            const int cnt = min(kAnchorThreads, nb + 1 - s0);
+            for (int t = wid; t < cnt; t += kAnchorThreads / 32) {
+                const int g = g0 + s0 + t;
+                const uint8_t *src = seg_ops + seg_ops_off[g];
+                const int64_t pos = s_pos[t];
+                const int len = s_len[t];
+                for (int u = lane; u < len; u += 32) ops_out[pos + u] = src[u];
+                if (s0 + t < nb) {
+                    const int z = bl[s0 + t].z;
+                    for (int u = lane; u < z; u += 32) ops_out[pos + len + u] = 'M';
+                }
+            }
+            carry += s_total;
+            __syncthreads();
         }
-        if (lane == 0) {
-            score_out[p] = score;
-            ops_len_out[p] = (int32_t)(w - ops_off[p]);
+        if (threadIdx.x == 0) {
+            const int matched = nb > 0 ? bl[nb - 1].w + bl[nb - 1].z : 0;
+            score_out[p] = s_score + matched * match;
+            ops_len_out[p] = (int32_t)(carry + matched);
         }
+        __syncthreads();
     }
 }
 
@@ -306,10 +455,10 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
     const int Pi = (int)P;
     int tbits = 4;
     while ((int64_t(1) << tbits) < 2 * (int64_t)std::max(max_len, 1)) ++tbits;
-    const int64_t slab = ((int64_t(1) << tbits) * (int64_t)sizeof(KmerSlot) + 4 * (int64_t)max_len * 4 + 255) / 256 * 256;
+    const int64_t slab = ((int64_t(1) << tbits) * (int64_t)sizeof(KmerSlot) + 4 * (((int64_t)max_len + 3) & ~int64_t(3)) * 4 + 255) / 256 * 256;
     const int32_t bcap = max_len / k + 1;
     Arena ar{ctx->ws, ctx->ws_bytes};
-    int3 *blocks = ar.take<int3>((int64_t)Pi * bcap);
+    int4 *blocks = ar.take<int4>((int64_t)Pi * bcap);
     int32_t *nblocks = ar.take<int32_t>(Pi);
     int32_t *seg_count = ar.take<int32_t>(Pi + 1);
     int64_t *seg_bytes = ar.take<int64_t>(Pi + 1);
@@ -364,9 +513,9 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
     if (msa_status rc = nw_run(ctx, ar, seg_codes, seg_offs, 2 * S, bytes, seg_max, seg_pairs, S, match, mismatch, gap,
                                seg_score, seg_ops, seg_ops_off, seg_ops_len, st))
         return rc;
-    assemble_kernel<<<std::max(1, std::min((Pi + 3) / 4, 65535)), 128, 0, st>>>(
-        Pi, blocks, bcap, nblocks, seg_start, seg_score, seg_ops, seg_ops_off, seg_ops_len, match, score_out, ops_out,
-        ops_off, ops_len_out);
+    assemble_kernel<<<std::min(Pi, 65535), kAnchorThreads, 0, st>>>(Pi, blocks, bcap, nblocks, seg_start, seg_score,
+                                                                     seg_ops, seg_ops_off, seg_ops_len, match,
+                                                                     score_out, ops_out, ops_off, ops_len_out);
     ++ctx->launches;
     return cuda_check(ctx, cudaGetLastError(), "anchored assemble");
 }
