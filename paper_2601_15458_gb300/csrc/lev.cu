@@ -5,6 +5,7 @@
 // call can be captured in a CUDA graph):
 //   1. count pairs per first index q (the query), checking every index;
 //   2. exclusive scan -> group starts; scatter (target, pair id) by query;
+//      the targets of each query with many of them ordered longest first;
 //   3. per query pick a kernel configuration from its word count
 //      W = ceil(m / 32) and its number of targets c_q: the lane kernel
 //      (one warp per query, a lane per target) when W <= 64 and c_q is large
@@ -252,6 +253,61 @@ __global__ void scatter_kernel(PairList L, int32_t n, const int64_t *__restrict_
     }
 }
 
+// Orders the targets of every query that has at least `min_count` of them
+// by length, longest first: a counting sort on 32-column length classes,
+// one block per query, through tmp_t / tmp_p.  The lanes of a warp then take
+// targets of about the same length one after another, so they switch
+// targets together and the two-column step holds for more of the work, and
+// a query's last targets are its shortest ones.
+constexpr int kLenClasses = 256;
+
+__global__ void __launch_bounds__(kLenClasses) length_order_kernel(
+    const int64_t *__restrict__ offs, int32_t n, const int32_t *__restrict__ qstart, int32_t min_count,
+    int32_t *__restrict__ sorted_t, int32_t *__restrict__ sorted_p, int32_t *__restrict__ tmp_t,
+    int32_t *__restrict__ tmp_p) {
+    __shared__ int32_t cur[kLenClasses];
+    __shared__ int32_t wsum[kLenClasses / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = blockIdx.x; q < n; q += gridDim.x) {
+        const int b = qstart[q], e = qstart[q + 1];
+        if (e - b < min_count) continue;
+        cur[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const int t = sorted_t[i];
+            const int cls = (int)min((offs[t + 1] - offs[t]) >> 5, (int64_t)(kLenClasses - 1));
+            atomicAdd(&cur[kLenClasses - 1 - cls], 1);
+        }
+        __syncthreads();
+        const int v = cur[threadIdx.x];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        cur[threadIdx.x] = b + before + incl - v;
+        __syncthreads();
+        for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const int t = sorted_t[i];
+            const int cls = (int)min((offs[t + 1] - offs[t]) >> 5, (int64_t)(kLenClasses - 1));
+            const int pos = atomicAdd(&cur[kLenClasses - 1 - cls], 1);
+            tmp_t[pos] = t;
+            tmp_p[pos] = sorted_p[i];
+        }
+        __syncthreads();
+        for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+            sorted_t[i] = tmp_t[i];
+            sorted_p[i] = tmp_p[i];
+        }
+        __syncthreads();
+    }
+}
+
 // pass 0: count tasks per bucket; pass 1: write them (bucket offsets by a
 // scan over <= kMaxBuckets counts done redundantly by every block).
 template <int PASS>
@@ -309,7 +365,7 @@ __global__ void __launch_bounds__(256) one_to_many_pairs_kernel(int32_t query, c
 
 int64_t lev_workspace(int64_t P, int32_t n) {
     auto r = [](int64_t b) { return (b + 255) & ~int64_t(255); };
-    return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 2 + r(8 * (P + n + 1)) +
+    return r(4 * int64_t(n)) * 3 + r(4 * (int64_t(n) + 1)) + r(4 * P) * 4 + r(8 * (P + n + 1)) +
            r(4 * kMaxBuckets) * 5 + r(4 * scan_tiles(n));
 }
 
@@ -373,6 +429,8 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     int32_t *qstart = ar.take<int32_t>(int64_t(n) + 1);
     int32_t *sorted_t = ar.take<int32_t>(P);
     int32_t *sorted_p = ar.take<int32_t>(P);
+    int32_t *tmp_t = ar.take<int32_t>(P);
+    int32_t *tmp_p = ar.take<int32_t>(P);
     int2 *tasks = ar.take<int2>(P + n + 1);
     int32_t *bcount = ar.take<int32_t>(kMaxBuckets);
     int32_t *bfill = ar.take<int32_t>(kMaxBuckets);
@@ -396,6 +454,9 @@ msa_status lev_run(msa_ctx *ctx, const msa_seqset *s, const int32_t *pairs, int6
     exclusive_scan(qcount, n, qstart, tsum, st);
     scatter_kernel<<<gP, 256, 0, st>>>(L, n, s->offs, s->total, qstart, qfill, sorted_t, sorted_p);
     const PlanParams pp = plan_params(R, T, P, ctx->sm_count);
+    length_order_kernel<<<grid_for((int)std::min<int64_t>(n, ctx->sm_count * 8)), kLenClasses, 0, st>>>(
+        s->offs, n, qstart, std::max(pp.lane_min_targets, 2), sorted_t, sorted_p, tmp_t, tmp_p);
+    ++ctx->launches;
     task_kernel<0><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, bsum, ctx->dev_err);
     task_kernel<1><<<gN, 256, 0, st>>>(s->offs, n, qstart, pp, bcount, bfill, boff, tasks, bsum, ctx->dev_err);
 
