@@ -35,6 +35,7 @@ namespace msa {
 
 constexpr int kAnchorThreads = 256;
 constexpr int kMaxK = 256;
+constexpr int64_t kSeqSmemMax = 64 * 1024;   // shared bytes for a pair's two sequences
 
 // One distinct k-mer of a: rep is the position in a of the occurrence that
 // claimed the slot (-1 = empty); k-mers are compared byte by byte, so any
@@ -56,6 +57,7 @@ struct AnchorArgs {
     int32_t match;
     int32_t max_len;
     int32_t tbits;            // log2 of the table size (>= 2 max_len entries)
+    int32_t seq_smem;         // bytes of shared memory per sequence (0: read from global)
     char *slabs;              // per-block scratch
     int64_t slab_bytes;
     int4 *blocks;             // [P][bcap]: start in a, start in b, length, matched before
@@ -68,16 +70,29 @@ struct AnchorArgs {
 };
 
 // Multiplicative hash of the k bytes at s (a polynomial in an odd 64-bit
-// base, then Fibonacci hashing to tbits bits).
+// base, then Fibonacci hashing to tbits bits); bytes are read 8 at a time
+// so that the loads of a group are in flight together.
 __device__ __forceinline__ uint32_t kmer_hash(const uint8_t *s, int k, int tbits) {
     unsigned long long h = 0;
-    for (int t = 0; t < k; ++t) h = h * 0x100000001B3ull + (unsigned long long)s[t] + 1ull;
+    for (int t0 = 0; t0 < k; t0 += 8) {
+        uint32_t c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c[u] = t0 + u < k ? s[t0 + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (t0 + u < k) h = h * 0x100000001B3ull + (unsigned long long)c[u] + 1ull;
+    }
     return (uint32_t)((h * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
 }
 
 __device__ __forceinline__ bool same_kmer(const uint8_t *x, const uint8_t *y, int k) {
-    for (int t = 0; t < k; ++t)
-        if (x[t] != y[t]) return false;
+    for (int t0 = 0; t0 < k; t0 += 8) {
+        uint32_t diff = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (t0 + u < k) diff |= (uint32_t)(x[t0 + u] ^ y[t0 + u]);
+        if (diff) return false;
+    }
     return true;
 }
 
@@ -87,6 +102,8 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
     constexpr int kChunk = 2048;
     __shared__ int32_t s_a[kChunk], s_b[kChunk];
     __shared__ int32_t s_pair, s_len, s_last, s_want;
+    // the pair's two sequences, when they fit (a.seq_smem: bytes per side)
+    extern __shared__ uint8_t s_seq[];
     char *slab = a.slabs + (int64_t)blockIdx.x * a.slab_bytes;
     const int64_t tsize = int64_t(1) << a.tbits;
     KmerSlot *table = reinterpret_cast<KmerSlot *>(slab);
@@ -124,6 +141,12 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
             continue;
         }
         const uint8_t *A = a.codes + xa, *B = a.codes + ya;
+        if (a.seq_smem) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) s_seq[i] = A[i];
+            for (int j = threadIdx.x; j < n; j += blockDim.x) s_seq[a.seq_smem + j] = B[j];
+            A = s_seq;
+            B = s_seq + a.seq_smem;
+        }
         // the table of a's k-mers, sized to at least twice their number
         int tb = 4;
         while ((int64_t(1) << tb) < 2 * (int64_t)max(m, 1)) ++tb;
@@ -162,37 +185,72 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
         for (int64_t t = threadIdx.x; t < (int64_t(1) << tb); t += blockDim.x)
             if (table[t].ca == 1 && table[t].cb == 1) aj[table[t].pa] = table[t].pb;
         __syncthreads();
-        // chain and blocks: one thread, over chunks the block stages.
-        // Patience sorting in a's order; an anchor past the last tail (most
-        // of them when the pair is related) extends the longest chain
-        // without a search.  level[i] = the chain length ending at anchor i,
-        // minus one.
+        // Chain and blocks: warp 0 over chunks the block stages.  Patience
+        // sorting in a's order; level[i] = the chain length ending at anchor
+        // i, minus one.  A window of 32 positions whose anchors all lie past
+        // the last tail and increase (most windows when the pair is related)
+        // appends them in one step; any other window is done one anchor at a
+        // time by lane 0, exactly as the definition reads.
+        const int lane = threadIdx.x & 31;
+        const unsigned lt_mask = (1u << lane) - 1u;
         int len = 0, last_j = -1, last_i = -1;
         for (int c0 = 0; c0 < m; c0 += kChunk) {
             const int cn = min(kChunk, m - c0);
             for (int t = threadIdx.x; t < cn; t += blockDim.x) s_a[t] = aj[c0 + t];
             __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int t = 0; t < cn; ++t) {
-                    const int j = s_a[t];
-                    if (j < 0) continue;
-                    int lo = len;
-                    if (j < last_j) {            // first tail >= j lies in [0, len - 1]
-                        int lo2 = 0, hi = len - 1;
-                        while (lo2 < hi) {
-                            const int mid = (lo2 + hi) >> 1;
-                            if (tails[mid] < j) lo2 = mid + 1;
-                            else hi = mid;
+            if (threadIdx.x < 32) {
+                for (int w0 = 0; w0 < cn; w0 += 32) {
+                    const int t = w0 + lane;
+                    const int j = t < cn ? s_a[t] : -1;
+                    const unsigned amask = __ballot_sync(0xffffffffu, j >= 0);
+                    if (!amask) continue;
+                    int pm = j;                              // running max of j (non-anchors: -1)
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, pm, o);
+                        if (lane >= o) pm = max(pm, v);
+                    }
+                    int before = __shfl_up_sync(0xffffffffu, pm, 1);
+                    before = lane == 0 ? last_j : max(before, last_j);
+                    if (__all_sync(0xffffffffu, j < 0 || j > before)) {
+                        const int r = __popc(amask & lt_mask);
+                        if (j >= 0) {
+                            tails[len + r] = j;
+                            s_b[t] = len + r;
                         }
-                        lo = lo2;
+                        const int top = 31 - __clz(amask);
+                        last_j = __shfl_sync(0xffffffffu, j, top);
+                        last_i = c0 + w0 + top;
+                        len += __popc(amask);
+                    } else {
+                        if (lane == 0) {
+                            for (int u = 0; u < 32 && w0 + u < cn; ++u) {
+                                const int jj = s_a[w0 + u];
+                                if (jj < 0) continue;
+                                int lo = len;
+                                if (jj < last_j) {       // first tail >= jj lies in [0, len - 1]
+                                    int lo2 = 0, hi = len - 1;
+                                    while (lo2 < hi) {
+                                        const int mid = (lo2 + hi) >> 1;
+                                        if (tails[mid] < jj) lo2 = mid + 1;
+                                        else hi = mid;
+                                    }
+                                    lo = lo2;
+                                }
+                                tails[lo] = jj;
+                                s_b[w0 + u] = lo;
+                                if (lo == len) ++len;
+                                if (lo == len - 1) {
+                                    last_j = jj;
+                                    last_i = c0 + w0 + u;
+                                }
+                            }
+                        }
+                        len = __shfl_sync(0xffffffffu, len, 0);
+                        last_j = __shfl_sync(0xffffffffu, last_j, 0);
+                        last_i = __shfl_sync(0xffffffffu, last_i, 0);
                     }
-                    tails[lo] = j;
-                    s_b[t] = lo;
-                    if (lo == len) ++len;
-                    if (lo == len - 1) {
-                        last_j = j;
-                        last_i = c0 + t;
-                    }
+                    __syncwarp();
                 }
             }
             __syncthreads();
@@ -210,7 +268,11 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
         last_i = s_last;
         // the chain, back to front: the anchor that set the last tail, then
         // before each chain anchor the nearest anchor one level lower (the
-        // one whose tail it linked to when it was placed)
+        // one whose tail it linked to when it was placed).  Warp 0 takes 32
+        // positions at a time, lane 0 the highest: when the window's anchors
+        // read want, want - 1, ... from the top they are all taken at once,
+        // otherwise one at a time (the highest anchor at level want below the
+        // last one taken).
         int c = len, want = len - 1;
         for (int hi = last_i + 1; hi > 0 && s_want >= 0; hi -= kChunk) {
             const int lo = max(0, hi - kChunk), cn = hi - lo;
@@ -219,22 +281,49 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
                 s_b[t] = level[lo + t];
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int t = cn - 1; t >= 0 && want >= 0; --t) {
-                    const int j = s_a[t];
-                    if (j >= 0 && s_b[t] == want) {
-                        --c;
-                        ci[c] = lo + t;
-                        cj[c] = j;
-                        --want;
+            if (threadIdx.x < 32) {
+                for (int top = cn - 1; top >= 0 && want >= 0; top -= 32) {
+                    const int t = top - lane;
+                    const int j = t >= 0 ? s_a[t] : -1;
+                    const int lev = j >= 0 ? s_b[t] : -1;
+                    const unsigned amask = __ballot_sync(0xffffffffu, j >= 0);
+                    if (!amask) continue;
+                    const int r = __popc(amask & lt_mask);
+                    if (__all_sync(0xffffffffu, j < 0 || lev == want - r)) {
+                        if (j >= 0) {
+                            ci[c - 1 - r] = lo + t;
+                            cj[c - 1 - r] = j;
+                        }
+                        c -= __popc(amask);
+                        want -= __popc(amask);
+                    } else {
+                        int from = 0;                    // lanes below `from` are above the last taken
+                        while (want >= 0) {
+                            const unsigned hit =
+                                __ballot_sync(0xffffffffu, j >= 0 && lev == want && lane >= from);
+                            if (!hit) break;
+                            const int h = __ffs(hit) - 1;
+                            if (lane == h) {
+                                ci[c - 1] = lo + t;
+                                cj[c - 1] = j;
+                            }
+                            --c;
+                            --want;
+                            from = h + 1;
+                        }
                     }
+                    __syncwarp();
                 }
-                s_want = want;
+                if (lane == 0) s_want = want;
             }
             __syncthreads();
         }
-        // blocks along the chain, the open one in thread 0's registers; each
-        // block records the matched length before it (for segment offsets)
+        // blocks along the chain, the open one held by every lane of warp 0;
+        // each block records the matched length before it (for the segment
+        // offsets).  A run of chain anchors on the open block's diagonal,
+        // each starting inside or right after the block as extended by the
+        // ones before it, extends it in one step; the anchor that ends such
+        // a run is taken alone.
         int4 *bl = a.blocks + (int64_t)p * a.bcap;
         int nb = 0, bx = -1, by = 0, bz = 0, ia = 0, ib = 0, longest = 0;
         int64_t matched = 0;
@@ -244,7 +333,8 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
                 full = true;
                 return;
             }
-            bl[nb++] = make_int4(bx, by, bz, (int)(matched - bz));
+            if (lane == 0) bl[nb] = make_int4(bx, by, bz, (int)(matched - bz));
+            ++nb;
             longest = max(longest, max(bx - ia, by - ib));
             ia = bx + bz;
             ib = by + bz;
@@ -256,23 +346,37 @@ __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs
                 s_b[t] = cj[c0 + t];
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int t = 0; t < cn && !full; ++t) {
-                    const int i = s_a[t], j = s_b[t];
-                    if (bx >= 0) {
-                        if (j - i == by - bx && i <= bx + bz) {
-                            const int nl = max(bz, i + k - bx);
+            if (threadIdx.x < 32) {
+                for (int w0 = 0; w0 < cn && !full; w0 += 32) {
+                    const int wn = min(32, cn - w0);
+                    const int i = lane < wn ? s_a[w0 + lane] : 0, j = lane < wn ? s_b[w0 + lane] : 0;
+                    const int prev_i = __shfl_up_sync(0xffffffffu, i, 1);
+                    int start = 0;
+                    while (start < wn && !full) {
+                        const int end_before = lane == start ? bx + bz : max(bx + bz, prev_i + k);
+                        const bool in = lane >= start && lane < wn;
+                        const bool ok = !in || (bx >= 0 && j - i == by - bx && i <= end_before);
+                        const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+                        const int f = bad ? __ffs(bad) - 1 : wn;
+                        if (f > start) {
+                            const int iend = __shfl_sync(0xffffffffu, i, f - 1);
+                            const int nl = max(bz, iend + k - bx);
                             matched += nl - bz;
                             bz = nl;
-                            continue;
                         }
-                        if (i < bx + bz || j < by + bz) continue;
-                        close_block();
+                        if (f >= wn) break;
+                        const int fi = __shfl_sync(0xffffffffu, i, f), fj = __shfl_sync(0xffffffffu, j, f);
+                        start = f + 1;
+                        if (bx >= 0) {
+                            if (fi < bx + bz || fj < by + bz) continue;   // dropped
+                            close_block();
+                            if (full) break;
+                        }
+                        bx = fi;
+                        by = fj;
+                        bz = k;
+                        matched += k;
                     }
-                    bx = i;
-                    by = j;
-                    bz = k;
-                    matched += k;
                 }
             }
             __syncthreads();
@@ -476,9 +580,14 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
     char *slabs = slabs_ar.take<char>(nblk * slab);
     cudaError_t e = cudaMemsetAsync(counter, 0, 8, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "anchored memset");
-    AnchorArgs aa{codes, offs, n_seqs, total, pairs, Pi, k, match, max_len, tbits, slabs, slab, blocks, bcap,
+    // the pair's sequences go to shared memory when both fit in kSeqSmemMax
+    const int32_t seq_smem = 2 * (((int64_t)max_len + 15) & ~int64_t(15)) <= kSeqSmemMax ? (max_len + 15) & ~15 : 0;
+    if (seq_smem && (e = cudaFuncSetAttribute(anchor_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              2 * seq_smem)) != cudaSuccess)
+        return cuda_check(ctx, e, "anchored smem attribute");
+    AnchorArgs aa{codes, offs, n_seqs, total, pairs, Pi, k, match, max_len, tbits, seq_smem, slabs, slab, blocks, bcap,
                   nblocks, seg_count, seg_bytes, counter, ctx->dev_err};
-    anchor_chain_kernel<<<(int)nblk, kAnchorThreads, 0, st>>>(aa);
+    anchor_chain_kernel<<<(int)nblk, kAnchorThreads, 2 * seq_smem, st>>>(aa);
     exclusive_scan(seg_count, Pi, seg_start, tsum, st);
     exclusive_scan64(seg_bytes, Pi, byte_start, tsum64, st);
     ctx->launches += 5;
