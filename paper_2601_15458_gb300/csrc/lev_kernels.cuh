@@ -243,6 +243,15 @@ __device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c) 
     return d;
 }
 
+// A warp whose index in the grid is past the bucket's task count leaves
+// before claiming anything: a bucket with few tasks then keeps only its
+// lowest blocks (their warps claim all its tasks from the counter), and the
+// others free their SM slots at once, without a round of atomics on the
+// bucket's counter, for the buckets running beside it on other streams.
+__device__ __forceinline__ bool warp_has_no_task(int ntasks) {
+    return (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) >= ntasks;
+}
+
 __device__ __forceinline__ int next_task(int32_t *counter, int lane) {
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);
@@ -287,6 +296,7 @@ __global__ void __launch_bounds__(128) lev_lane_kernel(LevArgs a) {
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
 
+    if (warp_has_no_task(ntasks)) return;
     for (int task = next_task(counter, lane); task < ntasks; task = next_task(counter, lane)) {
         int q = -1, m = 0, cbeg = 0, cnt = 0, total = 0;
         const uint32_t *peq = sPeq;
@@ -450,6 +460,7 @@ __global__ void __launch_bounds__(128) lev_warp_kernel(LevArgs a) {
     const int2 *tasks = a.tasks + a.boff[a.bucket];
     int32_t *counter = a.bcounter + a.bucket;
 
+    if (warp_has_no_task(ntasks)) return;
     for (int task = next_task(counter, lane); task < ntasks; task = next_task(counter, lane)) {
         const int q = tasks[task].x;
         const int64_t qpos = a.offs[q];
