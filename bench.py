@@ -36,7 +36,7 @@ ALU_OPS_PER_WORD = 9
 # workload, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # (profiles/launches_tree_dna_allpairs_2000x1500.md); valid only while the
 # kernel source is the one that was measured.
-TRAFFIC = dict(kernel_sha256_16="e4005b47723512ec", bytes_per_launch=20.1e6)
+TRAFFIC = dict(kernel_sha256_16="8ee36c74ea96d418", bytes_per_launch=20.1e6)
 WORKLOAD = "tree_dna_allpairs_2000x1500"
 
 
