@@ -264,6 +264,13 @@ def band_bench(ctx, args, stream):
     mism_full = dict(learned=int((d_band != d_full).sum().item()), uncalibrated=int((d_raw != d_full).sum().item()),
                      l1_bound=int((d_l1 != d_full).sum().item()))
     band_share = float((k_used.cpu().numpy() < np.maximum(lens[0::2], lens[1::2])).mean())
+    # cells of the band that certified each distance (about min(m, 2k + 1)
+    # rows per column; m x n for pairs the full DP computed; the cells of
+    # failed narrower attempts are not counted)
+    ku = k_used.cpu().numpy().astype(np.int64)
+    m_rows, n_cols = lens[0::2].astype(np.int64), lens[1::2].astype(np.int64)
+    full_pairs = ku >= np.maximum(m_rows, n_cols)
+    cells_band = int(np.where(full_pairs, m_rows * n_cols, np.minimum(m_rows, 2 * ku + 1) * n_cols).sum())
 
     def timed(fn, reps):
         fn()
@@ -307,6 +314,8 @@ def band_bench(ctx, args, stream):
                                  k_mean_over_f_uncalibrated=float(
                                      (k_raw.double() / d_full.double().clamp(min=1)).mean().item())),
                 gcups_full=cells / (t_full / 1e3) / 1e9, gcups_equiv_learned=cells / (t_band / 1e3) / 1e9,
+                cells_computed_learned=cells_band, computed_share_learned=cells_band / cells,
+                gcups_computed_learned=cells_band / (t_band / 1e3) / 1e9,
                 ms_learned=t_band, ms_full=t_full, mismatches=mism,
                 parity=dict(oracle_pairs=int(len(samp)), oracle_seconds=t_oracle,
                             mismatches_vs_oracle=mism_oracle, mismatches_vs_full_dp_all_pairs=mism_full),
