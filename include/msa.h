@@ -408,6 +408,10 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
  * are HOST int32 arrays with room for 2n - 1 nodes, in breadth-first order
  * (node 0 = root; -1 = none).  *n_nodes (host) receives 2n - 1.
  * Synchronous: the host reads the left-child sizes once per tree level.
+ * A cluster of at most 256 members keeps the distances of its medoid batch
+ * (all its pairs) as a matrix in the workspace (up to 256 n_seqs int32 in
+ * all, at most a quarter of the free workspace); it and its sub-clusters
+ * read every later distance from it instead of computing it again.
  */
 msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order, int32_t *lo, int32_t *hi,
                               int32_t *center, int32_t *left, int32_t *right, int32_t *parent,

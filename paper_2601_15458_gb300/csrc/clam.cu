@@ -13,7 +13,10 @@
 //     cluster's contiguous range in `order`, so every cluster stays sorted by
 //     index and occupies one range.
 // The host keeps the node table and reads back only the left sizes once per
-// level; all distances, reductions and the partition run on the device.
+// level; all distances, reductions and the partition run on the device.  A
+// cluster of at most 256 members keeps its medoid batch as a distance
+// matrix, from which it and all its descendants read every later distance
+// (the same values the DP would give, so the tree is unchanged).
 //
 // Merge, height by height (all merges of one height at once): every
 // sequence s keeps pos_s[k], the column of its k-th residue in the MSA of the
@@ -45,49 +48,93 @@ __device__ __forceinline__ int cand_pos(int lo, int size, int s, int j) {
     return size <= kMedoidSample ? lo + j : lo + (int)(((int64_t)j * size) / kMedoidSample);
 }
 
-// Medoid pairs of node k: candidate i with i + d (mod s) for d = 1..h,
-// h = (s - 1) / 2, and for even s also i + s/2 for i < s/2.
+// Distance matrices of small clusters.  A cluster of at most 256 members
+// computes all its unordered pairs for its medoid; they are kept as a
+// |C| x |C| matrix in a pool, and every distance the cluster and all its
+// descendants need later (c, l and r against the members, the medoids of
+// the sub-clusters) is read from it instead of being computed again.
+// base[k] < 0: cluster k has no matrix.
+struct MatView {
+    const int64_t *base;    // [A] offset of the cluster's matrix in the pool
+    const int32_t *stride;  // [A] its row length (the size of the cluster that made it)
+    const int32_t *local;   // [N] a sequence's row in its matrix
+    const int32_t *pool;
+    __device__ __forceinline__ bool has(int k) const { return base[k] >= 0; }
+    __device__ __forceinline__ int32_t d(int k, int x, int y) const {
+        return pool[base[k] + (int64_t)local[x] * stride[k] + local[y]];
+    }
+};
+
+// Pair t of a medoid batch over s candidates: candidate i with i + d (mod s)
+// for d = 1..h, h = (s - 1) / 2, and for even s also i + s/2 for i < s/2.
+__device__ __forceinline__ void medoid_pair(int64_t t, int s, int &i, int &j) {
+    const int h = (s - 1) / 2;
+    if (t < (int64_t)s * h) {
+        i = (int)(t / h);
+        j = (i + (int)(t % h) + 1) % s;
+    } else {
+        i = (int)(t - (int64_t)s * h);
+        j = i + s / 2;
+    }
+}
+
+// Medoid pairs of the nodes whose medoid is computed (poff[k + 1] > poff[k]).
 __global__ void medoid_pairs_kernel(const int32_t *__restrict__ order, const int32_t *__restrict__ nlo,
                                     const int32_t *__restrict__ nsize, const int64_t *__restrict__ poff, int A,
                                     int32_t *__restrict__ pairs) {
     for (int k = blockIdx.x; k < A; k += gridDim.x) {
         const int lo = nlo[k], size = nsize[k];
         const int s = min(size, kMedoidSample);
-        const int h = (s - 1) / 2;
-        const int64_t base = poff[k];
-        const int64_t cnt = (int64_t)s * (s - 1) / 2;
+        const int64_t base = poff[k], cnt = poff[k + 1] - poff[k];
         for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
             int i, j;
-            if (t < (int64_t)s * h) {
-                i = (int)(t / h);
-                j = (i + (int)(t % h) + 1) % s;
-            } else {
-                i = (int)(t - (int64_t)s * h);
-                j = i + s / 2;
-            }
+            medoid_pair(t, s, i, j);
             pairs[2 * (base + t)] = order[cand_pos(lo, size, s, i)];
             pairs[2 * (base + t) + 1] = order[cand_pos(lo, size, s, j)];
         }
     }
 }
 
-__global__ void medoid_sums_kernel(const int32_t *__restrict__ nsize, const int64_t *__restrict__ poff,
-                                   const int64_t *__restrict__ soff, int A, const int32_t *__restrict__ d,
+// The matrices of the nodes that make one at this level (fresh[k]): their
+// medoid distances in both orders, zeros on the diagonal, and each member's
+// row.
+__global__ void build_matrix_kernel(const int32_t *__restrict__ order, const int32_t *__restrict__ nlo,
+                                    const int32_t *__restrict__ nsize, const int64_t *__restrict__ poff, int A,
+                                    const int32_t *__restrict__ fresh, const int64_t *__restrict__ mbase,
+                                    const int32_t *__restrict__ d, int32_t *__restrict__ pool,
+                                    int32_t *__restrict__ local) {
+    for (int k = blockIdx.x; k < A; k += gridDim.x) {
+        if (!fresh[k]) continue;
+        const int lo = nlo[k], s = nsize[k];
+        const int64_t base = mbase[k], cnt = poff[k + 1] - poff[k];
+        for (int i = threadIdx.x; i < s; i += blockDim.x) {
+            local[order[lo + i]] = i;
+            pool[base + (int64_t)i * s + i] = 0;
+        }
+        for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            int i, j;
+            medoid_pair(t, s, i, j);
+            const int32_t v = d[poff[k] + t];
+            pool[base + (int64_t)i * s + j] = v;
+            pool[base + (int64_t)j * s + i] = v;
+        }
+    }
+}
+
+__global__ void medoid_sums_kernel(const int32_t *__restrict__ order, const int32_t *__restrict__ nlo,
+                                   const int32_t *__restrict__ nsize, const int64_t *__restrict__ poff,
+                                   const int64_t *__restrict__ soff, int A, const int32_t *__restrict__ d, MatView M,
                                    unsigned long long *__restrict__ sums) {
     for (int k = blockIdx.x; k < A; k += gridDim.x) {
+        const int lo = nlo[k];
         const int s = min(nsize[k], kMedoidSample);
-        const int h = (s - 1) / 2;
+        const bool mat = M.has(k);                 // then the candidates are all s members
         const int64_t cnt = (int64_t)s * (s - 1) / 2;
         for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
             int i, j;
-            if (t < (int64_t)s * h) {
-                i = (int)(t / h);
-                j = (i + (int)(t % h) + 1) % s;
-            } else {
-                i = (int)(t - (int64_t)s * h);
-                j = i + s / 2;
-            }
-            const unsigned long long v = (unsigned long long)d[poff[k] + t];
+            medoid_pair(t, s, i, j);
+            const unsigned long long v =
+                (unsigned long long)(mat ? M.d(k, order[lo + i], order[lo + j]) : d[poff[k] + t]);
             atomicAdd(sums + soff[k] + i, v);
             atomicAdd(sums + soff[k] + j, v);
         }
@@ -124,31 +171,37 @@ __global__ void medoid_argmin_kernel(const int32_t *__restrict__ order, const in
     }
 }
 
-// one-to-many pairs (q_k, order[i]) for i in node k's range
+// one-to-many pairs (q_k, order[i]) for i in node k's range, for the nodes
+// whose distances are computed (moff[k + 1] > moff[k])
 __global__ void one_to_many_kernel(const int32_t *__restrict__ order, const int32_t *__restrict__ nlo,
-                                   const int32_t *__restrict__ nsize, const int64_t *__restrict__ moff, int A,
-                                   const int32_t *__restrict__ q, int32_t *__restrict__ pairs) {
+                                   const int64_t *__restrict__ moff, int A, const int32_t *__restrict__ q,
+                                   int32_t *__restrict__ pairs) {
     for (int k = blockIdx.x; k < A; k += gridDim.x) {
-        const int lo = nlo[k], size = nsize[k];
+        const int lo = nlo[k];
+        const int cnt = (int)(moff[k + 1] - moff[k]);
         const int qk = q[k];
-        for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             pairs[2 * (moff[k] + i)] = qk;
             pairs[2 * (moff[k] + i) + 1] = order[lo + i];
         }
     }
 }
 
-// argmax over (distance, -index) per node
+// argmax over (distance from q_k, -index) per node
 __global__ void argmax_kernel(const int32_t *__restrict__ order, const int32_t *__restrict__ nlo,
                               const int32_t *__restrict__ nsize, const int64_t *__restrict__ moff, int A,
-                              const int32_t *__restrict__ d, int32_t *__restrict__ out) {
+                              const int32_t *__restrict__ d, const int32_t *__restrict__ q, MatView M,
+                              int32_t *__restrict__ out) {
     __shared__ unsigned long long best[32];
     for (int k = blockIdx.x; k < A; k += gridDim.x) {
         const int lo = nlo[k], size = nsize[k];
+        const bool mat = M.has(k);
+        const int qk = q[k];
         unsigned long long b = 0;
         for (int i = threadIdx.x; i < size; i += blockDim.x) {
-            const unsigned long long key =
-                ((unsigned long long)(unsigned)d[moff[k] + i] << 32) | (0xffffffffu - (unsigned)order[lo + i]);
+            const int x = order[lo + i];
+            const unsigned dist = (unsigned)(mat ? M.d(k, qk, x) : d[moff[k] + i]);
+            const unsigned long long key = ((unsigned long long)dist << 32) | (0xffffffffu - (unsigned)x);
             b = key > b ? key : b;
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -172,14 +225,25 @@ __global__ void __launch_bounds__(1024) split_kernel(const int32_t *__restrict__
                                                      const int32_t *__restrict__ nlo, const int32_t *__restrict__ nsize,
                                                      const int64_t *__restrict__ moff, int A,
                                                      const int32_t *__restrict__ dl, const int32_t *__restrict__ dr,
-                                                     int32_t *__restrict__ nleft) {
+                                                     const int32_t *__restrict__ ql, const int32_t *__restrict__ qr,
+                                                     MatView M, int32_t *__restrict__ nleft) {
     __shared__ int32_t wsum[32];
     __shared__ int32_t base_l;
     for (int k = blockIdx.x; k < A; k += gridDim.x) {
         const int lo = nlo[k], size = nsize[k];
+        const bool mat = M.has(k);
+        const int lk = ql[k], rk = qr[k];
+        // x goes left when f(l, x) <= f(r, x)
+        auto goes_left = [&](int i) {
+            if (mat) {
+                const int x = order[lo + i];
+                return M.d(k, lk, x) <= M.d(k, rk, x);
+            }
+            return dl[moff[k] + i] <= dr[moff[k] + i];
+        };
         // pass 1: count lefts
         int c = 0;
-        for (int i = threadIdx.x; i < size; i += blockDim.x) c += dl[moff[k] + i] <= dr[moff[k] + i];
+        for (int i = threadIdx.x; i < size; i += blockDim.x) c += goes_left(i);
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
         __syncthreads();
@@ -195,7 +259,7 @@ __global__ void __launch_bounds__(1024) split_kernel(const int32_t *__restrict__
         int run_l = 0, run_r = 0;
         for (int c0 = 0; c0 < size; c0 += blockDim.x) {
             const int i = c0 + threadIdx.x;
-            const int f = i < size ? (dl[moff[k] + i] <= dr[moff[k] + i]) : 0;
+            const int f = i < size ? (int)goes_left(i) : 0;
             const int valid = i < size;
             // block exclusive scan of f
             const unsigned mask = __ballot_sync(0xffffffffu, f);
@@ -355,7 +419,19 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
     std::vector<int32_t> active = N > 1 ? std::vector<int32_t>{0} : std::vector<int32_t>{};
     Arena base{ctx->ws, ctx->ws_bytes};
     int32_t *order_tmp = base.take<int32_t>(N);
-    if (!order_tmp) return set_error(ctx, MSA_ENOMEM, "msa_clam_partition: workspace");
+    int32_t *mlocal = base.take<int32_t>(N);
+    if (!mlocal) return set_error(ctx, MSA_ENOMEM, "msa_clam_partition: workspace");
+    // the matrix pool: at most 256 N entries are ever needed (the clusters
+    // that make matrices are disjoint and have at most 256 members); a
+    // quarter of the free workspace at most, and a cluster that does not fit
+    // computes its distances as a large one does
+    const int64_t pool_cap = std::min<int64_t>((int64_t)kMedoidSample * N, (base.cap - base.used) / 16);
+    int32_t *pool = base.take<int32_t>(std::max<int64_t>(pool_cap, 1));
+    if (!pool) return set_error(ctx, MSA_ENOMEM, "msa_clam_partition: workspace");
+    int64_t pool_used = 0;
+    // per node: its matrix (offset in the pool, -1: none) and row length
+    std::vector<int64_t> node_mbase(2 * (size_t)N, -1);
+    std::vector<int32_t> node_mstride(2 * (size_t)N, 0);
     // order_tmp mirrors order: each level's split rewrites the active ranges
     // in order_tmp and one copy of the whole array brings them back (ranges
     // that are no longer active are equal in both)
@@ -365,17 +441,31 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
     }
     while (!active.empty()) {
         const int A = (int)active.size();
-        std::vector<int32_t> hlo(A), hsz(A);
-        std::vector<int64_t> poff(A + 1), soff(A + 1), moff(A + 1);
+        std::vector<int32_t> hlo(A), hsz(A), hfresh(A, 0), hstride(A, 0);
+        std::vector<int64_t> poff(A + 1), soff(A + 1), moff(A + 1), hmbase(A, -1);
         poff[0] = soff[0] = moff[0] = 0;
         for (int k = 0; k < A; ++k) {
             const int nd = active[k];
             hlo[k] = lo[nd];
             hsz[k] = hi[nd] - lo[nd];
             const int64_t sk = std::min(hsz[k], kMedoidSample);
-            poff[k + 1] = poff[k] + sk * (sk - 1) / 2;
+            // a cluster of at most 256 members without a matrix makes one
+            // from its medoid batch, if the pool has room
+            if (node_mbase[nd] < 0 && hsz[k] <= kMedoidSample &&
+                pool_used + (int64_t)hsz[k] * hsz[k] <= pool_cap) {
+                node_mbase[nd] = pool_used;
+                node_mstride[nd] = hsz[k];
+                pool_used += (int64_t)hsz[k] * hsz[k];
+                hfresh[k] = 1;
+            }
+            hmbase[k] = node_mbase[nd];
+            hstride[k] = node_mstride[nd];
+            const bool mat = hmbase[k] >= 0;
+            // computed: the medoid batch unless an ancestor's matrix holds it,
+            // the one-to-many batches unless the cluster has a matrix
+            poff[k + 1] = poff[k] + (mat && !hfresh[k] ? 0 : sk * (sk - 1) / 2);
             soff[k + 1] = soff[k] + sk;
-            moff[k + 1] = moff[k] + hsz[k];
+            moff[k + 1] = moff[k] + (mat ? 0 : hsz[k]);
         }
         const int64_t PM = poff[A], PC = moff[A];
         Arena ar = base;
@@ -383,6 +473,8 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
         int64_t *d_poff = ar.take<int64_t>(A + 1), *d_soff = ar.take<int64_t>(A + 1), *d_moff = ar.take<int64_t>(A + 1);
         int32_t *d_c = ar.take<int32_t>(A), *d_l = ar.take<int32_t>(A), *d_r = ar.take<int32_t>(A),
                 *d_nl = ar.take<int32_t>(A);
+        int64_t *d_mbase = ar.take<int64_t>(A);
+        int32_t *d_stride = ar.take<int32_t>(A), *d_fresh = ar.take<int32_t>(A);
         unsigned long long *sums = ar.take<unsigned long long>(soff[A]);
         int32_t *pairs = ar.take<int32_t>(2 * std::max(PM, PC));
         int32_t *dm = ar.take<int32_t>(PM), *dc = ar.take<int32_t>(PC), *dl = ar.take<int32_t>(PC),
@@ -406,25 +498,29 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
             return lev_banded_run(ctx, s, pr, np, k0, out, ku, st, tmp);
         };
         if ((rc = h2d(ctx, d_lo, hlo, st)) || (rc = h2d(ctx, d_sz, hsz, st)) || (rc = h2d(ctx, d_poff, poff, st)) ||
-            (rc = h2d(ctx, d_soff, soff, st)) || (rc = h2d(ctx, d_moff, moff, st)))
+            (rc = h2d(ctx, d_soff, soff, st)) || (rc = h2d(ctx, d_moff, moff, st)) ||
+            (rc = h2d(ctx, d_mbase, hmbase, st)) || (rc = h2d(ctx, d_stride, hstride, st)) ||
+            (rc = h2d(ctx, d_fresh, hfresh, st)))
             return rc;
+        const MatView M{d_mbase, d_stride, mlocal, pool};
         cudaError_t e = cudaMemsetAsync(sums, 0, soff[A] * sizeof(unsigned long long), st);
         if (e != cudaSuccess) return cuda_check(ctx, e, "partition memset");
         const int g = std::min(A, 65535);
         medoid_pairs_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_poff, A, pairs);
-        if ((rc = dist(pairs, PM, dm))) return rc;
-        medoid_sums_kernel<<<g, 256, 0, st>>>(d_sz, d_poff, d_soff, A, dm, sums);
+        if (PM > 0 && (rc = dist(pairs, PM, dm))) return rc;
+        build_matrix_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_poff, A, d_fresh, d_mbase, dm, pool, mlocal);
+        medoid_sums_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_poff, d_soff, A, dm, M, sums);
         medoid_argmin_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_soff, A, sums, d_c);
-        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_c, pairs);
-        if ((rc = dist(pairs, PC, dc))) return rc;
-        argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dc, d_l);
-        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_l, pairs);
-        if ((rc = dist(pairs, PC, dl))) return rc;
-        argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dl, d_r);
-        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, d_r, pairs);
-        if ((rc = dist(pairs, PC, dr))) return rc;
-        split_kernel<<<g, 1024, 0, st>>>(order, order_tmp, d_lo, d_sz, d_moff, A, dl, dr, d_nl);
-        ctx->launches += 9;
+        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_moff, A, d_c, pairs);
+        if (PC > 0 && (rc = dist(pairs, PC, dc))) return rc;
+        argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dc, d_c, M, d_l);
+        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_moff, A, d_l, pairs);
+        if (PC > 0 && (rc = dist(pairs, PC, dl))) return rc;
+        argmax_kernel<<<g, 256, 0, st>>>(order, d_lo, d_sz, d_moff, A, dl, d_l, M, d_r);
+        one_to_many_kernel<<<g, 256, 0, st>>>(order, d_lo, d_moff, A, d_r, pairs);
+        if (PC > 0 && (rc = dist(pairs, PC, dr))) return rc;
+        split_kernel<<<g, 1024, 0, st>>>(order, order_tmp, d_lo, d_sz, d_moff, A, dl, dr, d_l, d_r, M, d_nl);
+        ctx->launches += 10;
         // the partitioned ranges back, in one copy (a copy per cluster cost
         // thousands of calls at the deep levels)
         e = cudaMemcpyAsync(order, order_tmp, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
@@ -451,6 +547,8 @@ static msa_status clam_partition_run(msa_ctx *ctx, const msa_seqset *s, const Pa
             lo[b] = hi[a];
             hi[b] = hi[nd];
             for (int c : {a, b}) {
+                node_mbase[c] = node_mbase[nd];      // a sub-cluster reads its parent's matrix
+                node_mstride[c] = node_mstride[nd];
                 parent[c] = nd;
                 left[c] = right[c] = -1;
                 center[c] = -1;
