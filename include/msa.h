@@ -417,11 +417,12 @@ msa_status msa_clam_partition(msa_ctx *ctx, const msa_seqset *s, int32_t *order,
                               int32_t *center, int32_t *left, int32_t *right, int32_t *parent,
                               int32_t *n_nodes, void *stream);
 /*
- * The same tree as msa_clam_partition, with every distance batch of Alg. 1
- * (medoid pairs, c, l and r against the cluster) started from the band the
- * network proposes (msa_band_predict with gamma, margin) and computed by the
- * certified banded DP of msa_lev_banded_batch, so every distance, and the
- * tree, equals the full-DP result.  state: network state (msa_mlp_state_bytes);
+ * The same tree as msa_clam_partition, with the medoid batches of Alg. 1
+ * started from the band the network proposes (msa_band_predict with gamma,
+ * margin) and computed by the certified banded DP of msa_lev_banded_batch,
+ * so every distance, and the tree, equals the full-DP result.  The c, l and
+ * r batches run on the full DP: their points lie far from most of the
+ * cluster, so their bands would cover most of each matrix.  state: network state (msa_mlp_state_bytes);
  * prof: msa_kmer_profile of s.  DNA sets only (MSA_EUNSUPPORTED otherwise).
  * The learned band is this library's addition, not the paper's.
  */
