@@ -101,6 +101,41 @@ def test_larger_tree_sampled_nodes(ctx):
     assert not np.any(np.all(rows == ord("-"), axis=0))
 
 
+def test_small_cluster_matrices_any_pool_size(ctx):
+    """Clusters of at most 256 members read their distances from matrices
+    kept in the workspace, as many as the pool (a quarter of the free
+    workspace) holds; the others compute them.  Workspaces from one that
+    holds few matrices to one that holds all give the same tree, and that
+    tree matches the oracle's step on sampled clusters."""
+    ds = synth.gg16s_dna(seed=7, n=700)
+    seqs = ds.seqs()
+    trees = []
+    for ws in (2 << 20, 5 << 19, 3 << 20, 1 << 30):
+        c = api.Context(0, workspace_bytes=ws)
+        try:
+            sq = api.upload_and_pack(c, ds)
+            tree = api.clam_partition(c, sq)
+            c.check()
+            trees.append(_gpu_nodes(tree))
+        except api.MsaError:
+            pass                              # a level needs more than this workspace
+        finally:
+            c.close()
+    assert len(trees) >= 2
+    for t in trees[1:]:
+        _check_same_tree(t, trees[0])
+    nodes = trees[0]
+    rng = np.random.default_rng(1)
+    internal = [k for k, nd in enumerate(nodes) if nd["left"] >= 0]
+    for k in [internal[0]] + list(rng.choice([k for k in internal if 2 <= len(nodes[k]["members"]) <= 64], 6,
+                                            replace=False)):
+        nd = nodes[k]
+        mem = nd["members"]
+        step = oracle.partition_levels([seqs[x] for x in mem], max_levels=1)
+        assert nd["center"] == mem[step[0]["center"]]
+        assert nodes[nd["left"]]["members"] == [mem[i] for i in step[1]["members"]]
+
+
 def test_protein_families_tree_and_merges_full_size(ctx):
     """The 10,000-protein workload (100 families, 10-40% mutation): Alg. 1
     over all members and all 9,999 guide-tree merges, against the oracle
