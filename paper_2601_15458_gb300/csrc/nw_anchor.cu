@@ -20,9 +20,9 @@
 //
 // Device steps: anchor_chain_kernel (one block per pair: a hash table of
 // a's k-mers with occurrence counts in both sequences, the anchors marked by
-// their i, the chain and the blocks by one thread), scans of the segment
-// counts and bytes, one read-back of the two totals and the longest segment,
-// seg_build_kernel (the segments' bytes into an arena of their own, one warp
+// their i, the chain and the blocks by one warp in 32-anchor steps), scans
+// of the segment counts and bytes, one read-back of the two totals and the
+// longest segment, seg_build_kernel (the segments' bytes into an arena of their own, one warp
 // per segment), nw_run on the segments, and assemble_kernel (a block scan of
 // the segments' script lengths places them; the costs are added up).
 #include <cuda_runtime.h>
@@ -98,7 +98,7 @@ __device__ __forceinline__ bool same_kmer(const uint8_t *x, const uint8_t *y, in
 
 __global__ void __launch_bounds__(kAnchorThreads) anchor_chain_kernel(AnchorArgs a) {
     // chunks of the per-position arrays staged by the whole block, so the
-    // serial chain passes of thread 0 read shared memory, not global
+    // sequential chain passes of warp 0 read shared memory, not global
     constexpr int kChunk = 2048;
     __shared__ int32_t s_a[kChunk], s_b[kChunk];
     __shared__ int32_t s_pair, s_len, s_last, s_want;
