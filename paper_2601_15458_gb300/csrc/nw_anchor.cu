@@ -22,9 +22,10 @@
 // a's k-mers with occurrence counts in both sequences, the anchors marked by
 // their i, the chain and the blocks by one warp in 32-anchor steps), scans
 // of the segment counts and bytes, one read-back of the two totals and the
-// longest segment, seg_build_kernel (the segments' bytes into an arena of their own, one warp
-// per segment), nw_run on the segments, and assemble_kernel (a block scan of
-// the segments' script lengths places them; the costs are added up).
+// longest segment, seg_build_kernel (the segments' bytes into an arena of
+// their own, one warp per segment), nw_run on the segments, and
+// assemble_kernel (a block scan of the segments' script lengths places
+// them; the costs are added up).
 #include <cuda_runtime.h>
 
 #include <algorithm>
