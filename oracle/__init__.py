@@ -570,21 +570,28 @@ def anchor_blocks(chain, k):
     return blocks
 
 
-def nw_anchored(a, b, k=12, match=0, mismatch=1, gap=1):
+def nw_anchored(a, b, k=12, match=0, mismatch=1, gap=1, gap_open=None, sub=None):
     """Needleman-Wunsch split at k-mer anchors: the blocks of
     :func:`anchor_blocks` (over :func:`anchor_chain` of
     :func:`kmer_anchors`) are aligned as runs of matches, the segments
-    between them (and before the first, after the last) by :func:`nw`.
-    Returns ``(score, ops)``; the score is an upper bound of the optimal NW
-    cost, equal to it whenever an optimal alignment passes through every
-    block.  Without anchors this is :func:`nw`."""
+    between them (and before the first, after the last) by :func:`nw`, or,
+    with ``gap_open``, by :func:`nw_affine` with gap extension ``gap`` (and
+    ``sub``, a 256 x 256 cost table over byte values, when given).  A block
+    residue costs ``match``, or ``sub[x, x]`` with a table.  Returns
+    ``(score, ops)``; the score is an upper bound of the optimal cost, equal
+    to it whenever an optimal alignment passes through every block.  Without
+    anchors this is the plain alignment."""
     a, b = bytes(a), bytes(b)
     blocks = anchor_blocks(anchor_chain(kmer_anchors(a, b, k)), k)
     score, ops = 0, bytearray()
     ia = ib = 0
     for sa, sb, ln in blocks + [(len(a), len(b), 0)]:
-        sc, op = nw(a[ia:sa], b[ib:sb], match, mismatch, gap)
-        score += sc + ln * match
+        if gap_open is None:
+            sc, op = nw(a[ia:sa], b[ib:sb], match, mismatch, gap)
+        else:
+            sc, op = nw_affine(a[ia:sa], b[ib:sb], match, mismatch, gap_open, gap, sub)
+        block = a[sa:sa + ln]
+        score += sc + (sum(int(sub[x, x]) for x in block) if sub is not None else ln * match)
         ops += op + b"M" * ln
         ia, ib = sa + ln, sb + ln
     return score, bytes(ops)

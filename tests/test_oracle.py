@@ -704,3 +704,39 @@ def test_nw_anchored_hand_worked_split():
     assert oracle.nw(b"AC", b"A") == (1, b"MD")
     assert oracle.nw(b"T", b"AT") == (1, b"IM")
     assert oracle.nw_anchored(a, b, k=6) == (2, b"MD" + b"M" * 9 + b"IM")
+
+
+def test_nw_anchored_affine_hand_worked_and_properties():
+    """Affine gaps in the anchored split (segments by nw_affine): the hand
+    example above with open 2, extension 1 costs 3 + 0 + 3 (a deletion run
+    of one, nine matches, an insertion run of one: each run pays open +
+    extension); random related pairs, flat and with a table whose entries
+    differ per pair of bytes: the script rescored under affine gaps gives the
+    reported cost, which is never below the affine optimum; identical
+    sequences cost the table's diagonal; without anchors the split is the
+    plain affine alignment."""
+    a, b = b"ACAGGGCCCTTT", b"AAGGGCCCTTAT"
+    assert oracle.nw_anchored(a, b, k=6, gap=1, gap_open=2) == (6, b"MD" + b"M" * 9 + b"IM")
+    rng = np.random.default_rng(71)
+    T = rng.integers(-3, 6, size=(256, 256)).astype(np.int32)
+    T = (T + T.T) // 2
+    for x in b"ACGT":
+        T[x, x] = -int(rng.integers(1, 4))
+    for t in range(16):
+        L = int(rng.integers(60, 400))
+        a = _rand_dna(rng, L)
+        b = bytearray(a)
+        for _ in range(int(rng.integers(0, L // 12 + 1))):
+            p = int(rng.integers(0, len(b)))
+            b[p] = b"ACGT"[int(rng.integers(0, 4))]
+        if len(b) > 30:
+            del b[10:12 + t % 3]
+        b = bytes(b)
+        sub = T if t % 2 else None
+        score, ops = oracle.nw_anchored(a, b, k=8, match=0, mismatch=2, gap=1, gap_open=3, sub=sub)
+        assert oracle.rescore_affine(a, b, ops, 0, 2, 3, 1, sub) == score
+        assert score >= oracle.nw_affine(a, b, 0, 2, 3, 1, sub)[0]
+    a = _rand_dna(rng, 200)
+    assert oracle.nw_anchored(a, a, k=8, gap=1, gap_open=3, sub=T) == (int(sum(T[x, x] for x in a)), b"M" * 200)
+    x, y = b"AC" * 40, b"GT" * 30
+    assert oracle.nw_anchored(x, y, k=4, gap=1, gap_open=3) == oracle.nw_affine(x, y, 0, 1, 3, 1)
