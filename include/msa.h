@@ -389,6 +389,25 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
                                        int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t k,
                                        int32_t match, int32_t mismatch, int32_t gap, int32_t *score_out,
                                        uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out, void *stream);
+/* The same split under affine gaps (section "Implementation"): segments by
+ * msa_nw_align_batch_affine (a gap run of L costs gap_open + L gap_ext;
+ * gap_open >= 0), a block residue costs match.  The _sub variant takes the
+ * substitution table of msa_nw_align_batch_affine_sub (device int32
+ * [nsym][nsym], nsym <= 32; a code >= nsym is reported as MSA_EDATA by
+ * msa_ctx_check): segments by that call, a block residue x costs
+ * sub[x][x].  Both are defined by this library (the paper fixes no anchored
+ * method); arguments and outputs as msa_nw_align_batch_anchored. */
+msa_status msa_nw_align_batch_anchored_affine(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs,
+                                              int32_t n_seqs, int64_t total, int32_t max_len, const int32_t *pairs,
+                                              int64_t P, int32_t k, int32_t match, int32_t mismatch, int32_t gap_open,
+                                              int32_t gap_ext, int32_t *score_out, uint8_t *ops_out,
+                                              const int64_t *ops_off, int32_t *ops_len_out, void *stream);
+msa_status msa_nw_align_batch_anchored_affine_sub(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs,
+                                                  int32_t n_seqs, int64_t total, int32_t max_len, const int32_t *pairs,
+                                                  int64_t P, int32_t k, const int32_t *sub, int32_t nsym,
+                                                  int32_t gap_open, int32_t gap_ext, int32_t *score_out,
+                                                  uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                                                  void *stream);
 
 /* ---- A11: guide tree by Alg. 1 (Partition) ------------------------------ */
 /*

@@ -93,6 +93,12 @@ SIGNATURES = {
     "msa_nw_align_batch_anchored": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p,
                                               c_int64, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                               c_void_p, c_void_p, c_void_p]),
+    "msa_nw_align_batch_anchored_affine": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32,
+                                                     c_void_p, c_int64, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "msa_nw_align_batch_anchored_affine_sub": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32,
+                                                         c_void_p, c_int64, c_int32, c_void_p, c_int32, c_int32,
+                                                         c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "msa_merge_tree_affine_sub": (c_int32, [c_void_p, ctypes.POINTER(SeqSetC), c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_int32,
                                             c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),

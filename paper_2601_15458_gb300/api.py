@@ -258,11 +258,15 @@ def nw_align_batch(ctx: Context, seqs, pairs, match=0, mismatch=1, gap=1, ops_of
 
 
 def nw_align_batch_anchored(ctx: Context, seqs, pairs, k=12, match=0, mismatch=1, gap=1,
-                            ops_off: torch.Tensor | None = None, stream=None):
+                            ops_off: torch.Tensor | None = None, stream=None, gap_open: int | None = None,
+                            sub: torch.Tensor | None = None):
     """NW split at unique k-mer anchors (msa_nw_align_batch_anchored):
     runs of matches along the chained anchors, NW on the segments between
-    them.  Returns ``(score[P] int32, ops uint8, ops_off[P+1] int64,
-    ops_len[P] int32)`` like :func:`nw_align_batch`."""
+    them.  With ``gap_open`` the segments take affine gaps (``gap`` is the
+    extension; msa_nw_align_batch_anchored_affine), with ``sub`` as well a
+    substitution table (msa_nw_align_batch_anchored_affine_sub).  Returns
+    ``(score[P] int32, ops uint8, ops_off[P+1] int64, ops_len[P] int32)``
+    like :func:`nw_align_batch`."""
     if isinstance(seqs, DeviceSeqs):
         seqs = ByteSeqs.from_device_seqs(seqs)
     pairs = _pairs_tensor(pairs)
@@ -277,9 +281,21 @@ def nw_align_batch_anchored(ctx: Context, seqs, pairs, k=12, match=0, mismatch=1
     ops = torch.empty(max(cap_total, 1), dtype=torch.uint8, device=dev)
     score = torch.empty(P, dtype=torch.int32, device=dev)
     ops_len = torch.empty(P, dtype=torch.int32, device=dev)
-    ctx.raise_if(_lib.lib().msa_nw_align_batch_anchored(
-        ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, k, match,
-        mismatch, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    L = _lib.lib()
+    if gap_open is None:
+        ctx.raise_if(L.msa_nw_align_batch_anchored(
+            ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, k,
+            match, mismatch, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    elif sub is None:
+        ctx.raise_if(L.msa_nw_align_batch_anchored_affine(
+            ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, k,
+            match, mismatch, gap_open, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len), _stream(stream)))
+    else:
+        sub = sub.to(device=dev, dtype=torch.int32).contiguous()
+        ctx.raise_if(L.msa_nw_align_batch_anchored_affine_sub(
+            ctx.handle, _ptr(seqs.codes), _ptr(seqs.offs), seqs.n, seqs.total, seqs.max_len, _ptr(pairs), P, k,
+            _ptr(sub), int(sub.shape[0]), gap_open, gap, _ptr(score), _ptr(ops), _ptr(ops_off), _ptr(ops_len),
+            _stream(stream)))
     return score, ops, ops_off, ops_len
 
 

@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(kAnchorThreads) assemble_kernel(
     int32_t P, const int4 *__restrict__ blocks, int32_t bcap, const int32_t *__restrict__ nblocks,
     const int32_t *__restrict__ seg_start, const int32_t *__restrict__ seg_score, const uint8_t *__restrict__ seg_ops,
     const int64_t *__restrict__ seg_ops_off, const int32_t *__restrict__ seg_ops_len, int32_t match,
-    int32_t *__restrict__ score_out, uint8_t *__restrict__ ops_out, const int64_t *__restrict__ ops_off,
-    int32_t *__restrict__ ops_len_out) {
+    const uint8_t *__restrict__ codes, const int64_t *__restrict__ offs, const int32_t *__restrict__ pairs,
+    const int32_t *__restrict__ sub, int32_t nsym, int32_t *err, int32_t *__restrict__ score_out,
+    uint8_t *__restrict__ ops_out, const int64_t *__restrict__ ops_off, int32_t *__restrict__ ops_len_out) {
     __shared__ int warp_sums[kAnchorThreads / 32];
     __shared__ int s_total, s_score;
     __shared__ int64_t s_pos[kAnchorThreads];
@@ -524,6 +525,18 @@ __global__ void __launch_bounds__(kAnchorThreads) assemble_kernel(
                 if (s0 + t < nb) {
                     const int z = bl[s0 + t].z;
                     for (int u = lane; u < z; u += 32) ops_out[pos + len + u] = 'M';
+                    if (sub) {                     // a block residue costs the table's diagonal
+                        const uint8_t *A = codes + offs[pairs[2 * p]] + bl[s0 + t].x;
+                        int v = 0;
+                        for (int u = lane; u < z; u += 32) {
+                            const int c = A[u];
+                            if (c < nsym) v += sub[c * nsym + c];
+                            else record_error(err, kErrSymbol, p, c);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0) atomicAdd(&s_score, v);
+                    }
                 }
             }
             carry += s_total;
@@ -531,24 +544,23 @@ __global__ void __launch_bounds__(kAnchorThreads) assemble_kernel(
         }
         if (threadIdx.x == 0) {
             const int matched = nb > 0 ? bl[nb - 1].w + bl[nb - 1].z : 0;
-            score_out[p] = s_score + matched * match;
+            score_out[p] = s_score + (sub ? 0 : matched * match);
             ops_len_out[p] = (int32_t)(carry + matched);
         }
         __syncthreads();
     }
 }
 
-}  // namespace msa
-
-using namespace msa;
-
-extern "C" {
-
-msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
-                                       int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t k,
-                                       int32_t match, int32_t mismatch, int32_t gap, int32_t *score_out,
-                                       uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
+// The anchored split with linear gaps (gap_open < 0: segments by nw_run) or
+// affine gaps (segments by nw_affine_run, with the table when sub is given).
+static msa_status anchored_run(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs, int64_t total,
+                               int32_t max_len, const int32_t *pairs, int64_t P, int32_t k, int32_t match,
+                               int32_t mismatch, int32_t gap, int32_t gap_open, const int32_t *sub, int32_t nsym,
+                               int32_t *score_out, uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                               void *stream) {
     if (!ctx) return MSA_EINVAL;
+    if (sub && (nsym < 1 || nsym > 32))
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_anchored: table of %d symbols outside 1..32", nsym);
     if (P < 0 || P >= (int64_t(1) << 30) || n_seqs < 0 || max_len < 0 || total < 0)
         return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_anchored: negative or oversized count");
     if (k < 1 || k > kMaxK)
@@ -620,14 +632,55 @@ msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const
     if ((e = cudaMemcpy2DAsync(seg_ops_off, sizeof(int64_t), seg_offs, 2 * sizeof(int64_t), sizeof(int64_t), S + 1,
                                cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_check(ctx, e, "anchored script offsets");
-    if (msa_status rc = nw_run(ctx, ar, seg_codes, seg_offs, 2 * S, bytes, seg_max, seg_pairs, S, match, mismatch, gap,
-                               seg_score, seg_ops, seg_ops_off, seg_ops_len, st))
+    if (msa_status rc = gap_open < 0
+                            ? nw_run(ctx, ar, seg_codes, seg_offs, 2 * S, bytes, seg_max, seg_pairs, S, match,
+                                     mismatch, gap, seg_score, seg_ops, seg_ops_off, seg_ops_len, st)
+                            : nw_affine_run(ctx, ar, seg_codes, seg_offs, 2 * S, bytes, seg_max, seg_pairs, S, match,
+                                            mismatch, gap_open, gap, seg_score, seg_ops, seg_ops_off, seg_ops_len, st,
+                                            sub, nsym))
         return rc;
-    assemble_kernel<<<std::min(Pi, 65535), kAnchorThreads, 0, st>>>(Pi, blocks, bcap, nblocks, seg_start, seg_score,
-                                                                     seg_ops, seg_ops_off, seg_ops_len, match,
-                                                                     score_out, ops_out, ops_off, ops_len_out);
+    assemble_kernel<<<std::min(Pi, 65535), kAnchorThreads, 0, st>>>(
+        Pi, blocks, bcap, nblocks, seg_start, seg_score, seg_ops, seg_ops_off, seg_ops_len, match, codes, offs, pairs,
+        sub, nsym, ctx->dev_err, score_out, ops_out, ops_off, ops_len_out);
     ++ctx->launches;
     return cuda_check(ctx, cudaGetLastError(), "anchored assemble");
+}
+
+}  // namespace msa
+
+using namespace msa;
+
+extern "C" {
+
+msa_status msa_nw_align_batch_anchored(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs, int32_t n_seqs,
+                                       int64_t total, int32_t max_len, const int32_t *pairs, int64_t P, int32_t k,
+                                       int32_t match, int32_t mismatch, int32_t gap, int32_t *score_out,
+                                       uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
+    return anchored_run(ctx, codes, offs, n_seqs, total, max_len, pairs, P, k, match, mismatch, gap, -1, nullptr, 0,
+                        score_out, ops_out, ops_off, ops_len_out, stream);
+}
+
+msa_status msa_nw_align_batch_anchored_affine(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs,
+                                              int32_t n_seqs, int64_t total, int32_t max_len, const int32_t *pairs,
+                                              int64_t P, int32_t k, int32_t match, int32_t mismatch, int32_t gap_open,
+                                              int32_t gap_ext, int32_t *score_out, uint8_t *ops_out,
+                                              const int64_t *ops_off, int32_t *ops_len_out, void *stream) {
+    if (ctx && gap_open < 0)
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_anchored_affine: negative gap_open %d", gap_open);
+    return anchored_run(ctx, codes, offs, n_seqs, total, max_len, pairs, P, k, match, mismatch, gap_ext, gap_open,
+                        nullptr, 0, score_out, ops_out, ops_off, ops_len_out, stream);
+}
+
+msa_status msa_nw_align_batch_anchored_affine_sub(msa_ctx *ctx, const uint8_t *codes, const int64_t *offs,
+                                                  int32_t n_seqs, int64_t total, int32_t max_len, const int32_t *pairs,
+                                                  int64_t P, int32_t k, const int32_t *sub, int32_t nsym,
+                                                  int32_t gap_open, int32_t gap_ext, int32_t *score_out,
+                                                  uint8_t *ops_out, const int64_t *ops_off, int32_t *ops_len_out,
+                                                  void *stream) {
+    if (ctx && (gap_open < 0 || !sub))
+        return set_error(ctx, MSA_EINVAL, "msa_nw_align_batch_anchored_affine_sub: negative gap_open or null table");
+    return anchored_run(ctx, codes, offs, n_seqs, total, max_len, pairs, P, k, 0, 0, gap_ext, gap_open, sub, nsym,
+                        score_out, ops_out, ops_off, ops_len_out, stream);
 }
 
 }  // extern "C"

@@ -151,3 +151,91 @@ def test_bad_arguments(ctx):
     api.nw_align_batch_anchored(ctx, seqs, np.array([[0, 2]], np.int32), 4, ops_off=off)
     with pytest.raises(RuntimeError):
         ctx.check()
+
+
+# ---------------------------------------------------------------------------
+# affine gaps in the segments (msa_nw_align_batch_anchored_affine / _sub)
+# ---------------------------------------------------------------------------
+
+def _ascii_table(T_code, letters):
+    """A table over codes (letters in code order) as a 256 x 256 table over
+    the oracle's bytes."""
+    T = np.zeros((256, 256), np.int32)
+    for i, x in enumerate(letters):
+        for j, y in enumerate(letters):
+            T[ord(x), ord(y)] = T_code[i][j]
+    return T
+
+
+@pytest.mark.parametrize("costs", [(0, 2, 3, 1), (0, 1, 10, 1), (-1, 2, 4, 2)])
+def test_affine_related_pairs(ctx, costs):
+    match, mismatch, gap_open, gap_ext = costs
+    rng = np.random.default_rng(100 + gap_open)
+    rows = []
+    for L, rate in ((2500, 0.03), (4000, 0.1), (600, 0.2), (1200, 0.05)):
+        a = rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes()
+        rows += [a, _mutate(rng, a, rate)]
+    rows += [b"", b"ACGTACGTACGT", b"ACGTACGTACGT"]
+    pairs = np.array([[0, 1], [1, 0], [2, 3], [4, 5], [6, 7], [8, 9], [9, 10], [8, 0]], np.int32)
+    seqs = api.ByteSeqs.from_list(rows)
+    score, ops, off, ln = api.nw_align_batch_anchored(ctx, seqs, pairs, 12, match, mismatch, gap_ext,
+                                                      gap_open=gap_open)
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    for p, (x, y) in enumerate(pairs):
+        rs, rops = oracle.nw_anchored(rows[x], rows[y], 12, match, mismatch, gap_ext, gap_open=gap_open)
+        assert score[p] == rs, (p, costs)
+        assert ops[off[p]:off[p] + ln[p]].tobytes() == rops, (p, costs)
+
+
+def test_affine_table_dna_codes(ctx):
+    """A random table over DNA codes (some costs negative, diagonal
+    included): segments by the table, block residues by its diagonal."""
+    rng = np.random.default_rng(111)
+    T4 = rng.integers(-3, 6, (4, 4)).astype(np.int32)
+    rows = []
+    for L, rate in ((1800, 0.05), (900, 0.15), (3000, 0.02)):
+        a = rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes()
+        rows += [a, _mutate(rng, a, rate)]
+    codes = [bytes(b"ACGT".index(c) for c in r) for r in rows]
+    pairs = np.array([[0, 1], [2, 3], [4, 5], [5, 4]], np.int32)
+    score, ops, off, ln = api.nw_align_batch_anchored(ctx, api.ByteSeqs.from_list(codes), pairs, 10, 0, 0, 1,
+                                                      gap_open=4, sub=torch.from_numpy(T4).cuda())
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    T = _ascii_table(T4.tolist(), "ACGT")
+    for p, (x, y) in enumerate(pairs):
+        rs, rops = oracle.nw_anchored(rows[x], rows[y], 10, 0, 0, 1, gap_open=4, sub=T)
+        assert score[p] == rs
+        assert ops[off[p]:off[p] + ln[p]].tobytes() == rops
+
+
+def test_affine_blosum62_protein(ctx):
+    """BLOSUM62 with affine gaps (open 10, extend 1) on packed protein
+    sequences: identical to the oracle's split over the same letters."""
+    from paper_2601_15458_gb300 import substitution
+    members, roots = synth.protein_families(seed=6, n_fam=3, per_fam=8)
+    rows = members.seqs() + roots.seqs()
+    ds = synth.SeqSet.from_list(rows, "protein")
+    sq = api.upload_and_pack(ctx, ds)
+    pairs = np.array([[members.n + f, f * 8 + j] for f in range(3) for j in range(8)] + [[0, 9]], np.int32)
+    score, ops, off, ln = api.nw_align_batch_anchored(ctx, sq, pairs, 4, 0, 0, 1, gap_open=10,
+                                                      sub=api.blosum62_table())
+    ctx.check()
+    score, ops, off, ln = score.cpu().numpy(), ops.cpu().numpy(), off.cpu().numpy(), ln.cpu().numpy()
+    T = oracle.blosum62_costs()
+    for p, (x, y) in enumerate(pairs):
+        rs, rops = oracle.nw_anchored(rows[x], rows[y], 4, 0, 0, 1, gap_open=10, sub=T)
+        assert score[p] == rs
+        assert ops[off[p]:off[p] + ln[p]].tobytes() == rops
+
+
+def test_affine_table_rejects_codes_outside(ctx):
+    """A block residue outside the table is reported (the segments' check
+    does not see block residues)."""
+    a = bytes([0, 1, 2, 3] * 10)
+    bs = api.ByteSeqs.from_list([a + bytes([9]) * 12 + a, a + bytes([9]) * 12 + a])
+    api.nw_align_batch_anchored(ctx, bs, np.array([[0, 1]], np.int32), 6, 0, 0, 1, gap_open=2,
+                                sub=torch.zeros(4, 4, dtype=torch.int32, device="cuda"))
+    with pytest.raises(RuntimeError):
+        ctx.check()
