@@ -145,6 +145,11 @@ def test_bad_arguments(ctx):
     for k in (0, 257):
         with pytest.raises(RuntimeError):
             api.nw_align_batch_anchored(ctx, seqs, np.array([[0, 1]], np.int32), k)
+    with pytest.raises(RuntimeError):                  # negative gap opening
+        api.nw_align_batch_anchored(ctx, seqs, np.array([[0, 1]], np.int32), 4, gap_open=-1)
+    with pytest.raises(RuntimeError):                  # table wider than 32 symbols
+        api.nw_align_batch_anchored(ctx, seqs, np.array([[0, 1]], np.int32), 4, gap_open=2,
+                                    sub=torch.zeros(33, 33, dtype=torch.int32, device="cuda"))
     # a pair index past the set: the kernel records it (the host sizes the
     # scripts from offsets given here, so nothing indexes the lengths with it)
     off = torch.tensor([0, 8], dtype=torch.int64, device="cuda")
