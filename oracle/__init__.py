@@ -16,8 +16,9 @@ computes the plain definition of what the GPU path computes:
   (:func:`blosum62_costs`: BLOSUM62, which the paper names for proteins).
 * :func:`brute_alignments` -- every alignment of two short strings, used to
   pin the functions above.
-* :func:`nw_anchored` -- NW split at unique k-mer anchors (the paper's
-  future work for long pairs; this project's definition).
+* :func:`nw_anchored` -- NW split at unique k-mer anchors, linear or affine
+  gaps, flat costs or a table (the paper's future work for long pairs; this
+  project's definition).
 * :func:`kmer_counts`, :func:`pair_feature` -- 4-mer count profiles and the
   pair feature of the learned band proposer (no counterpart in the paper; the
   definition is this project's).
